@@ -1,0 +1,315 @@
+/*
+ * MAPA allocation oracle -- TEST INFRASTRUCTURE ONLY.
+ *
+ * Only tests/, __graft_entry__.smoke() and bench.py's CPU-baseline leg may
+ * load this library.  The product (the CUDA path behind include/mapa.h) never
+ * links, loads or calls it, and shares no code, header or table with it.
+ *
+ * What it computes: a plain, slow restatement of the allocation problem of
+ * MAPA (Ranganath et al., SC'21, arXiv 2110.03214), Sec. 3.2-3.5:
+ *
+ *   G  hardware graph, symmetric integer weights w[u][v] (0 = no link).  With
+ *      fill > 0 every non-adjacent pair of distinct vertices gets weight
+ *      `fill` (Sec. 3.2: the graph is taken as fully connected through PCIe).
+ *   P  application (pattern) graph with k vertices (Sec. 3.1).
+ *   F  free vertices (not busy).  Busy vertices are removed from G by the
+ *      state management of Sec. 3.6.
+ *   match: an injective phi: V(P) -> F with w[phi a][phi b] > 0 for every
+ *      pattern edge (a, b): a one-to-one mapping under which adjacent pattern
+ *      vertices stay adjacent (Sec. 3.3).  Non-induced.
+ *   agg(phi)  = sum over pattern edges (a,b) of w[phi a][phi b]   (Eq. 1)
+ *   pres(phi) = total weight of the subgraph induced by F minus phi(V(P))
+ *                                                                  (Eq. 3)
+ *   score     = alpha * agg + beta * pres, in 64-bit integers.
+ *   decision  = the match with the largest score; among equal scores the
+ *               lexicographically smallest (phi(0), ..., phi(k-1)).  This is
+ *               Algorithm 1's strict ">" scan run over matches enumerated in
+ *               lexicographic order, with the first match as the initial
+ *               incumbent.
+ *   count     = matches / |Aut(P)|: matches counted once per distinct
+ *               subgraph (the graph-mining system of Sec. 3.3 reports each
+ *               match once; Aut(P) acts freely on injective maps).
+ *
+ * Algorithms, all deliberately plain:
+ *   - matches: recursive backtracking over pattern vertices 0..k-1 in id
+ *     order, trying every free unused hardware vertex in increasing order,
+ *     checking every pattern edge to an earlier vertex.  Boolean arrays only,
+ *     no bitsets, no symmetry breaking, no incremental scoring.
+ *   - pres: recomputed from its definition for every match (double loop over
+ *     the remaining free vertices).
+ *   - |Aut(P)|: backtracking over vertex bijections that preserve adjacency
+ *     in both directions.
+ */
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#define OR_MAX_N 256
+#define OR_MAX_K 32
+
+enum {
+    OR_OK = 0,
+    OR_NO_MATCH = 1,
+    OR_INVALID = -1,
+    OR_NOT_DIVISIBLE = -2,
+    OR_BUDGET = -5,
+};
+
+typedef struct {
+    int32_t status;
+    int32_t k;
+    int64_t score;
+    int64_t agg;
+    int64_t pres;
+    uint64_t maps;    /* adjacency-preserving injective maps found */
+    uint64_t aut;     /* |Aut(P)| */
+    uint64_t classes; /* maps / aut */
+    uint8_t tuple[OR_MAX_K];
+} oracle_result;
+
+/* ------------------------------------------------------------------ */
+/* Hardware graph (Sec. 3.2)                                           */
+
+int oracle_weight_matrix(int32_t n, int32_t m, const int32_t *u, const int32_t *v, const int32_t *w,
+                         int32_t fill, int32_t *wmat)
+{
+    if (n < 1 || n > OR_MAX_N || m < 0) return OR_INVALID;
+    memset(wmat, 0, sizeof(int32_t) * (size_t)n * (size_t)n);
+    for (int32_t e = 0; e < m; ++e) {
+        int32_t a = u[e], b = v[e];
+        if (a < 0 || b < 0 || a >= n || b >= n || a == b || w[e] <= 0) return OR_INVALID;
+        if (wmat[a * n + b] != 0) return OR_INVALID; /* duplicate link */
+        wmat[a * n + b] = w[e];
+        wmat[b * n + a] = w[e];
+    }
+    if (fill > 0) {
+        for (int32_t a = 0; a < n; ++a)
+            for (int32_t b = 0; b < n; ++b)
+                if (a != b && wmat[a * n + b] == 0) wmat[a * n + b] = fill;
+    }
+    return OR_OK;
+}
+
+/* ------------------------------------------------------------------ */
+/* Pattern graph (Sec. 3.1) and its automorphisms                      */
+
+static int build_pattern(int32_t k, int32_t m, const int32_t *pa, const int32_t *pb,
+                         uint8_t padj[OR_MAX_K][OR_MAX_K])
+{
+    if (k < 1 || k > OR_MAX_K || m < 0) return OR_INVALID;
+    memset(padj, 0, OR_MAX_K * OR_MAX_K);
+    for (int32_t e = 0; e < m; ++e) {
+        int32_t a = pa[e], b = pb[e];
+        if (a < 0 || b < 0 || a >= k || b >= k || a == b) return OR_INVALID;
+        if (padj[a][b]) return OR_INVALID;
+        padj[a][b] = 1;
+        padj[b][a] = 1;
+    }
+    return OR_OK;
+}
+
+typedef struct {
+    int32_t k;
+    uint8_t (*padj)[OR_MAX_K];
+    int32_t sigma[OR_MAX_K];
+    uint8_t taken[OR_MAX_K];
+    uint64_t count;
+} aut_state;
+
+static void aut_search(aut_state *s, int32_t i)
+{
+    if (i == s->k) {
+        s->count += 1;
+        return;
+    }
+    for (int32_t j = 0; j < s->k; ++j) {
+        if (s->taken[j]) continue;
+        int ok = 1;
+        for (int32_t a = 0; a < i && ok; ++a)
+            if (s->padj[a][i] != s->padj[s->sigma[a]][j]) ok = 0;
+        if (!ok) continue;
+        s->taken[j] = 1;
+        s->sigma[i] = j;
+        aut_search(s, i + 1);
+        s->taken[j] = 0;
+    }
+}
+
+uint64_t oracle_aut_count(int32_t k, int32_t m, const int32_t *pa, const int32_t *pb)
+{
+    uint8_t padj[OR_MAX_K][OR_MAX_K];
+    if (build_pattern(k, m, pa, pb, padj) != OR_OK) return 0;
+    aut_state s;
+    memset(&s, 0, sizeof(s));
+    s.k = k;
+    s.padj = padj;
+    aut_search(&s, 0);
+    return s.count;
+}
+
+/* ------------------------------------------------------------------ */
+/* Scores of one complete map (Eq. 1 and Eq. 3)                        */
+
+static int64_t aggregated_bw(int32_t n, const int32_t *wmat, int32_t m, const int32_t *pa, const int32_t *pb,
+                             const int32_t *phi)
+{
+    int64_t s = 0;
+    for (int32_t e = 0; e < m; ++e) s += wmat[phi[pa[e]] * n + phi[pb[e]]];
+    return s;
+}
+
+static int64_t preserved_bw(int32_t n, const int32_t *wmat, const uint8_t *free_v, int32_t k, const int32_t *phi)
+{
+    uint8_t remain[OR_MAX_N];
+    for (int32_t v = 0; v < n; ++v) remain[v] = free_v[v];
+    for (int32_t i = 0; i < k; ++i) remain[phi[i]] = 0;
+    int64_t s = 0;
+    for (int32_t a = 0; a < n; ++a) {
+        if (!remain[a]) continue;
+        for (int32_t b = a + 1; b < n; ++b)
+            if (remain[b]) s += wmat[a * n + b];
+    }
+    return s;
+}
+
+/* Checks that `tuple` is a match on the free vertices and scores it.
+ * Returns OR_OK, OR_NO_MATCH (not a match) or OR_INVALID. */
+int oracle_score_tuple(int32_t n, const int32_t *wmat, const uint8_t *busy, int32_t k, int32_t m,
+                       const int32_t *pa, const int32_t *pb, int64_t alpha, int64_t beta, const uint8_t *tuple,
+                       int64_t *agg_out, int64_t *pres_out, int64_t *score_out)
+{
+    uint8_t padj[OR_MAX_K][OR_MAX_K];
+    if (n < 1 || n > OR_MAX_N || build_pattern(k, m, pa, pb, padj) != OR_OK) return OR_INVALID;
+    uint8_t free_v[OR_MAX_N], seen[OR_MAX_N];
+    int32_t phi[OR_MAX_K];
+    for (int32_t v = 0; v < n; ++v) {
+        free_v[v] = busy[v] ? 0 : 1;
+        seen[v] = 0;
+    }
+    for (int32_t i = 0; i < k; ++i) {
+        phi[i] = tuple[i];
+        if (phi[i] >= n || !free_v[phi[i]] || seen[phi[i]]) return OR_NO_MATCH;
+        seen[phi[i]] = 1;
+    }
+    for (int32_t e = 0; e < m; ++e)
+        if (wmat[phi[pa[e]] * n + phi[pb[e]]] <= 0) return OR_NO_MATCH;
+    int64_t agg = aggregated_bw(n, wmat, m, pa, pb, phi);
+    int64_t pres = preserved_bw(n, wmat, free_v, k, phi);
+    *agg_out = agg;
+    *pres_out = pres;
+    *score_out = alpha * agg + beta * pres;
+    return OR_OK;
+}
+
+/* ------------------------------------------------------------------ */
+/* Enumeration of all matches and the argmax (Sec. 3.3-3.5, Alg. 1)    */
+
+typedef struct {
+    int32_t n;
+    const int32_t *wmat;
+    uint8_t free_v[OR_MAX_N];
+    uint8_t used[OR_MAX_N];
+    int32_t k, m;
+    const int32_t *pa, *pb;
+    uint8_t (*padj)[OR_MAX_K];
+    int64_t alpha, beta;
+    uint64_t max_maps;
+    int32_t phi[OR_MAX_K];
+    uint64_t maps;
+    int have_best;
+    int64_t best_score, best_agg, best_pres;
+    int32_t best_phi[OR_MAX_K];
+    int aborted;
+} match_state;
+
+static void visit_match(match_state *s)
+{
+    s->maps += 1;
+    if (s->max_maps && s->maps > s->max_maps) {
+        s->aborted = 1;
+        return;
+    }
+    int64_t agg = aggregated_bw(s->n, s->wmat, s->m, s->pa, s->pb, s->phi);
+    int64_t pres = preserved_bw(s->n, s->wmat, s->free_v, s->k, s->phi);
+    int64_t score = s->alpha * agg + s->beta * pres;
+    /* Strict ">" over lexicographically increasing matches: the first
+     * maximum wins, i.e. the lexicographically smallest tuple. */
+    if (!s->have_best || score > s->best_score) {
+        s->have_best = 1;
+        s->best_score = score;
+        s->best_agg = agg;
+        s->best_pres = pres;
+        memcpy(s->best_phi, s->phi, sizeof(int32_t) * (size_t)s->k);
+    }
+}
+
+static void extend(match_state *s, int32_t i)
+{
+    if (s->aborted) return;
+    if (i == s->k) {
+        visit_match(s);
+        return;
+    }
+    for (int32_t x = 0; x < s->n; ++x) {
+        if (!s->free_v[x] || s->used[x]) continue;
+        int ok = 1;
+        for (int32_t a = 0; a < i && ok; ++a)
+            if (s->padj[a][i] && s->wmat[s->phi[a] * s->n + x] <= 0) ok = 0;
+        if (!ok) continue;
+        s->used[x] = 1;
+        s->phi[i] = x;
+        extend(s, i + 1);
+        s->used[x] = 0;
+        if (s->aborted) return;
+    }
+}
+
+int oracle_decide(int32_t n, const int32_t *wmat, const uint8_t *busy, int32_t k, int32_t m, const int32_t *pa,
+                  const int32_t *pb, int64_t alpha, int64_t beta, uint64_t max_maps, oracle_result *out)
+{
+    memset(out, 0, sizeof(*out));
+    out->k = k;
+    uint8_t padj[OR_MAX_K][OR_MAX_K];
+    if (n < 1 || n > OR_MAX_N || build_pattern(k, m, pa, pb, padj) != OR_OK) {
+        out->status = OR_INVALID;
+        return OR_INVALID;
+    }
+    match_state *s = (match_state *)calloc(1, sizeof(match_state));
+    if (!s) {
+        out->status = OR_INVALID;
+        return OR_INVALID;
+    }
+    s->n = n;
+    s->wmat = wmat;
+    for (int32_t v = 0; v < n; ++v) s->free_v[v] = busy[v] ? 0 : 1;
+    s->k = k;
+    s->m = m;
+    s->pa = pa;
+    s->pb = pb;
+    s->padj = padj;
+    s->alpha = alpha;
+    s->beta = beta;
+    s->max_maps = max_maps;
+    extend(s, 0);
+
+    out->maps = s->maps;
+    /* |Aut(P)| only when there is something to divide (k! for a clique). */
+    if (s->have_best && !s->aborted) out->aut = oracle_aut_count(k, m, pa, pb);
+    if (s->aborted) {
+        out->status = OR_BUDGET;
+    } else if (!s->have_best) {
+        out->status = OR_NO_MATCH;
+    } else if (out->aut == 0 || s->maps % out->aut != 0) {
+        out->status = OR_NOT_DIVISIBLE;
+    } else {
+        out->status = OR_OK;
+        out->classes = s->maps / out->aut;
+        out->score = s->best_score;
+        out->agg = s->best_agg;
+        out->pres = s->best_pres;
+        for (int32_t i = 0; i < k; ++i) out->tuple[i] = (uint8_t)s->best_phi[i];
+    }
+    int32_t st = out->status;
+    free(s);
+    return st;
+}
