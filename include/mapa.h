@@ -1,0 +1,238 @@
+/*
+ * mapa.h -- C ABI of the GB300 MAPA allocation engine.
+ *
+ * MAPA (Ranganath et al., "MAPA: Multi-Accelerator Pattern Allocation Policy
+ * for Multi-Tenant GPU Servers", SC'21, arXiv 2110.03214) places a job whose
+ * GPUs communicate in a known pattern (ring, tree, all-to-all: the
+ * application graph of Sec. 3.1) onto the free accelerators of a server whose
+ * links are a weighted hardware graph (Sec. 3.2).  This library runs the
+ * data-parallel core of that policy on one GPU:
+ *
+ *   1. enumerate every match of the pattern in the free part of the hardware
+ *      graph: injective maps phi: V(P) -> F under which adjacent pattern
+ *      vertices land on linked accelerators (Sec. 3.3), counted once per
+ *      distinct subgraph (maps modulo the pattern's automorphisms);
+ *   2. score each match in int32:  S = alpha * AggBW + beta * PreservedBW,
+ *      AggBW = sum of the link weights under the pattern's edges (Eq. 1),
+ *      PreservedBW = total link weight among the free accelerators that the
+ *      match leaves idle (Eq. 3);
+ *   3. pick the largest S; among equal S the lexicographically smallest
+ *      (phi(0), ..., phi(k-1)) (Algorithm 1's ">" scan, run in lexicographic
+ *      order), and on request commit it to the device-resident occupancy
+ *      (state management, Sec. 3.6).
+ *
+ * alpha = 0, beta = 1 is the paper's Preserve policy for bandwidth-insensitive
+ * jobs (Sec. 3.5.2); alpha = 1, beta = 0 is its Greedy comparison policy
+ * (Sec. 4, argmax of AggBW).
+ *
+ * Conventions for every call:
+ *   - A negative return value is an error; details in mapa_last_error().
+ *     MAPA_NO_FIT is a normal outcome (nothing matched, nothing committed).
+ *   - Input arrays belong to the caller and are copied before the call
+ *     returns.  Output structs belong to the caller.
+ *   - A context owns its device memory, stream, topologies, patterns and
+ *     occupancy; mapa_ctx_destroy frees all of it.  One context per host
+ *     thread; calls on one context must not overlap.
+ *   - All vertex ids are 0-based.  Bitmasks hold vertex v in bit (v % 32) of
+ *     32-bit word v / 32.
+ */
+#ifndef MAPA_H
+#define MAPA_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define MAPA_MAX_N 256       /* accelerators in one hardware graph */
+#define MAPA_MAX_K 32        /* vertices in one pattern */
+#define MAPA_MASK_WORDS 8    /* 256-bit vertex masks */
+#define MAPA_MAX_CLASSES 8   /* distinct link weights in one hardware graph */
+#define MAPA_MAX_WEIGHT (1 << 20)
+
+typedef struct mapa_ctx_s *mapa_ctx;
+
+enum mapa_status {
+    MAPA_OK = 0,
+    MAPA_NO_FIT = 1,        /* no match on the free vertices; nothing committed */
+    MAPA_E_INVALID = -1,    /* malformed argument (ids, sizes, graph shape) */
+    MAPA_E_RANGE = -2,      /* value outside the supported range (n, k, weights, int32 scores) */
+    MAPA_E_NOMEM = -3,      /* device or host allocation failed, or frontier cap too small */
+    MAPA_E_CUDA = -4,       /* a CUDA call failed */
+    MAPA_E_BUDGET = -5,     /* the request's max_embeddings was exceeded; no decision */
+    MAPA_E_TIMEOUT = -6,    /* a bounded device wait gave up */
+    MAPA_E_STATE = -7       /* call not valid in the current state (e.g. unknown job id) */
+};
+
+/* Pattern shapes for mapa_pattern_builtin (k always counts vertices).
+ *   RING:   cycle 0-1-...-(k-1)-0 for k >= 3; k = 2 is one edge; k = 1 one vertex.
+ *   TREE:   binary tree in heap order, parent(i) = (i - 1) / 2.
+ *   CLIQUE: all pairs (all-to-all).
+ *   PATH:   chain 0-1-...-(k-1).
+ * Ring and tree are the NCCL communication shapes of Sec. 3.1 (Fig. 5). */
+enum mapa_pattern_kind { MAPA_RING = 0, MAPA_TREE = 1, MAPA_CLIQUE = 2, MAPA_PATH = 3 };
+
+enum mapa_mode {
+    MAPA_MODE_EXHAUSTIVE = 0 /* enumerate every match (count is exact) */
+};
+
+/* Scoring policy of one request.  S = alpha * AggBW + beta * PreservedBW is
+ * computed in int32; the call fails with MAPA_E_RANGE unless
+ * (|alpha| + |beta|) * (total link weight of the graph) < 2^31.
+ * max_embeddings > 0 bounds the matches a request may enumerate; past it the
+ * request ends with MAPA_E_BUDGET and no decision. */
+typedef struct {
+    int32_t alpha;
+    int32_t beta;
+    int32_t mode;
+    int32_t reserved;
+    uint64_t max_embeddings;
+} mapa_policy; /* 24 bytes */
+
+/* One request of a batch (64 bytes, no pointers, so an array of them can live
+ * in host or device memory).  busy: vertices unavailable to this request
+ * (see the flags of mapa_allocate_batch for how it combines with the
+ * device occupancy). */
+typedef struct {
+    int32_t pattern_id;
+    int32_t reserved;
+    mapa_policy policy;
+    uint32_t busy[MAPA_MASK_WORDS];
+} mapa_request;
+
+/* Decision for one request (80 bytes).
+ *   status: MAPA_OK, MAPA_NO_FIT or a negative error for this request.
+ *   score, agg, pres: S, AggBW (Eq. 1) and PreservedBW (Eq. 3) of the chosen match.
+ *   count: matches found, once per distinct subgraph (maps / |Aut(P)|).
+ *   job_id: id of the committed allocation (>= 1), or 0 when nothing was committed.
+ *   verts[i] = phi(i) for i < k. */
+typedef struct {
+    int32_t status;
+    int32_t score;
+    int32_t agg;
+    int32_t pres;
+    uint64_t count;
+    int64_t job_id;
+    int32_t k;
+    int32_t reserved;
+    uint8_t verts[MAPA_MAX_K];
+    uint64_t reserved2;
+} mapa_result;
+
+/* ---- context ----------------------------------------------------------- */
+
+/* Creates a context on CUDA device `device`.  frontier_mem_cap bounds the
+ * device memory used for partial-match frontiers, in bytes (0 = 4 GiB); the
+ * enumeration proceeds in chunks so any request fits, only slower.
+ * Returns MAPA_E_CUDA if the device cannot be used. */
+int mapa_ctx_create(int device, uint64_t frontier_mem_cap, mapa_ctx *out);
+
+/* Frees every resource of the context (NULL is ignored). */
+void mapa_ctx_destroy(mapa_ctx ctx);
+
+/* Work of this context is issued on `cuda_stream` (a cudaStream_t; NULL =
+ * the context's own stream).  The stream must outlive its use. */
+int mapa_ctx_set_stream(mapa_ctx ctx, void *cuda_stream);
+
+/* Message of the last failed call on ctx (never NULL; "" if none).  Valid
+ * until the next call on ctx.  mapa_last_error(NULL) reports failures of
+ * mapa_ctx_create. */
+const char *mapa_last_error(mapa_ctx ctx);
+
+/* ---- inputs ------------------------------------------------------------ */
+
+/* Loads a hardware graph (Sec. 3.2): n accelerators, m undirected links
+ * (u[i], v[i]) with bandwidth weight w[i].  fill_weight > 0 gives every
+ * unlinked pair that weight (the paper's "fully connected through PCIe",
+ * fill 12 GB/s); 0 keeps only the listed links.  Requires 1 <= n <= 256,
+ * no self-loops or duplicate links, 0 < w < 2^20, at most 8 distinct
+ * weights.  Its occupancy starts all free.  *topo_id receives the id. */
+int mapa_topology_load(mapa_ctx ctx, int32_t n, int32_t m, const int32_t *u, const int32_t *v,
+                       const int32_t *w, int32_t fill_weight, int32_t *topo_id);
+
+/* Loads an application graph (Sec. 3.1): k vertices, m undirected edges
+ * (a[i], b[i]).  Requires 1 <= k <= 32, no self-loops or duplicate edges.
+ * The host computes its automorphism group and symmetry-breaking order
+ * constraints here.  *pattern_id receives the id. */
+int mapa_pattern_load(mapa_ctx ctx, int32_t k, int32_t m, const int32_t *a, const int32_t *b,
+                      int32_t *pattern_id);
+
+/* Loads one of the built-in shapes (enum mapa_pattern_kind) with k vertices. */
+int mapa_pattern_builtin(mapa_ctx ctx, int32_t kind, int32_t k, int32_t *pattern_id);
+
+/* ---- allocation -------------------------------------------------------- */
+
+/* Allocates one job against the topology's current occupancy: enumerate,
+ * score, pick (Sec. 3.3-3.5), and on MAPA_OK mark the chosen vertices busy
+ * under a new job id (Sec. 3.6).  policy NULL = {alpha 1, beta 1}.
+ * Returns MAPA_OK, MAPA_NO_FIT or an error; *out is always written. */
+int mapa_allocate(mapa_ctx ctx, int32_t topo_id, int32_t pattern_id, const mapa_policy *policy,
+                  mapa_result *out);
+
+/* Returns the vertices of a committed job to the free pool (Sec. 3.6).
+ * MAPA_E_STATE if job_id is not a live job of this topology. */
+int mapa_release(mapa_ctx ctx, int32_t topo_id, int64_t job_id);
+
+/* Flags of mapa_allocate_batch. */
+#define MAPA_BATCH_INDEPENDENT 0u /* each request sees only its own busy mask; nothing is committed */
+#define MAPA_BATCH_SEQUENTIAL 1u  /* in array order: busy = occupancy | request mask; OK results commit */
+#define MAPA_BATCH_DEVICE 2u      /* reqs and out are device pointers (else host pointers) */
+
+/* Decides nreq requests in one call.  With MAPA_BATCH_INDEPENDENT the
+ * requests are grouped by pattern and enumerated together (frontiers of
+ * many requests share each launch); results are independent of the batch's
+ * composition and order.  With MAPA_BATCH_SEQUENTIAL each request sees the
+ * commits of the ones before it.  out[i] answers reqs[i].  Returns MAPA_OK
+ * when every request was processed (per-request outcomes are in
+ * out[i].status), or a negative error for the call as a whole. */
+int mapa_allocate_batch(mapa_ctx ctx, int32_t topo_id, int32_t nreq, const mapa_request *reqs,
+                        mapa_result *out, uint32_t flags);
+
+/* ---- introspection ----------------------------------------------------- */
+
+/* Counters of one context since creation or the last mapa_stats_reset. */
+typedef struct {
+    uint64_t kernel_launches;  /* kernels this context launched */
+    uint64_t tail_launches;    /* launches of the fused last-level kernel */
+    double tail_ms;            /* their device time (CUDA events; only while timing is on) */
+    uint64_t tail_parents;     /* stored partial matches they expanded */
+    uint64_t tail_nodes;       /* first-tail-level nodes (two fused levels) */
+    uint64_t tail_leaves;      /* complete matches they scored */
+    uint64_t tail_int_ops;     /* algorithmic integer operations of those launches */
+    uint64_t spill_entries;    /* partial matches written to frontiers */
+    uint64_t spill_bytes;      /* frontier bytes written plus read back */
+    uint64_t requests;         /* requests decided */
+    uint64_t embeddings;       /* matches scored, once per distinct subgraph */
+} mapa_stats;
+
+/* Copies the counters into *out. */
+int mapa_stats_get(mapa_ctx ctx, mapa_stats *out);
+
+/* Zeroes the counters. */
+int mapa_stats_reset(mapa_ctx ctx);
+
+/* on != 0: bracket every fused last-level launch with CUDA events on the
+ * context's stream and add their device time to tail_ms (costs a stream
+ * synchronisation per request group). */
+int mapa_ctx_set_timing(mapa_ctx ctx, int on);
+
+/* Copies the topology's occupancy (busy mask, 8 words) to host memory. */
+int mapa_occupancy_get(mapa_ctx ctx, int32_t topo_id, uint32_t *busy_out);
+
+/* Host-only pattern analysis (no GPU, no context): |Aut(P)| and, per pattern
+ * vertex i, back_masks[i] = earlier neighbours of i and lo_masks[i] = the
+ * earlier vertices j with the constraint phi(j) < phi(i).  These constraints
+ * keep exactly one map per automorphism class, the lexicographically
+ * smallest.  Arrays hold k entries.  Returns MAPA_OK or an error. */
+int mapa_pattern_analyze(int32_t k, int32_t m, const int32_t *a, const int32_t *b, uint64_t *aut_order,
+                         uint32_t *back_masks, uint32_t *lo_masks);
+
+/* Library version string. */
+const char *mapa_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* MAPA_H */

@@ -1,0 +1,91 @@
+"""Builds the in-tree C-ABI library ``_build/libmapa.so`` for sm_103a.
+
+Two translation units (the CUDA engine and the host runtime) compile in
+parallel with nvcc / g++; nothing is installed outside the package.
+"""
+
+from __future__ import annotations
+
+import os
+import shutil
+import subprocess
+import sys
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+CSRC = os.path.join(HERE, "csrc")
+BUILD = os.path.join(HERE, "_build")
+LIB = os.path.join(BUILD, "libmapa.so")
+INCLUDE = os.path.join(os.path.dirname(HERE), "include")
+
+ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
+
+
+def _cuda_home() -> str:
+    home = os.environ.get("CUDA_HOME") or os.environ.get("CUDA_PATH")
+    if home and os.path.isdir(home):
+        return home
+    nvcc = shutil.which("nvcc")
+    if nvcc:
+        return os.path.dirname(os.path.dirname(os.path.realpath(nvcc)))
+    return "/usr/local/cuda"
+
+
+def _sources():
+    return [os.path.join(CSRC, f) for f in sorted(os.listdir(CSRC)) if f.endswith((".cu", ".cpp", ".h"))] + [
+        os.path.join(INCLUDE, "mapa.h")
+    ]
+
+
+def up_to_date() -> bool:
+    if not os.path.exists(LIB):
+        return False
+    t = os.path.getmtime(LIB)
+    return all(os.path.getmtime(s) <= t for s in _sources())
+
+
+def build(force: bool = False, verbose: bool = False, ptxas_info: bool = False) -> str:
+    if not force and up_to_date():
+        return LIB
+    os.makedirs(BUILD, exist_ok=True)
+    cuda = _cuda_home()
+    nvcc = os.path.join(cuda, "bin", "nvcc")
+    common = ["-O3", "-std=c++17", "-I", CSRC, "-I", INCLUDE]
+    jobs = []
+    objs = []
+    for src in sorted(os.listdir(CSRC)):
+        path = os.path.join(CSRC, src)
+        obj = os.path.join(BUILD, os.path.splitext(src)[0] + ".o")
+        if src.endswith(".cu"):
+            cmd = [nvcc, *ARCH, "-lineinfo", "-Xcompiler", "-fPIC", "-c", path, "-o", obj, *common]
+            if ptxas_info:
+                cmd += ["-Xptxas", "-v"]
+        elif src.endswith(".cpp"):
+            cmd = ["g++", "-fPIC", "-c", path, "-o", obj, "-I", os.path.join(cuda, "include"), *common]
+        else:
+            continue
+        objs.append(obj)
+        if verbose:
+            print(" ".join(cmd), flush=True)
+        jobs.append((cmd, subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.STDOUT)))
+    failed = []
+    for cmd, proc in jobs:
+        out, _ = proc.communicate()
+        text = out.decode(errors="replace")
+        if proc.returncode != 0:
+            failed.append(f"$ {' '.join(cmd)}\n{text}")
+        elif verbose or ptxas_info:
+            sys.stdout.write(text)
+    if failed:
+        raise RuntimeError("build of libmapa failed:\n" + "\n".join(failed))
+    lib_dir = os.path.join(cuda, "lib64")
+    tmp = LIB + ".tmp"
+    link = [nvcc, *ARCH, "-shared", "-o", tmp, *objs, "-cudart", "shared", "-Xlinker", f"-rpath,{lib_dir}"]
+    if verbose:
+        print(" ".join(link), flush=True)
+    subprocess.check_call(link)
+    os.replace(tmp, LIB)
+    return LIB
+
+
+if __name__ == "__main__":
+    print(build(force="--force" in sys.argv, verbose=True, ptxas_info="--ptxas" in sys.argv))

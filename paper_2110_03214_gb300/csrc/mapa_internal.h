@@ -1,0 +1,126 @@
+// Internal declarations shared by the host runtime (mapa_capi.cpp) and the
+// device engine (mapa_engine.cu).  Not part of the public ABI.
+#pragma once
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "../../include/mapa.h"
+
+namespace mapa {
+
+constexpr int kMaxN = MAPA_MAX_N;
+constexpr int kMaxK = MAPA_MAX_K;
+constexpr int kMaxClasses = MAPA_MAX_CLASSES;
+
+// Level kernels: 256 threads, each warp owns 32 * kIpt consecutive parents.
+constexpr int kTpb = 256;
+constexpr int kWarps = kTpb / 32;
+constexpr int kIpt = 4;
+constexpr int kTile = kTpb * kIpt;
+
+// Largest request group enumerated together (larger groups are sliced).
+constexpr int kMaxGroup = 1 << 20;
+
+// Pattern as the device sees it: vertex i is matched at level i; back[i] holds
+// the earlier neighbours of i, lo[i] the earlier vertices j with the
+// symmetry-breaking constraint phi(j) < phi(i).
+struct PatternArgs {
+    int32_t k;
+    uint32_t back[kMaxK];
+    uint32_t lo[kMaxK];
+};
+
+// Hardware graph in device memory.
+//   adj[v * W + w]            bit u of word w: link v-u exists
+//   clsv[(v * C + c) * W + w] bit u: link v-u has weight class c
+//   wc[c]                     weight of class c
+struct TopoArgs {
+    int32_t n;
+    int32_t W;  // words per vertex mask: 1, 2, 4 or 8
+    int32_t C;  // distinct link weights
+    const uint32_t *adj;
+    const uint32_t *clsv;
+    const int32_t *wc;
+};
+
+// One frontier level in structure-of-arrays form, `cap` entries per column.
+//   S[i]                      partial score of entry i
+//   r[i]                      request index within the group
+//   R[w * cap + i]            free vertices not yet used (word w)
+//   T[j * cap + i]            tuple bytes 4j..4j+3 (phi of pattern vertices)
+struct LevelView {
+    int32_t *S;
+    uint32_t *r;
+    uint32_t *R;
+    uint32_t *T;
+    uint64_t cap;
+};
+
+// Per-request state of a group being enumerated.
+struct GroupArgs {
+    int32_t size;              // requests in the group
+    const int32_t *req_index;  // group slot -> position in the batch
+    const mapa_request *reqs;  // the batch (device)
+    mapa_result *out;          // results (device), indexed by batch position
+    int32_t *alpha;            // [size]
+    int32_t *beta;             // [size]
+    uint64_t *key;             // [size] argmax key of the current last-level chunk
+    unsigned long long *count; // [size] matches found
+    int32_t *best_s;           // [size]
+    int32_t *best_valid;       // [size]
+    uint32_t *best_t;          // [size * 8] best tuple bytes
+    const uint32_t *occupancy; // device occupancy or nullptr (request masks only)
+    int64_t total_weight;      // for the int32 range check
+    int32_t *error;            // device error word (0 = fine)
+};
+
+// Device-side error codes written to the error word.
+enum DeviceError : int32_t {
+    kDevOk = 0,
+    kDevScoreMismatch = 1,  // finalize found a score that disagrees with its tuple
+    kDevResolveMiss = 2,    // resolve could not re-find the argmax tail
+};
+
+struct Engine;  // device buffers + launch helpers (mapa_engine.cu)
+
+Engine *engine_create(int device, uint64_t frontier_cap, std::string *err);
+void engine_destroy(Engine *e);
+void engine_set_stream(Engine *e, cudaStream_t s);
+cudaStream_t engine_stream(Engine *e);
+
+struct TopoDevice {
+    int32_t n = 0, W = 1, C = 0;
+    int64_t total_weight = 0;
+    uint32_t *adj = nullptr;
+    uint32_t *clsv = nullptr;
+    int32_t *wc = nullptr;
+    uint32_t *occupancy = nullptr;  // [8]
+    int64_t *owner = nullptr;       // [n] job id holding each vertex, 0 = free
+    unsigned long long *next_job = nullptr;
+    int32_t *scratch = nullptr;     // small per-topology scratch (release count)
+    TopoArgs args() const { return TopoArgs{n, W, C, adj, clsv, wc}; }
+};
+
+// Runs one batch on the device.  reqs/out are device arrays of nreq entries.
+// sequential: process in order against the topology occupancy and commit.
+int engine_run_batch(Engine *e, const TopoDevice &t, const std::vector<PatternArgs> &patterns, int32_t nreq,
+                     const mapa_request *reqs_dev, mapa_result *out_dev, bool sequential, std::string *err);
+
+int engine_stats(Engine *e, mapa_stats *out);
+void engine_stats_reset(Engine *e);
+void engine_set_timing(Engine *e, bool on);
+
+int engine_release(Engine *e, const TopoDevice &t, int64_t job_id, int32_t *freed, std::string *err);
+
+// Scratch for staging host batches.
+int engine_stage(Engine *e, int32_t nreq, mapa_request **reqs_dev, mapa_result **out_dev, std::string *err);
+
+// Host-side pattern analysis (automorphisms and order constraints).
+int analyze_pattern(int32_t k, const std::vector<std::pair<int, int>> &edges, PatternArgs *out,
+                    uint64_t *aut_order, std::string *err);
+
+}  // namespace mapa

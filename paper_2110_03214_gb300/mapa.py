@@ -1,0 +1,329 @@
+"""ctypes binding of the C ABI in include/mapa.h (argument marshalling only).
+
+Every function named ``mapa_*`` here forwards to the C function of the same
+name in ``_build/libmapa.so``; all enumeration, scoring and selection runs in
+that library's CUDA kernels.  Importing this module raises if the library has
+not been built (``python -m paper_2110_03214_gb300.build``): there is no
+fallback path.
+"""
+
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from . import build as _build
+
+MAPA_OK = 0
+MAPA_NO_FIT = 1
+MAPA_E_INVALID = -1
+MAPA_E_RANGE = -2
+MAPA_E_NOMEM = -3
+MAPA_E_CUDA = -4
+MAPA_E_BUDGET = -5
+MAPA_E_TIMEOUT = -6
+MAPA_E_STATE = -7
+
+MAPA_RING, MAPA_TREE, MAPA_CLIQUE, MAPA_PATH = 0, 1, 2, 3
+KIND = {"ring": MAPA_RING, "tree": MAPA_TREE, "clique": MAPA_CLIQUE, "path": MAPA_PATH}
+
+MAPA_BATCH_INDEPENDENT = 0
+MAPA_BATCH_SEQUENTIAL = 1
+MAPA_BATCH_DEVICE = 2
+
+MAX_K = 32
+
+REQUEST_DTYPE = np.dtype(
+    {
+        "names": ["pattern_id", "reserved", "alpha", "beta", "mode", "reserved1", "max_embeddings", "busy"],
+        "formats": ["<i4", "<i4", "<i4", "<i4", "<i4", "<i4", "<u8", ("<u4", (8,))],
+        "offsets": [0, 4, 8, 12, 16, 20, 24, 32],
+        "itemsize": 64,
+    }
+)
+
+RESULT_DTYPE = np.dtype(
+    {
+        "names": ["status", "score", "agg", "pres", "count", "job_id", "k", "reserved", "verts", "reserved2"],
+        "formats": ["<i4", "<i4", "<i4", "<i4", "<u8", "<i8", "<i4", "<i4", ("u1", (32,)), "<u8"],
+        "offsets": [0, 4, 8, 12, 16, 24, 32, 36, 40, 72],
+        "itemsize": 80,
+    }
+)
+
+
+class Stats(ctypes.Structure):
+    """mirror of mapa_stats"""
+
+    _fields_ = [
+        ("kernel_launches", ctypes.c_uint64),
+        ("tail_launches", ctypes.c_uint64),
+        ("tail_ms", ctypes.c_double),
+        ("tail_parents", ctypes.c_uint64),
+        ("tail_nodes", ctypes.c_uint64),
+        ("tail_leaves", ctypes.c_uint64),
+        ("tail_int_ops", ctypes.c_uint64),
+        ("spill_entries", ctypes.c_uint64),
+        ("spill_bytes", ctypes.c_uint64),
+        ("requests", ctypes.c_uint64),
+        ("embeddings", ctypes.c_uint64),
+    ]
+
+    def as_dict(self):
+        return {name: getattr(self, name) for name, _ in self._fields_}
+
+
+class MapaError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"mapa error {code}: {msg}")
+        self.code = code
+
+
+def _load() -> ctypes.CDLL:
+    if not os.path.exists(_build.LIB):
+        raise ImportError(f"{_build.LIB} is missing: build it with `python -m paper_2110_03214_gb300.build`")
+    lib = ctypes.CDLL(_build.LIB)
+    vp, i32, u32, i64, u64 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_uint32, ctypes.c_int64, ctypes.c_uint64
+    i32p = ctypes.POINTER(ctypes.c_int32)
+    sig = {
+        "mapa_version": ([], ctypes.c_char_p),
+        "mapa_ctx_create": ([ctypes.c_int, u64, ctypes.POINTER(vp)], ctypes.c_int),
+        "mapa_ctx_destroy": ([vp], None),
+        "mapa_ctx_set_stream": ([vp, vp], ctypes.c_int),
+        "mapa_last_error": ([vp], ctypes.c_char_p),
+        "mapa_topology_load": ([vp, i32, i32, i32p, i32p, i32p, i32, i32p], ctypes.c_int),
+        "mapa_pattern_load": ([vp, i32, i32, i32p, i32p, i32p], ctypes.c_int),
+        "mapa_pattern_builtin": ([vp, i32, i32, i32p], ctypes.c_int),
+        "mapa_allocate": ([vp, i32, i32, vp, vp], ctypes.c_int),
+        "mapa_release": ([vp, i32, i64], ctypes.c_int),
+        "mapa_allocate_batch": ([vp, i32, i32, vp, vp, u32], ctypes.c_int),
+        "mapa_occupancy_get": ([vp, i32, ctypes.POINTER(ctypes.c_uint32)], ctypes.c_int),
+        "mapa_stats_get": ([vp, ctypes.POINTER(Stats)], ctypes.c_int),
+        "mapa_stats_reset": ([vp], ctypes.c_int),
+        "mapa_ctx_set_timing": ([vp, ctypes.c_int], ctypes.c_int),
+        "mapa_pattern_analyze": ([i32, i32, i32p, i32p, ctypes.POINTER(ctypes.c_uint64),
+                                  ctypes.POINTER(ctypes.c_uint32), ctypes.POINTER(ctypes.c_uint32)], ctypes.c_int),
+    }
+    for name, (args, res) in sig.items():
+        fn = getattr(lib, name)
+        fn.argtypes = args
+        fn.restype = res
+    return lib
+
+
+lib = _load()
+
+#: C symbols the header declares; tests check the library exports each one.
+SYMBOLS = (
+    "mapa_ctx_create", "mapa_ctx_destroy", "mapa_ctx_set_stream", "mapa_last_error", "mapa_topology_load",
+    "mapa_pattern_load", "mapa_pattern_builtin", "mapa_allocate", "mapa_release", "mapa_allocate_batch",
+    "mapa_occupancy_get", "mapa_pattern_analyze", "mapa_version", "mapa_stats_get", "mapa_stats_reset",
+    "mapa_ctx_set_timing",
+)
+
+
+def _i32(a):
+    a = np.ascontiguousarray(a, dtype=np.int32)
+    return a, a.ctypes.data_as(ctypes.POINTER(ctypes.c_int32))
+
+
+def _check(ctx, rc: int, ok=(MAPA_OK,)):
+    if rc not in ok:
+        raise MapaError(rc, lib.mapa_last_error(ctx).decode())
+    return rc
+
+
+# ---- functions with the C names ---------------------------------------------
+
+
+def mapa_version() -> str:
+    return lib.mapa_version().decode()
+
+
+def mapa_ctx_create(device: int = 0, frontier_mem_cap: int = 0):
+    h = ctypes.c_void_p()
+    rc = lib.mapa_ctx_create(device, frontier_mem_cap, ctypes.byref(h))
+    if rc != MAPA_OK:
+        raise MapaError(rc, lib.mapa_last_error(None).decode())
+    return h
+
+
+def mapa_ctx_destroy(ctx) -> None:
+    lib.mapa_ctx_destroy(ctx)
+
+
+def mapa_ctx_set_stream(ctx, stream_ptr: int) -> None:
+    _check(ctx, lib.mapa_ctx_set_stream(ctx, ctypes.c_void_p(stream_ptr or None)))
+
+
+def mapa_last_error(ctx) -> str:
+    return lib.mapa_last_error(ctx).decode()
+
+
+def mapa_topology_load(ctx, n: int, u, v, w, fill_weight: int = 0) -> int:
+    ua, up = _i32(u)
+    va, vp_ = _i32(v)
+    wa, wp = _i32(w)
+    out = ctypes.c_int32()
+    _check(ctx, lib.mapa_topology_load(ctx, n, len(ua), up, vp_, wp, fill_weight, ctypes.byref(out)))
+    return out.value
+
+
+def mapa_pattern_load(ctx, k: int, a, b) -> int:
+    aa, ap = _i32(a)
+    ba, bp = _i32(b)
+    out = ctypes.c_int32()
+    _check(ctx, lib.mapa_pattern_load(ctx, k, len(aa), ap, bp, ctypes.byref(out)))
+    return out.value
+
+
+def mapa_pattern_builtin(ctx, kind, k: int) -> int:
+    kind = KIND.get(kind, kind)
+    out = ctypes.c_int32()
+    _check(ctx, lib.mapa_pattern_builtin(ctx, int(kind), k, ctypes.byref(out)))
+    return out.value
+
+
+def mapa_allocate(ctx, topo_id: int, pattern_id: int, alpha: int = 1, beta: int = 1, max_embeddings: int = 0):
+    pol = np.zeros(1, dtype=np.dtype([("alpha", "<i4"), ("beta", "<i4"), ("mode", "<i4"), ("r", "<i4"),
+                                       ("max_embeddings", "<u8")]))
+    pol["alpha"], pol["beta"], pol["max_embeddings"] = alpha, beta, max_embeddings
+    res = np.zeros(1, RESULT_DTYPE)
+    rc = lib.mapa_allocate(ctx, topo_id, pattern_id, pol.ctypes.data, res.ctypes.data)
+    if rc < 0 and res["status"][0] == rc and rc not in (MAPA_E_BUDGET, MAPA_E_RANGE):
+        raise MapaError(rc, lib.mapa_last_error(ctx).decode())
+    return res[0]
+
+
+def mapa_release(ctx, topo_id: int, job_id: int) -> None:
+    _check(ctx, lib.mapa_release(ctx, topo_id, int(job_id)))
+
+
+def mapa_allocate_batch(ctx, topo_id: int, reqs, flags: int = MAPA_BATCH_INDEPENDENT, out=None):
+    """Host batch: reqs is a REQUEST_DTYPE array; returns a RESULT_DTYPE array."""
+    reqs = np.ascontiguousarray(reqs, dtype=REQUEST_DTYPE)
+    if out is None:
+        out = np.zeros(reqs.shape[0], RESULT_DTYPE)
+    _check(ctx, lib.mapa_allocate_batch(ctx, topo_id, reqs.shape[0], reqs.ctypes.data, out.ctypes.data, flags))
+    return out
+
+
+def mapa_allocate_batch_device(ctx, topo_id: int, nreq: int, reqs_ptr: int, out_ptr: int,
+                               flags: int = MAPA_BATCH_INDEPENDENT) -> None:
+    """Device batch: reqs_ptr / out_ptr are device addresses (e.g. torch data_ptr())."""
+    _check(ctx, lib.mapa_allocate_batch(ctx, topo_id, nreq, ctypes.c_void_p(reqs_ptr), ctypes.c_void_p(out_ptr),
+                                        flags | MAPA_BATCH_DEVICE))
+
+
+def mapa_occupancy_get(ctx, topo_id: int) -> np.ndarray:
+    busy = np.zeros(8, np.uint32)
+    _check(ctx, lib.mapa_occupancy_get(ctx, topo_id, busy.ctypes.data_as(ctypes.POINTER(ctypes.c_uint32))))
+    return busy
+
+
+def mapa_stats_get(ctx) -> dict:
+    st = Stats()
+    _check(ctx, lib.mapa_stats_get(ctx, ctypes.byref(st)))
+    return st.as_dict()
+
+
+def mapa_stats_reset(ctx) -> None:
+    _check(ctx, lib.mapa_stats_reset(ctx))
+
+
+def mapa_ctx_set_timing(ctx, on: bool) -> None:
+    _check(ctx, lib.mapa_ctx_set_timing(ctx, 1 if on else 0))
+
+
+def mapa_pattern_analyze(k: int, a, b):
+    """Host-only: (|Aut(P)|, back_masks[k], lo_masks[k])."""
+    aa, ap = _i32(a)
+    ba, bp = _i32(b)
+    aut = ctypes.c_uint64()
+    back = np.zeros(max(k, 1), np.uint32)
+    lo = np.zeros(max(k, 1), np.uint32)
+    rc = lib.mapa_pattern_analyze(k, len(aa), ap, bp, ctypes.byref(aut),
+                                  back.ctypes.data_as(ctypes.POINTER(ctypes.c_uint32)),
+                                  lo.ctypes.data_as(ctypes.POINTER(ctypes.c_uint32)))
+    if rc != MAPA_OK:
+        raise MapaError(rc, "pattern analysis failed")
+    return aut.value, back[:k], lo[:k]
+
+
+# ---- convenience ----------------------------------------------------------------
+
+
+def make_requests(pattern_ids, alpha, beta, busy, max_embeddings=0) -> np.ndarray:
+    pattern_ids = np.asarray(pattern_ids, np.int32)
+    r = np.zeros(pattern_ids.shape[0], REQUEST_DTYPE)
+    r["pattern_id"] = pattern_ids
+    r["alpha"] = alpha
+    r["beta"] = beta
+    r["max_embeddings"] = max_embeddings
+    r["busy"] = np.asarray(busy, np.uint32).reshape(-1, 8)
+    return r
+
+
+class Context:
+    """Owns one mapa_ctx; the methods forward to the mapa_* functions."""
+
+    def __init__(self, device: int = 0, frontier_mem_cap: int = 0):
+        self.h = mapa_ctx_create(device, frontier_mem_cap)
+
+    def close(self):
+        if self.h:
+            mapa_ctx_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def topology_load(self, topo) -> int:
+        return mapa_topology_load(self.h, topo.n, topo.u, topo.v, topo.w, topo.fill_weight)
+
+    def pattern_load(self, pattern) -> int:
+        if pattern.kind in KIND:
+            return mapa_pattern_builtin(self.h, pattern.kind, pattern.k)
+        return mapa_pattern_load(self.h, pattern.k, pattern.a, pattern.b)
+
+    def requests(self, workload_requests, pattern_ids) -> np.ndarray:
+        ids = np.asarray(pattern_ids, np.int32)[workload_requests.pattern_index]
+        return make_requests(ids, workload_requests.alpha, workload_requests.beta, workload_requests.busy)
+
+    def set_stream(self, stream_ptr: int):
+        mapa_ctx_set_stream(self.h, stream_ptr)
+
+    def allocate(self, topo_id, pattern_id, alpha=1, beta=1, max_embeddings=0):
+        return mapa_allocate(self.h, topo_id, pattern_id, alpha, beta, max_embeddings)
+
+    def release(self, topo_id, job_id):
+        mapa_release(self.h, topo_id, job_id)
+
+    def allocate_batch(self, topo_id, reqs, flags=MAPA_BATCH_INDEPENDENT):
+        return mapa_allocate_batch(self.h, topo_id, reqs, flags)
+
+    def allocate_batch_device(self, topo_id, nreq, reqs_ptr, out_ptr, flags=MAPA_BATCH_INDEPENDENT):
+        mapa_allocate_batch_device(self.h, topo_id, nreq, reqs_ptr, out_ptr, flags)
+
+    def occupancy(self, topo_id):
+        return mapa_occupancy_get(self.h, topo_id)
+
+    def stats(self) -> dict:
+        return mapa_stats_get(self.h)
+
+    def stats_reset(self):
+        mapa_stats_reset(self.h)
+
+    def set_timing(self, on: bool):
+        mapa_ctx_set_timing(self.h, on)

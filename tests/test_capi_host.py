@@ -1,0 +1,136 @@
+"""CPU-side checks of the C-ABI library: it builds, loads without a GPU,
+exports every symbol include/mapa.h declares, and its host pattern analysis
+(automorphism group and order constraints) agrees with brute force."""
+
+import itertools
+import os
+import re
+
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_2110_03214_gb300 import build as B
+from paper_2110_03214_gb300 import workloads as W
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def M():
+    B.build()
+    from paper_2110_03214_gb300 import mapa
+
+    return mapa
+
+
+def _header_functions():
+    text = open(os.path.join(ROOT, "include", "mapa.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(mapa_[a-z_]+)\s*\(", text)))
+
+
+def test_library_exports_every_declared_symbol(M):
+    declared = _header_functions()
+    assert len(declared) >= 13
+    for name in declared:
+        assert hasattr(M.lib, name), name
+    assert set(declared) == set(M.SYMBOLS)
+    assert "sm_103a" in M.mapa_version()
+
+
+def test_struct_layouts(M):
+    assert M.REQUEST_DTYPE.itemsize == 64
+    assert M.RESULT_DTYPE.itemsize == 80
+
+
+def _brute_orbit_constraints(k, pa, pb):
+    """All automorphisms by brute force, then the stabiliser-chain orbits."""
+    edges = {frozenset((int(a), int(b))) for a, b in zip(pa, pb)}
+    auts = [s for s in itertools.permutations(range(k)) if {frozenset((s[a], s[b])) for a, b in map(tuple, edges)} == edges]
+    lo = [0] * k
+    group = auts
+    for v in range(k):
+        orbit = {s[v] for s in group}
+        for u in orbit:
+            if u != v:
+                assert u > v
+                lo[u] |= 1 << v
+        group = [s for s in group if s[v] == v]
+    return len(auts), lo
+
+
+@pytest.mark.parametrize("kind,k", [(kd, k) for kd in ("ring", "tree", "clique", "path") for k in range(1, 8)])
+def test_pattern_analysis_matches_brute_force(M, kind, k):
+    p = W.pattern(kind, k)
+    aut, back, lo = M.mapa_pattern_analyze(k, p.a, p.b)
+    want_aut, want_lo = _brute_orbit_constraints(k, p.a, p.b)
+    assert aut == want_aut == O.aut_count(k, p.a, p.b)
+    assert list(lo) == want_lo
+    for i in range(k):
+        nb = {int(b) for a, b in zip(p.a, p.b) if a == i} | {int(a) for a, b in zip(p.a, p.b) if b == i}
+        assert int(back[i]) == sum(1 << j for j in nb if j < i)
+
+
+def test_pattern_analysis_random_patterns(M):
+    rng = W.Rng(11, 4)
+    for trial in range(40):
+        k = int(rng.integers(1, 7, 1)[0])
+        p = W.random_pattern(rng, k, p_edge=0.35, connected=bool(trial % 2))
+        aut, back, lo = M.mapa_pattern_analyze(k, p.a, p.b)
+        want_aut, want_lo = _brute_orbit_constraints(k, p.a, p.b)
+        assert aut == want_aut and list(lo) == want_lo, trial
+
+
+def test_expected_constraint_sets(M):
+    # ring-4: 0<1, 0<2, 0<3, 1<3 ; ring-5: 0<1..4, 1<4 ; tree-7: 1<2, 3<4, 5<6 ; path-3: 0<2
+    def lo_of(kind, k):
+        p = W.pattern(kind, k)
+        return [int(x) for x in M.mapa_pattern_analyze(k, p.a, p.b)[2]]
+
+    assert lo_of("ring", 4) == [0, 1, 1, 0b11]
+    assert lo_of("ring", 5) == [0, 1, 1, 1, 0b11]
+    assert lo_of("tree", 7) == [0, 0, 0b10, 0, 0b1000, 0, 0b100000]
+    assert lo_of("path", 3) == [0, 0, 1]
+    assert lo_of("tree", 4) == [0, 1, 0, 0]  # path 3-1-0-2: reversal swaps 0 and 1
+
+
+def test_large_pattern_groups(M):
+    for kind, k, want in (("tree", 31, 32768), ("ring", 32, 64), ("clique", 8, 40320), ("tree", 15, 128)):
+        p = W.pattern(kind, k)
+        aut, _, _ = M.mapa_pattern_analyze(k, p.a, p.b)
+        assert aut == want, (kind, k)
+    p = W.pattern("clique", 32)  # 32! saturates the 64-bit order
+    aut, _, lo = M.mapa_pattern_analyze(32, p.a, p.b)
+    assert aut == 2**64 - 1
+    assert all(int(lo[i]) == (1 << i) - 1 for i in range(32))
+
+
+def test_lex_min_representatives_by_brute_force(M):
+    """Maps obeying the constraints are exactly one per Aut-class, and each
+    is the lexicographic minimum of its class (tiny graph, every built-in k<=5)."""
+    topo = W.hybrid_cube_mesh8(W.Rng(1, 1))
+    adj = {(int(a), int(b)) for a, b in zip(topo.u, topo.v)} | {(int(b), int(a)) for a, b in zip(topo.u, topo.v)}
+    for kind in ("ring", "tree", "clique", "path"):
+        for k in range(1, 6):
+            p = W.pattern(kind, k)
+            aut, back, lo = M.mapa_pattern_analyze(k, p.a, p.b)
+            edges = list(zip(p.a.tolist(), p.b.tolist()))
+            maps = [t for t in itertools.permutations(range(8), k) if all((t[a], t[b]) in adj for a, b in edges)]
+            reps = [t for t in maps if all(t[j] < t[i] for i in range(k) for j in range(k) if (int(lo[i]) >> j) & 1)]
+            assert len(reps) * aut == len(maps), (kind, k)
+            auts = [s for s in itertools.permutations(range(k))
+                    if {frozenset((s[a], s[b])) for a, b in edges} == {frozenset(e) for e in edges}]
+            for t in reps:
+                assert t == min(tuple(t[s[i]] for i in range(k)) for s in auts)
+
+
+def test_invalid_patterns_rejected(M):
+    with pytest.raises(M.MapaError):
+        M.mapa_pattern_analyze(3, [0, 0], [1, 1])  # duplicate edge
+    with pytest.raises(M.MapaError):
+        M.mapa_pattern_analyze(3, [0], [0])  # self-loop
+    with pytest.raises(M.MapaError):
+        M.mapa_pattern_analyze(33, [], [])
+    with pytest.raises(M.MapaError):
+        M.mapa_pattern_analyze(3, [0], [5])
