@@ -39,7 +39,7 @@ def _args():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--config", type=int, default=2)
+    ap.add_argument("--workload", default="regular32", choices=("cube_mesh8", "regular32", "torus64", "dragonfly128", "boards256"))
     ap.add_argument("--requests", type=int, default=None)
     ap.add_argument("--cpu-seconds", type=float, default=15.0, help="bounded oracle sample length")
     ap.add_argument("--plain-requests", type=int, default=300, help="requests timed through the plain per-request path")
@@ -112,14 +112,82 @@ class ClockSampler:
                 "samples": len(rows), "reasons": sorted(reasons)}
 
 
+class NvmlSampler:
+    """Polls SM clock and clock-event reasons through NVML every ~1 ms (read only)."""
+
+    REASONS = {0x4: "sw_power_cap", 0x8: "hw_slowdown", 0x20: "sw_thermal_slowdown", 0x40: "hw_thermal_slowdown",
+               0x80: "hw_power_brake_slowdown"}
+
+    def __init__(self, index: int):
+        import ctypes
+        import threading
+
+        self.ok = False
+        self.samples = []
+        self.max_mhz = None
+        self._stop = threading.Event()
+        self._thread = None
+        try:
+            lib = ctypes.CDLL("libnvidia-ml.so.1")
+            if lib.nvmlInit_v2() != 0:
+                return
+            h = ctypes.c_void_p()
+            if lib.nvmlDeviceGetHandleByIndex_v2(index, ctypes.byref(h)) != 0:
+                return
+            self._lib, self._h, self._ct = lib, h, ctypes
+            mx = ctypes.c_uint()
+            if lib.nvmlDeviceGetMaxClockInfo(h, 1, ctypes.byref(mx)) == 0:
+                self.max_mhz = float(mx.value)
+            self._reasons_fn = getattr(lib, "nvmlDeviceGetCurrentClocksEventReasons", None) or getattr(
+                lib, "nvmlDeviceGetCurrentClocksThrottleReasons", None)
+            self.ok = True
+        except OSError:
+            pass
+
+    def _run(self):
+        ct = self._ct
+        clk = ct.c_uint()
+        rs = ct.c_ulonglong()
+        while not self._stop.is_set():
+            r = 0
+            if self._reasons_fn is not None and self._reasons_fn(self._h, ct.byref(rs)) == 0:
+                r = rs.value
+            if self._lib.nvmlDeviceGetClockInfo(self._h, 1, ct.byref(clk)) == 0:
+                self.samples.append((float(clk.value), r))
+            time.sleep(0.001)
+
+    def start(self):
+        import threading
+
+        if self.ok:
+            self._thread = threading.Thread(target=self._run, daemon=True)
+            self._thread.start()
+
+    def stop(self):
+        if not self._thread:
+            return None
+        self._stop.set()
+        self._thread.join()
+        if not self.samples:
+            return None
+        reasons = set()
+        for _, r in self.samples:
+            for bit, name in self.REASONS.items():
+                if r & bit:
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(c for c, _ in self.samples), "sm_max_mhz": self.max_mhz,
+                "samples": len(self.samples), "source": "nvml", "reasons": sorted(reasons)}
+
+
 def _kernel_source_hash() -> str:
     with open(os.path.join(ROOT, "paper_2110_03214_gb300", "csrc", "mapa_engine.cu"), "rb") as f:
         return hashlib.sha256(f.read()).hexdigest()[:16]
 
 
-def _traffic_per_launch(workload: str):
-    """DRAM bytes per launch of the fused-tail kernel from the committed ncu
-    summary, if it was taken on the current kernel source."""
+def _traffic_per_launch(workload: str, parents_per_launch: float):
+    """DRAM bytes per launch of the fused-tail kernel: the committed ncu
+    per-parent figure times the parents of an average launch, or None when
+    the kernel source changed since the capture."""
     path = os.path.join(ROOT, "profiles", "k_last_traffic.json")
     try:
         with open(path) as f:
@@ -128,7 +196,7 @@ def _traffic_per_launch(workload: str):
         return None
     if rec.get("source_sha256_16") != _kernel_source_hash() or rec.get("workload") != workload:
         return None
-    return rec.get("dram_bytes_per_launch")
+    return rec["dram_bytes_per_parent"] * parents_per_launch
 
 
 def _oracle_sample(wl, budget_s: float, threads: int, start: int = 0):
@@ -169,7 +237,7 @@ def run_reference(a):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
-    wl = W.config(a.config, num_requests=a.requests)
+    wl = W.workload(a.workload, num_requests=a.requests)
     threads = os.cpu_count() or 1
     per_step = max(0.5, min(20.0, 120.0 / max(1, a.steps + a.warmup)))
     for _ in range(a.warmup):
@@ -216,7 +284,7 @@ def run_ours(a):
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
 
     # Each rank decides its own batch of the same shape (independent requests shard with no exchange).
-    wl = W.config(a.config, num_requests=a.requests, seed=a.config + 1000 * rank)
+    wl = W.workload(a.workload, num_requests=a.requests, seed=W.WORKLOADS.index(a.workload) + 1 + 1000 * rank)
     nreq = len(wl.requests)
     stream = torch.cuda.current_stream()
     ctx = M.Context(local)
@@ -240,10 +308,12 @@ def run_ours(a):
     ctx.stats_reset()
     ctx.set_timing(True)
     clocks = ClockSampler(local)
+    nvml = NvmlSampler(local)
     if world > 1:
         dist.barrier()
     torch.cuda.synchronize()
     clocks.start()
+    nvml.start()
     times = []
     for _ in range(a.steps):
         flush.zero_()
@@ -257,7 +327,12 @@ def run_ours(a):
     torch.cuda.synchronize()
     if world > 1:
         dist.barrier()
-    clk = clocks.stop()
+    clk = nvml.stop()
+    smi = clocks.stop()
+    if clk is None:
+        clk = smi
+    elif smi:
+        clk["nvidia_smi_samples"] = smi["samples"]
     st = ctx.stats()
     ctx.set_timing(False)
     got = d_out.cpu().numpy().view(M.RESULT_DTYPE)
@@ -320,7 +395,7 @@ def run_ours(a):
     ops_per_launch = st["tail_int_ops"] / max(1, st["tail_launches"])
     achieved_gops = ops_per_launch / (tail_launch_ms / 1000.0) / 1e9 if tail_launch_ms > 0 else 0.0
     workload_name = f"{wl.name}: {wl.description}, {nreq} requests"
-    traffic = _traffic_per_launch(f"{wl.name}/{nreq}")
+    traffic = _traffic_per_launch(f"{wl.name}/{nreq}", st["tail_parents"] / max(1, st["tail_launches"]))
 
     if rank == 0:
         line = {

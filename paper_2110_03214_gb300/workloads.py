@@ -363,19 +363,37 @@ class Workload:
     description: str
 
 
-def config(cfg: int, num_requests: int | None = None, seed: int | None = None) -> Workload:
-    """The five workload shapes (1-based `cfg`), seeded by config index."""
-    seed = cfg if seed is None else seed
+WORKLOADS = ("cube_mesh8", "regular32", "torus64", "dragonfly128", "boards256")
+
+
+def workload(name: str, num_requests: int | None = None, seed: int | None = None) -> Workload:
+    """The five workload shapes, each seeded by its own default seed.
+
+    cube_mesh8:   8-vertex hybrid cube-mesh, 1000 independent requests, ring-4 /
+                  clique-3 / path-2, 0-3 busy vertices.
+    regular32:    32-vertex random 6-regular graph, 10^4 independent requests,
+                  ring-8 / tree-7 / clique-4, occupancy U[0, 0.5].
+    torus64:      4x4x4 torus, 10^5 requests, ring/tree k in 2..16, clique k
+                  in 2..4, occupancy U[0, 0.6].
+    dragonfly128: 16 groups x K8 plus one global link per group pair, request
+                  mix of torus64, occupancy kept on the device (served).
+    boards256:    32 boards x hybrid cube-mesh with a 4-uplink ring of boards,
+                  ring-32 / tree-31 / clique-8, streamed.
+    """
+    if name not in WORKLOADS:
+        raise ValueError(f"unknown workload {name!r}; one of {WORKLOADS}")
+    default_seed = WORKLOADS.index(name) + 1
+    seed = default_seed if seed is None else seed
     trng = Rng(seed, 1)
     rrng = Rng(seed, 2)
-    if cfg == 1:
+    if name == "cube_mesh8":
         topo = hybrid_cube_mesh8(trng)
         r = 1000 if num_requests is None else num_requests
         pats = [pattern("ring", 4), pattern("clique", 3), pattern("path", 2)]
         index = rrng.integers(0, 2, r).astype(np.int32)
         busy = _busy_masks(rrng, topo.n, rrng.integers(0, 3, r))
         desc = "8-vertex hybrid cube-mesh, ring-4/clique-3/path-2, 0-3 busy vertices"
-    elif cfg == 2:
+    elif name == "regular32":
         topo = random_regular(trng, 32, 6)
         r = 10_000 if num_requests is None else num_requests
         pats = [pattern("ring", 8), pattern("tree", 7), pattern("clique", 4)]
@@ -383,31 +401,29 @@ def config(cfg: int, num_requests: int | None = None, seed: int | None = None) -
         u = rrng.uniform(r) * 0.5
         busy = _busy_masks(rrng, topo.n, np.floor(u * topo.n).astype(np.int64))
         desc = "32-vertex random 6-regular graph, ring-8/tree-7/clique-4, occupancy U[0,0.5]"
-    elif cfg == 3:
+    elif name == "torus64":
         topo = torus3d(4)
         r = 100_000 if num_requests is None else num_requests
         pats, index = _mix_patterns(rrng, r, 16, 4)
         u = rrng.uniform(r) * 0.6
         busy = _busy_masks(rrng, topo.n, np.floor(u * topo.n).astype(np.int64))
         desc = "4x4x4 torus, ring/tree k in 2..16, clique k in 2..4, occupancy U[0,0.6]"
-    elif cfg == 4:
+    elif name == "dragonfly128":
         topo = dragonfly(trng)
         r = 10_000 if num_requests is None else num_requests
         pats, index = _mix_patterns(rrng, r, 16, 4)
         busy = np.zeros((r, BUSY_WORDS), np.uint32)  # served: occupancy lives on the device
         desc = "128-vertex dragonfly (16 x K8 + one global link per group pair), served"
-    elif cfg == 5:
+    else:
         topo = boards256(trng)
         r = 1_000_000 if num_requests is None else num_requests
         pats = [pattern("ring", 32), pattern("tree", 31), pattern("clique", 8)]
         index = rrng.integers(0, 2, r).astype(np.int32)
         busy = np.zeros((r, BUSY_WORDS), np.uint32)
         desc = "256-vertex boards (32 x hybrid cube-mesh, 4-uplink ring of boards), streamed"
-    else:
-        raise ValueError("config index is 1..5")
     ones = np.ones(r, np.int32)
     reqs = Requests(pats, index, ones.copy(), ones.copy(), busy)
-    return Workload(f"config{cfg}", topo, reqs, desc)
+    return Workload(name, topo, reqs, desc)
 
 
 def arrivals(rng: Rng, count: int, rate: float, mean_k: float, n: int, occupancy: float = 0.6):

@@ -56,14 +56,14 @@ def _run_and_compare(M, ctx, topo, reqs, idx=None, flags=0, max_maps=0):
 
 
 def test_config1_every_request(M, ctx):
-    wl = W.config(1)
+    wl = W.workload("cube_mesh8")
     _, compared = _run_and_compare(M, ctx, wl.topology, wl.requests)
     assert compared == 1000
 
 
 def test_config2_full_batch_sampled(M, ctx):
     """10^4 requests in one batch (the benchmark's workload), sampled parity."""
-    wl = W.config(2)
+    wl = W.workload("regular32")
     rng = W.Rng(2, 99)
     sample = sorted(set(rng.integers(0, len(wl.requests) - 1, 64).tolist()))
     res, compared = _run_and_compare(M, ctx, wl.topology, wl.requests, idx=sample)
@@ -74,7 +74,7 @@ def test_config2_full_batch_sampled(M, ctx):
 
 
 def test_config3_torus_subset(M, ctx):
-    wl = W.config(3, num_requests=4000)
+    wl = W.workload("torus64", num_requests=4000)
     ks = np.asarray([wl.requests.patterns[i].k for i in wl.requests.pattern_index])
     busy = np.asarray([sum(bin(int(x)).count("1") for x in row) for row in wl.requests.busy])
     keep = np.nonzero((ks <= 9) | (busy >= 24))[0][:1500]
@@ -153,10 +153,12 @@ def test_dgx_worked_example_through_gpu(M, ctx):
 
 def test_small_frontier_cap_forces_chunks(M):
     """A 64 MiB frontier forces depth-first chunking; results must not change."""
-    wl = W.config(2, num_requests=3000)
+    wl = W.workload("regular32", num_requests=3000)
     with M.Context(0, frontier_mem_cap=64 << 20) as small:
         tid, pids = _load(small, wl)
         res_small = small.allocate_batch(tid, small.requests(wl.requests, pids))
+        # three pattern groups; more fused-tail launches than groups means chunks were taken
+        assert small.stats()["tail_launches"] > 3
     with M.Context(0) as big:
         tid, pids = _load(big, wl)
         res_big = big.allocate_batch(tid, big.requests(wl.requests, pids))
@@ -168,7 +170,7 @@ def test_small_frontier_cap_forces_chunks(M):
 
 
 def test_results_independent_of_batch_composition(M, ctx):
-    wl = W.config(2, num_requests=600)
+    wl = W.workload("regular32", num_requests=600)
     tid, pids = _load(ctx, wl)
     reqs = ctx.requests(wl.requests, pids)
     whole = ctx.allocate_batch(tid, reqs)
@@ -196,8 +198,8 @@ def test_edge_cases(M, ctx):
         M.make_requests([ring4], 1, 1, some),
         M.make_requests([clique5], 1, 1, np.zeros((1, 8), np.uint32)),
         M.make_requests([one], 0, 1, np.zeros((1, 8), np.uint32)),
-        M.make_requests([99], 1, 1, np.zeros((1, 8), np.uint32)),
-        M.make_requests([ring4], 1 << 20, 1, np.zeros((1, 8), np.uint32)),
+        M.make_requests([1 << 30], 1, 1, np.zeros((1, 8), np.uint32)),
+        M.make_requests([ring4], 1 << 24, 1, np.zeros((1, 8), np.uint32)),  # (2^24+1) * W(G) > 2^31
         M.make_requests([ring4], 1, 1, np.zeros((1, 8), np.uint32), max_embeddings=3),
     ])
     res = ctx.allocate_batch(tid, reqs)
@@ -211,7 +213,7 @@ def test_edge_cases(M, ctx):
 
 def test_sequential_commits_and_release(M, ctx):
     """mapa_allocate commits against device occupancy (Sec. 3.6); replayed on the oracle."""
-    wl = W.config(1)
+    wl = W.workload("cube_mesh8")
     tid, pids = _load(ctx, wl)
     inst = O.Instance.from_topology(wl.topology)
     busy = np.zeros(8, bool)
@@ -240,7 +242,7 @@ def test_sequential_commits_and_release(M, ctx):
 
 
 def test_sequential_batch_matches_replay(M, ctx):
-    wl = W.config(2, num_requests=40)
+    wl = W.workload("regular32", num_requests=40)
     tid, pids = _load(ctx, wl)
     reqs = ctx.requests(wl.requests, pids)
     reqs["busy"][:] = 0
@@ -259,7 +261,7 @@ def test_sequential_batch_matches_replay(M, ctx):
 
 def test_device_pointer_batch(M, ctx):
     torch = pytest.importorskip("torch")
-    wl = W.config(2, num_requests=500)
+    wl = W.workload("regular32", num_requests=500)
     tid, pids = _load(ctx, wl)
     reqs = ctx.requests(wl.requests, pids)
     host = ctx.allocate_batch(tid, reqs)

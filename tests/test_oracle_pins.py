@@ -186,7 +186,7 @@ def _pres_identity(n, wm, busy, tup):
 
 def test_preserved_identity_and_aut_invariance():
     rng = W.Rng(99, 3)
-    wl = W.config(2, num_requests=12)
+    wl = W.workload("regular32", num_requests=12)
     topo = wl.topology
     inst = O.Instance.from_topology(topo)
     wm = inst.wmat.reshape(topo.n, topo.n)
