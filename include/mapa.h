@@ -189,6 +189,41 @@ int mapa_release(mapa_ctx ctx, int32_t topo_id, int64_t job_id);
 int mapa_allocate_batch(mapa_ctx ctx, int32_t topo_id, int32_t nreq, const mapa_request *reqs,
                         mapa_result *out, uint32_t flags);
 
+/* ---- allocation-free decisions ------------------------------------------ */
+
+/* Limits of mapa_allocate_batch_noalloc. */
+#define MAPA_NOALLOC_MAX_REQUESTS 4096
+#define MAPA_NOALLOC_MAX_N 32
+#define MAPA_NOALLOC_MAX_K 8
+
+/* Decides up to 4096 independent requests without allocating any memory.
+ * (The paper has no counterpart; this exists for callers that must not
+ * allocate.)  Some callers cannot call cudaMalloc: a scheduler loop running
+ * while a CUDA graph is being captured on its thread, a hook running inside
+ * another framework's allocator, or a process whose device memory a serving
+ * runtime has fully reserved.  This call launches one kernel whose scratch
+ * (per-request argmax keys, match counts and a completion ticket) is a fixed
+ * 64 KiB + 256 B device array compiled into the library; every GPU that
+ * loads the library holds it until the process exits.  Nothing is allocated,
+ * freed or committed.
+ *
+ * reqs_dev and out_dev are device pointers to nreq entries; every request
+ * must carry pattern_id and is decided on its own busy mask exactly as
+ * mapa_allocate_batch with MAPA_BATCH_INDEPENDENT decides it (same status,
+ * score, AggBW, PreservedBW, count and tuple).  A request with another
+ * pattern id gets MAPA_E_INVALID.
+ * Limits: nreq <= 4096, the topology has at most 32 vertices, the pattern at
+ * most 8; beyond them the call returns MAPA_E_RANGE and launches nothing.
+ * The first call on a device resolves the scratch array's device address
+ * (cudaGetSymbolAddress with that device current); make that first call
+ * before any stream capture.  Work is issued on the context's stream and the
+ * call returns without waiting for it.  All calls on a device share the one
+ * scratch array and reset it at their start: calls whose kernels overlap on
+ * the GPU (other streams, other contexts, other host threads) race and
+ * corrupt each other's results -- serialise them. */
+int mapa_allocate_batch_noalloc(mapa_ctx ctx, int32_t topo_id, int32_t pattern_id, int32_t nreq,
+                                const mapa_request *reqs_dev, mapa_result *out_dev);
+
 /* ---- introspection ----------------------------------------------------- */
 
 /* Counters of one context since creation or the last mapa_stats_reset. */

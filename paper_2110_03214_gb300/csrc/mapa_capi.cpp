@@ -463,6 +463,22 @@ int mapa_occupancy_get(mapa_ctx ctx, int32_t topo_id, uint32_t *busy_out) {
     return MAPA_OK;
 }
 
+int mapa_allocate_batch_noalloc(mapa_ctx ctx, int32_t topo_id, int32_t pattern_id, int32_t nreq,
+                                const mapa_request *reqs_dev, mapa_result *out_dev) {
+    if (!ctx) return MAPA_E_INVALID;
+    TopoEntry *te = get_topo(ctx, topo_id);
+    if (!te) return fail(ctx, MAPA_E_INVALID, "unknown topology id");
+    if (pattern_id < 0 || pattern_id >= static_cast<int32_t>(ctx->patterns.size()))
+        return fail(ctx, MAPA_E_INVALID, "unknown pattern id");
+    if (nreq > 0 && (!reqs_dev || !out_dev)) return fail(ctx, MAPA_E_INVALID, "bad request arrays");
+    CTX_CUDA(ctx, cudaSetDevice(ctx->device));
+    std::string err;
+    const int rc = mapa::noalloc_decide(te->dev, ctx->pattern_args[pattern_id], pattern_id, nreq, reqs_dev, out_dev,
+                                        mapa::engine_stream(ctx->engine), &err);
+    if (rc != MAPA_OK) return fail(ctx, rc, err);
+    return MAPA_OK;
+}
+
 int mapa_stats_get(mapa_ctx ctx, mapa_stats *out) {
     if (!ctx || !out) return MAPA_E_INVALID;
     return mapa::engine_stats(ctx->engine, out);

@@ -114,6 +114,10 @@ int engine_stats(Engine *e, mapa_stats *out);
 void engine_stats_reset(Engine *e);
 void engine_set_timing(Engine *e, bool on);
 
+// Allocation-free single-kernel decision (mapa_noalloc.cu).
+int noalloc_decide(const TopoDevice &t, const PatternArgs &pat, int32_t pattern_id, int32_t nreq,
+                   const mapa_request *reqs_dev, mapa_result *out_dev, cudaStream_t stream, std::string *err);
+
 int engine_release(Engine *e, const TopoDevice &t, int64_t job_id, int32_t *freed, std::string *err);
 
 // Scratch for staging host batches.

@@ -99,6 +99,7 @@ def _load() -> ctypes.CDLL:
         "mapa_allocate": ([vp, i32, i32, vp, vp], ctypes.c_int),
         "mapa_release": ([vp, i32, i64], ctypes.c_int),
         "mapa_allocate_batch": ([vp, i32, i32, vp, vp, u32], ctypes.c_int),
+        "mapa_allocate_batch_noalloc": ([vp, i32, i32, i32, vp, vp], ctypes.c_int),
         "mapa_occupancy_get": ([vp, i32, ctypes.POINTER(ctypes.c_uint32)], ctypes.c_int),
         "mapa_stats_get": ([vp, ctypes.POINTER(Stats)], ctypes.c_int),
         "mapa_stats_reset": ([vp], ctypes.c_int),
@@ -120,7 +121,7 @@ SYMBOLS = (
     "mapa_ctx_create", "mapa_ctx_destroy", "mapa_ctx_set_stream", "mapa_last_error", "mapa_topology_load",
     "mapa_pattern_load", "mapa_pattern_builtin", "mapa_allocate", "mapa_release", "mapa_allocate_batch",
     "mapa_occupancy_get", "mapa_pattern_analyze", "mapa_version", "mapa_stats_get", "mapa_stats_reset",
-    "mapa_ctx_set_timing",
+    "mapa_ctx_set_timing", "mapa_allocate_batch_noalloc",
 )
 
 
@@ -215,6 +216,13 @@ def mapa_allocate_batch_device(ctx, topo_id: int, nreq: int, reqs_ptr: int, out_
     """Device batch: reqs_ptr / out_ptr are device addresses (e.g. torch data_ptr())."""
     _check(ctx, lib.mapa_allocate_batch(ctx, topo_id, nreq, ctypes.c_void_p(reqs_ptr), ctypes.c_void_p(out_ptr),
                                         flags | MAPA_BATCH_DEVICE))
+
+
+def mapa_allocate_batch_noalloc(ctx, topo_id: int, pattern_id: int, nreq: int, reqs_ptr: int, out_ptr: int) -> None:
+    """Allocation-free decision of up to 4096 requests of one pattern (device
+    pointers; see mapa.h for the limits and the shared-scratch rules)."""
+    _check(ctx, lib.mapa_allocate_batch_noalloc(ctx, topo_id, pattern_id, nreq, ctypes.c_void_p(reqs_ptr),
+                                                ctypes.c_void_p(out_ptr)))
 
 
 def mapa_occupancy_get(ctx, topo_id: int) -> np.ndarray:
