@@ -1,0 +1,91 @@
+// Internal engine state shared by the batch driver (mapa_engine.cu) and the
+// per-mask-width runner translation units (mapa_engine_w*.cu).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "mapa_internal.h"
+
+namespace mapa {
+
+#define MAPA_CUDA_TRY(x)                                                                 \
+    do {                                                                                 \
+        cudaError_t e_ = (x);                                                            \
+        if (e_ != cudaSuccess) {                                                         \
+            if (err) *err = std::string(#x) + ": " + cudaGetErrorString(e_);             \
+            return MAPA_E_CUDA;                                                          \
+        }                                                                                \
+    } while (0)
+
+constexpr int kStatWords = 8;
+
+struct Engine {
+    int device = 0;
+    int sm_count = 0;
+    cudaStream_t own_stream = nullptr;
+    cudaStream_t stream = nullptr;
+    uint64_t frontier_cap = 0;
+    char *arena = nullptr;        // frontier levels and their control words
+    uint64_t arena_bytes = 0;
+    char *group_mem = nullptr;    // per-request group arrays
+    uint64_t group_bytes = 0;
+    mapa_request *stage_reqs = nullptr;
+    mapa_result *stage_out = nullptr;
+    int32_t stage_cap = 0;
+    int32_t *order = nullptr;
+    int32_t order_cap = 0;
+    int32_t *hist = nullptr;
+    int32_t hist_cap = 0;
+    int32_t *overflow = nullptr;  // one flag per request group of a batch
+    int32_t overflow_cap = 0;
+    int32_t *d_error = nullptr;
+    unsigned long long *d_stats = nullptr;  // kStatWords counters of the current batch
+    unsigned long long *h_pinned = nullptr;  // small pinned scratch
+    mapa_stats st{};
+    bool timing = false;
+    int tail_override = 0;  // 0 = automatic tail depth
+    int tail_blocks_per_sm = 0;  // 0 = from the occupancy calculator
+    std::vector<cudaEvent_t> events;  // pairs around fused last-level launches
+    size_t events_used = 0;
+
+    cudaEvent_t next_event() {
+        if (events_used == events.size()) {
+            cudaEvent_t ev;
+            cudaEventCreate(&ev);
+            events.push_back(ev);
+        }
+        return events[events_used++];
+    }
+};
+
+int ensure_device(char **ptr, uint64_t *have, uint64_t need, std::string *err);
+
+inline uint64_t ceil_div(uint64_t a, uint64_t b) { return (a + b - 1) / b; }
+inline uint64_t align_up(uint64_t a, uint64_t b) { return (a + b - 1) / b * b; }
+inline uint64_t entry_bytes(int ell, int W) { return 4ull * (2 + W + ((ell + 3) / 4)); }
+
+// One request group (all requests of one pattern in a batch slice).
+struct GroupRun {
+    const PatternArgs *pat;
+    GroupArgs g;
+    int tail;           // fused tail depth T
+    int32_t *overflow;  // device flag for this group (device-driven path)
+};
+
+// Per-mask-width entry points (mapa_engine_w{1,2,4,8}.cu).
+//   run_group_device_*: enqueue the whole group without host synchronisation;
+//   run_group_host_*:   host-driven, chunked so any frontier fits.
+#define MAPA_DECLARE_W(W)                                                                                  \
+    int run_group_device_w##W(Engine *e, const TopoDevice &t, const GroupRun &gr, std::string *err);      \
+    int run_group_host_w##W(Engine *e, const TopoDevice &t, const GroupRun &gr, std::string *err);
+MAPA_DECLARE_W(1)
+MAPA_DECLARE_W(2)
+MAPA_DECLARE_W(4)
+MAPA_DECLARE_W(8)
+#undef MAPA_DECLARE_W
+
+}  // namespace mapa

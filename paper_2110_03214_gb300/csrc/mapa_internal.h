@@ -83,9 +83,10 @@ enum DeviceError : int32_t {
     kDevOk = 0,
     kDevScoreMismatch = 1,  // finalize found a score that disagrees with its tuple
     kDevResolveMiss = 2,    // resolve could not re-find the argmax tail
+    kDevLookbackTimeout = 3,  // a bounded look-back wait gave up
 };
 
-struct Engine;  // device buffers + launch helpers (mapa_engine.cu)
+struct Engine;  // device buffers + launch helpers (mapa_engine.h)
 
 Engine *engine_create(int device, uint64_t frontier_cap, std::string *err);
 void engine_destroy(Engine *e);

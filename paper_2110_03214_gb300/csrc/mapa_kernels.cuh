@@ -1,0 +1,957 @@
+// Device kernels of the MAPA allocation hot path (sm_103a), templated on the
+// mask width W (32-bit words per vertex set), the number of weight classes CT
+// (1..3 specialised, 0 = any) and the fused tail depth T.
+//
+// What is computed (MAPA, arXiv 2110.03214, Sec. 3.3-3.6): for each request,
+// every match phi of the pattern P in the free part F of the hardware graph
+// (injective, adjacency-preserving, Sec. 3.3), its int32 score
+//     S = alpha * AggBW(phi) + beta * PreservedBW(phi)          (Eq. 1, Eq. 3)
+// and the argmax with the lexicographically smallest tuple among equal scores
+// (Algorithm 1's strict ">" scan over a lexicographic enumeration).
+//
+// How (our design; the paper has no GPU kernel):
+//   * Matches grow one pattern vertex per level in pattern-id order.  A
+//     partial match at level l stores, in structure-of-arrays columns, its
+//     running score S, its request r, R = F minus the vertices used so far,
+//     and its tuple bytes.  Order constraints phi(j) < phi(i) for j in lo[i]
+//     keep one map per automorphism class; chosen in increasing id order they
+//     keep the lexicographically smallest map of each class, so the argmax
+//     tuple is the one a plain lexicographic scan over all maps would choose.
+//   * Candidates: R & (AND over earlier neighbours b of adj[phi b]) & (vertices
+//     above max over lo of phi), on bitsets staged in shared memory.
+//   * Score increment of adding v (B = images of v's earlier neighbours,
+//     R = still-free vertices), summed over weight classes c:
+//         dS = sum_c w_c * (alpha * popc(B & cls_c[v]) - beta * popc(R & cls_c[v]))
+//     The first term is v's share of Eq. 1, the second the links from v to
+//     free vertices that Eq. 3 loses; a request's root starts at beta * W(F).
+//   * Non-final levels are written to HBM by k_expand, a single-pass kernel:
+//     each 256-parent tile counts its children, learns its output offset by
+//     a decoupled look-back over earlier tiles (tiles are handed out in
+//     increasing order, so a tile only waits on tiles already running), and
+//     writes its children warp-cooperatively (lane c emits child c of the
+//     warp, so consecutive lanes store consecutive entries of every column).
+//     Levels therefore stay in lexicographic order.
+//   * The last T levels are fused in k_last: no frontier write; each thread
+//     walks its parent's subtree in registers, keeps the best score, and a
+//     warp-then-block reduction feeds one 64-bit atomicMax per request of
+//     key = (biased S << 32) | ~parent.  Lexicographic order of parents makes
+//     the smallest parent index the lexicographic tie-break; k_resolve re-walks
+//     the winning parent's subtree to recover the tail.
+//   * Every wait (the look-back) is bounded: after kSpinLimit polls the kernel
+//     records an error word and stops writing, so a fault can never hang.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <climits>
+#include <cstdint>
+
+#include "mapa_internal.h"
+
+namespace mapa {
+
+constexpr unsigned kFull = 0xFFFFFFFFu;
+constexpr uint32_t kNoReq = 0xFFFFFFFFu;
+constexpr unsigned long long kFlagAgg = 1ull << 62;
+constexpr unsigned long long kFlagPrefix = 2ull << 62;
+constexpr unsigned long long kValueMask = (1ull << 62) - 1;
+constexpr unsigned kSpinLimit = 1u << 24;
+
+// Device stats slots (summed over a batch, read once at its end).
+enum StatSlot { kStatNodes = 0, kStatLeaves, kStatParents, kStatOps, kStatSpill, kStatSpillBytes, kStatSlots };
+
+// ----------------------------------------------------------------------------
+// Mask helpers
+
+__device__ __forceinline__ uint32_t biased(int32_t s) { return static_cast<uint32_t>(s) ^ 0x80000000u; }
+__device__ __forceinline__ int32_t unbiased(uint32_t b) { return static_cast<int32_t>(b ^ 0x80000000u); }
+
+__host__ __device__ __forceinline__ uint32_t valid_word(int n, int w) {
+    const int lo = 32 * w;
+    if (n >= lo + 32) return ~0u;
+    if (n <= lo) return 0u;
+    return (1u << (n - lo)) - 1u;
+}
+
+template <int W>
+__device__ __forceinline__ void set_bit(uint32_t (&m)[W], int v) {
+#pragma unroll
+    for (int w = 0; w < W; ++w) m[w] |= ((v >> 5) == w) ? (1u << (v & 31)) : 0u;
+}
+
+template <int W>
+__device__ __forceinline__ void clear_bit(uint32_t (&m)[W], int v) {
+#pragma unroll
+    for (int w = 0; w < W; ++w) m[w] &= ((v >> 5) == w) ? ~(1u << (v & 31)) : ~0u;
+}
+
+template <int W>
+__device__ __forceinline__ int popc_mask(const uint32_t (&m)[W]) {
+    int c = 0;
+#pragma unroll
+    for (int w = 0; w < W; ++w) c += __popc(m[w]);
+    return c;
+}
+
+// Keeps only vertices > lb (lb = -1 keeps all).
+template <int W>
+__device__ __forceinline__ void and_above(uint32_t (&c)[W], int lb) {
+#pragma unroll
+    for (int w = 0; w < W; ++w) {
+        const int base = 32 * w;
+        uint32_t m;
+        if (lb < base)
+            m = ~0u;
+        else if (lb >= base + 31)
+            m = 0u;
+        else
+            m = ~0u << (lb - base + 1);
+        c[w] &= m;
+    }
+}
+
+// Removes and returns the lowest set vertex of a W-word mask (-1 if empty).
+template <int W>
+__device__ __forceinline__ int pop_lowest(uint32_t (&m)[W]) {
+    int v = -1;
+#pragma unroll
+    for (int w = 0; w < W; ++w) {
+        if (v < 0 && m[w] != 0u) {
+            v = 32 * w + __ffs(m[w]) - 1;
+            m[w] &= m[w] - 1u;
+        }
+    }
+    return v;
+}
+
+// Position of the rank-th (0-based) set bit of x (x has more than rank bits set).
+__device__ __forceinline__ int nth_bit32(uint32_t x, int rank) {
+    int pos = 0;
+    int c = __popc(x & 0xFFFFu);
+    if (rank >= c) { rank -= c; x >>= 16; pos += 16; }
+    c = __popc(x & 0xFFu);
+    if (rank >= c) { rank -= c; x >>= 8; pos += 8; }
+    c = __popc(x & 0xFu);
+    if (rank >= c) { rank -= c; x >>= 4; pos += 4; }
+    c = __popc(x & 0x3u);
+    if (rank >= c) { rank -= c; x >>= 2; pos += 2; }
+    if (rank >= static_cast<int>(x & 1u)) pos += 1;
+    return pos;
+}
+
+template <int W>
+__device__ __forceinline__ int nth_bit(const uint32_t (&m)[W], int rank) {
+    int v = 0;
+    bool done = false;
+#pragma unroll
+    for (int w = 0; w < W; ++w) {
+        const int c = __popc(m[w]);
+        if (!done) {
+            if (rank < c) {
+                v = 32 * w + nth_bit32(m[w], rank);
+                done = true;
+            } else {
+                rank -= c;
+            }
+        }
+    }
+    return v;
+}
+
+__device__ __forceinline__ int warp_sum_int(int v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
+    return v;
+}
+
+__device__ __forceinline__ unsigned long long warp_sum_u64(unsigned long long v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
+    return v;
+}
+
+__device__ __forceinline__ int warp_incl_scan(int v, int lane) {
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int t = __shfl_up_sync(kFull, v, o);
+        if (lane >= o) v += t;
+    }
+    return v;
+}
+
+// ----------------------------------------------------------------------------
+// Topology in shared memory
+
+struct SmemTopo {
+    const uint32_t *adj;
+    const uint32_t *cls;
+    const int32_t *wc;
+    int n, C;
+};
+
+__host__ __device__ inline size_t topo_smem_bytes(int n, int W, int C, bool with_cls) {
+    size_t words = static_cast<size_t>(n) * W;
+    if (with_cls) words += static_cast<size_t>(n) * C * W + C;
+    return words * 4;
+}
+
+template <int W>
+__device__ __forceinline__ SmemTopo stage_topology(const TopoArgs &t, bool with_cls) {
+    extern __shared__ uint32_t smem_words[];
+    uint32_t *adj = smem_words;
+    uint32_t *cls = adj + t.n * W;
+    int32_t *wc = reinterpret_cast<int32_t *>(cls + (with_cls ? t.n * t.C * W : 0));
+    for (int i = threadIdx.x; i < t.n * W; i += blockDim.x) adj[i] = t.adj[i];
+    if (with_cls) {
+        for (int i = threadIdx.x; i < t.n * t.C * W; i += blockDim.x) cls[i] = t.clsv[i];
+        for (int i = threadIdx.x; i < t.C; i += blockDim.x) wc[i] = t.wc[i];
+    }
+    __syncthreads();
+    return SmemTopo{adj, cls, wc, t.n, t.C};
+}
+
+__device__ __forceinline__ int tuple_byte(const LevelView &L, uint64_t p, int j) {
+    return static_cast<int>((L.T[static_cast<uint64_t>(j >> 2) * L.cap + p] >> ((j & 3) * 8)) & 0xFFu);
+}
+
+// Intersection of the adjacency rows of placed back-neighbours (A), the set of
+// their images (B) and the lower bound from the order constraints (lb).
+template <int W>
+__device__ __forceinline__ void level_masks(const LevelView &L, uint64_t p, uint32_t back, uint32_t lo,
+                                            const uint32_t *s_adj, uint32_t (&A)[W], uint32_t (&B)[W], int &lb) {
+#pragma unroll
+    for (int w = 0; w < W; ++w) {
+        A[w] = ~0u;
+        B[w] = 0u;
+    }
+    lb = -1;
+    while (back) {
+        const int b = __ffs(back) - 1;
+        back &= back - 1u;
+        const int x = tuple_byte(L, p, b);
+#pragma unroll
+        for (int w = 0; w < W; ++w) A[w] &= s_adj[x * W + w];
+        set_bit<W>(B, x);
+    }
+    while (lo) {
+        const int a = __ffs(lo) - 1;
+        lo &= lo - 1u;
+        lb = max(lb, tuple_byte(L, p, a));
+    }
+}
+
+// Score increments (see the file header).  CT > 0: the class count is known at
+// compile time and alpha*w_c, beta*w_c live in registers.
+template <int W, int CT>
+struct Scorer {
+    const uint32_t *cls;
+    const int32_t *wc;
+    int C;
+    int32_t al, be;
+    int32_t aw[CT > 0 ? CT : 1];
+    int32_t bw[CT > 0 ? CT : 1];
+
+    __device__ __forceinline__ Scorer(const SmemTopo &s, int32_t al_, int32_t be_)
+        : cls(s.cls), wc(s.wc), C(CT > 0 ? CT : s.C), al(al_), be(be_) {
+        if constexpr (CT > 0) {
+#pragma unroll
+            for (int c = 0; c < CT; ++c) {
+                aw[c] = al_ * s.wc[c];
+                bw[c] = be_ * s.wc[c];
+            }
+        }
+    }
+
+    __device__ __forceinline__ int32_t delta(int v, const uint32_t (&B)[W], const uint32_t (&R)[W]) const {
+        int32_t acc = 0;
+        if constexpr (CT > 0) {
+            const uint32_t *x = cls + v * (CT * W);
+#pragma unroll
+            for (int c = 0; c < CT; ++c) {
+                int pb = 0, pr = 0;
+#pragma unroll
+                for (int w = 0; w < W; ++w) {
+                    const uint32_t xw = x[c * W + w];
+                    pb += __popc(B[w] & xw);
+                    pr += __popc(R[w] & xw);
+                }
+                acc += aw[c] * pb - bw[c] * pr;
+            }
+        } else {
+            const uint32_t *x = cls + static_cast<size_t>(v) * C * W;
+            for (int c = 0; c < C; ++c) {
+                int pb = 0, pr = 0;
+#pragma unroll
+                for (int w = 0; w < W; ++w) {
+                    const uint32_t xw = x[c * W + w];
+                    pb += __popc(B[w] & xw);
+                    pr += __popc(R[w] & xw);
+                }
+                acc += wc[c] * (al * pb - be * pr);
+            }
+        }
+        return acc;
+    }
+};
+
+// ----------------------------------------------------------------------------
+// Fused tail: the last T pattern vertices ell .. ell+T-1 of a stored parent.
+
+struct TailArgs {
+    int32_t ell;              // level of the stored parents (= k - T)
+    uint32_t back_old[3];     // earlier neighbours among stored vertices (< ell), per tail level
+    uint32_t lo_old[3];       // order constraints from stored vertices, per tail level
+    uint32_t back_tail[3];    // bit j: tail vertex ell+j is an earlier neighbour
+    uint32_t lo_tail[3];      // bit j: constraint phi(ell+j) < phi(this)
+    uint64_t cost_parent;     // algorithmic integer ops per parent, tail node, leaf (telemetry)
+    uint64_t cost_node;
+    uint64_t cost_leaf;
+};
+
+template <int W, int T>
+struct TailPre {
+    uint32_t A[T][W];
+    uint32_t B[T][W];
+    int lb[T];
+};
+
+template <int W, int T>
+__device__ __forceinline__ void tail_precompute(const LevelView &in, uint64_t p, const TailArgs &ta,
+                                                const uint32_t *s_adj, TailPre<W, T> &pre) {
+#pragma unroll
+    for (int t = 0; t < T; ++t) level_masks<W>(in, p, ta.back_old[t], ta.lo_old[t], s_adj, pre.A[t], pre.B[t], pre.lb[t]);
+}
+
+// Walks tail level t (pattern vertex ell + t) below the tail prefix tv[0..t-1].
+// Leaf provides add(count) for every level-(T-1) candidate set and
+// visit(score, tv, v) for every complete match (return false to stop).
+template <int W, int CT, int T, int t, typename Leaf>
+__device__ __forceinline__ bool tail_walk(const SmemTopo &s, const Scorer<W, CT> &sc, const TailArgs &ta,
+                                          const TailPre<W, T> &pre, const uint32_t (&R)[W], int32_t S, int (&tv)[T],
+                                          Leaf &leaf, uint32_t &nodes) {
+    uint32_t c[W], B[W];
+#pragma unroll
+    for (int w = 0; w < W; ++w) {
+        c[w] = R[w] & pre.A[t][w];
+        B[w] = pre.B[t][w];
+    }
+    int lb = pre.lb[t];
+#pragma unroll
+    for (int j = 0; j < t; ++j) {
+        if ((ta.back_tail[t] >> j) & 1u) {
+#pragma unroll
+            for (int w = 0; w < W; ++w) c[w] &= s.adj[tv[j] * W + w];
+            set_bit<W>(B, tv[j]);
+        }
+        if ((ta.lo_tail[t] >> j) & 1u) lb = max(lb, tv[j]);
+    }
+    and_above<W>(c, lb);
+    if constexpr (t == T - 1) {
+        leaf.add(popc_mask<W>(c));
+        int v;
+        while ((v = pop_lowest<W>(c)) >= 0) {
+            if (!leaf.visit(S + sc.delta(v, B, R), tv, v)) return false;
+        }
+    } else {
+        int v;
+        while ((v = pop_lowest<W>(c)) >= 0) {
+            ++nodes;
+            const int32_t s1 = S + sc.delta(v, B, R);
+            uint32_t R1[W];
+#pragma unroll
+            for (int w = 0; w < W; ++w) R1[w] = R[w];
+            clear_bit<W>(R1, v);
+            tv[t] = v;
+            if (!tail_walk<W, CT, T, t + 1>(s, sc, ta, pre, R1, s1, tv, leaf, nodes)) return false;
+        }
+    }
+    return true;
+}
+
+// ----------------------------------------------------------------------------
+// Kernels
+
+// Per request: free set F, root entry (S = beta * W(F), R = F), accumulators.
+template <int W>
+__global__ void k_setup(TopoArgs topo, GroupArgs g, LevelView L0, unsigned long long *count0) {
+    const SmemTopo s = stage_topology<W>(topo, true);
+    const int lane = threadIdx.x & 31;
+    const int gw = static_cast<int>((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+    const int nw = static_cast<int>((gridDim.x * blockDim.x) >> 5);
+    if (count0 && blockIdx.x == 0 && threadIdx.x == 0) *count0 = static_cast<unsigned long long>(g.size);
+    for (int i = gw; i < g.size; i += nw) {
+        const mapa_request &q = g.reqs[g.req_index[i]];
+        uint32_t F[W];
+#pragma unroll
+        for (int w = 0; w < W; ++w) {
+            uint32_t busy = q.busy[w];
+            if (g.occupancy) busy |= g.occupancy[w];
+            F[w] = ~busy & valid_word(s.n, w);
+        }
+        long long acc = 0;
+        for (int v = lane; v < s.n; v += 32) {
+            if (!((F[v >> 5] >> (v & 31)) & 1u)) continue;
+            const uint32_t *x = s.cls + static_cast<size_t>(v) * s.C * W;
+            for (int c = 0; c < s.C; ++c) {
+                int pc = 0;
+#pragma unroll
+                for (int w = 0; w < W; ++w) pc += __popc(x[c * W + w] & F[w]);
+                acc += static_cast<long long>(s.wc[c]) * pc;
+            }
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(kFull, acc, o);
+        if (lane == 0) {
+            const int32_t al = q.policy.alpha, be = q.policy.beta;
+            const long long mag = (llabs(static_cast<long long>(al)) + llabs(static_cast<long long>(be))) *
+                                  static_cast<long long>(g.total_weight);
+            int32_t state = 0;
+            if (q.policy.mode != MAPA_MODE_EXHAUSTIVE)
+                state = -3;
+            else if (mag >= (1LL << 31))
+                state = -2;
+            const long long wfree = acc / 2;
+            L0.S[i] = state == 0 ? static_cast<int32_t>(be * wfree) : 0;
+            L0.r[i] = static_cast<uint32_t>(i);
+#pragma unroll
+            for (int w = 0; w < W; ++w) L0.R[w * L0.cap + i] = state == 0 ? F[w] : 0u;
+            g.alpha[i] = al;
+            g.beta[i] = be;
+            g.key[i] = 0ull;
+            g.count[i] = 0ull;
+            g.best_valid[i] = state;
+        }
+    }
+}
+
+// Count pass of the host-driven (chunked) path: children per warp and block.
+template <int W>
+__global__ void __launch_bounds__(kTpb) k_count(TopoArgs topo, LevelView in, uint64_t P, uint32_t back, uint32_t lo,
+                                                uint32_t *warp_cnt, unsigned long long *blk_cnt) {
+    const SmemTopo s = stage_topology<W>(topo, false);
+    __shared__ uint32_t s_w[kWarps];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const uint64_t wbase = static_cast<uint64_t>(blockIdx.x) * kTile + static_cast<uint64_t>(warp) * 32 * kIpt;
+    int wsum = 0;
+#pragma unroll
+    for (int j = 0; j < kIpt; ++j) {
+        const uint64_t p = wbase + j * 32 + lane;
+        int cnt = 0;
+        if (p < P) {
+            uint32_t A[W], B[W], c[W];
+            int lb;
+            level_masks<W>(in, p, back, lo, s.adj, A, B, lb);
+#pragma unroll
+            for (int w = 0; w < W; ++w) c[w] = in.R[w * in.cap + p] & A[w];
+            and_above<W>(c, lb);
+            cnt = popc_mask<W>(c);
+        }
+        wsum += warp_sum_int(cnt);
+    }
+    if (lane == 0) {
+        warp_cnt[static_cast<uint64_t>(blockIdx.x) * kWarps + warp] = static_cast<uint32_t>(wsum);
+        s_w[warp] = static_cast<uint32_t>(wsum);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        unsigned long long t = 0;
+        for (int w = 0; w < kWarps; ++w) t += s_w[w];
+        blk_cnt[blockIdx.x] = t;
+    }
+}
+
+// Emits the children of one group of 32 parents (one per lane) at
+// out[obase + c], c = 0 .. total-1, lane c taking child c of each round.
+template <int W, int CT>
+__device__ __forceinline__ void emit_children(const SmemTopo &s, const LevelView &in, const LevelView &out, int ell,
+                                              uint64_t p_first, int lane, const uint32_t (&cand)[W],
+                                              const uint32_t (&B)[W], const uint32_t (&R)[W], int32_t S, uint32_t r,
+                                              int cnt, int incl, int total, uint64_t obase, const int32_t *alpha,
+                                              const int32_t *beta) {
+    const int nw_in = (ell + 3) >> 2;
+    const int new_word = ell >> 2;
+    const uint32_t new_shift = (ell & 3) * 8;
+    for (int c0 = 0; c0 < total; c0 += 32) {
+        const int c = c0 + lane;
+        int src = 0;
+#pragma unroll
+        for (int step = 16; step >= 1; step >>= 1) {
+            const int t = __shfl_sync(kFull, incl, src + step - 1);
+            if (t <= c) src += step;
+        }
+        const int incl_s = __shfl_sync(kFull, incl, src);
+        const int cnt_s = __shfl_sync(kFull, cnt, src);
+        uint32_t cs[W], Bs[W], Rs[W];
+#pragma unroll
+        for (int w = 0; w < W; ++w) {
+            cs[w] = __shfl_sync(kFull, cand[w], src);
+            Bs[w] = __shfl_sync(kFull, B[w], src);
+            Rs[w] = __shfl_sync(kFull, R[w], src);
+        }
+        const int32_t Ss = __shfl_sync(kFull, S, src);
+        const uint32_t rs = __shfl_sync(kFull, r, src);
+        if (c < total) {
+            const int v = nth_bit<W>(cs, c - (incl_s - cnt_s));
+            const Scorer<W, CT> sc(s, alpha[rs], beta[rs]);
+            const int32_t d = sc.delta(v, Bs, Rs);
+            const uint64_t o = obase + c;
+            const uint64_t ps = p_first + src;
+            out.S[o] = Ss + d;
+            out.r[o] = rs;
+            clear_bit<W>(Rs, v);
+#pragma unroll
+            for (int w = 0; w < W; ++w) out.R[w * out.cap + o] = Rs[w];
+            for (int jw = 0; jw < nw_in; ++jw) {
+                uint32_t word = in.T[jw * in.cap + ps];
+                if (jw == new_word) word |= static_cast<uint32_t>(v) << new_shift;
+                out.T[jw * out.cap + o] = word;
+            }
+            if (new_shift == 0) out.T[new_word * out.cap + o] = static_cast<uint32_t>(v);
+        }
+    }
+}
+
+template <int W>
+__device__ __forceinline__ void parent_state(const SmemTopo &s, const LevelView &in, uint64_t p, uint32_t back,
+                                             uint32_t lo, uint32_t (&cand)[W], uint32_t (&B)[W], uint32_t (&R)[W],
+                                             int32_t &S, uint32_t &r) {
+    uint32_t A[W];
+    int lb;
+    level_masks<W>(in, p, back, lo, s.adj, A, B, lb);
+#pragma unroll
+    for (int w = 0; w < W; ++w) {
+        R[w] = in.R[w * in.cap + p];
+        cand[w] = R[w] & A[w];
+    }
+    and_above<W>(cand, lb);
+    S = in.S[p];
+    r = in.r[p];
+}
+
+// Write pass of the host-driven (chunked) path.
+template <int W, int CT>
+__global__ void __launch_bounds__(kTpb) k_write(TopoArgs topo, LevelView in, uint64_t P, int ell, uint32_t back,
+                                                uint32_t lo, LevelView out, const uint32_t *warp_cnt,
+                                                const unsigned long long *blk_off, uint64_t blk_first,
+                                                const int32_t *alpha, const int32_t *beta) {
+    const SmemTopo s = stage_topology<W>(topo, true);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const uint64_t b = blk_first + blockIdx.x;
+    uint64_t obase = blk_off[b] - blk_off[blk_first];
+    for (int w2 = 0; w2 < warp; ++w2) obase += warp_cnt[b * kWarps + w2];
+    const uint64_t wbase = b * kTile + static_cast<uint64_t>(warp) * 32 * kIpt;
+    for (int j = 0; j < kIpt; ++j) {
+        const uint64_t p = wbase + j * 32 + lane;
+        uint32_t cand[W], B[W], R[W];
+        int32_t S = 0;
+        uint32_t r = 0;
+#pragma unroll
+        for (int w = 0; w < W; ++w) cand[w] = B[w] = R[w] = 0u;
+        if (p < P) parent_state<W>(s, in, p, back, lo, cand, B, R, S, r);
+        const int cnt = popc_mask<W>(cand);
+        const int incl = warp_incl_scan(cnt, lane);
+        const int total = __shfl_sync(kFull, incl, 31);
+        emit_children<W, CT>(s, in, out, ell, wbase + j * 32, lane, cand, B, R, S, r, cnt, incl, total, obase, alpha,
+                             beta);
+        obase += total;
+    }
+}
+
+// Decoupled look-back (warp 0 of a block): publishes this tile's total and
+// returns the sum of all earlier tiles' totals.  Bounded: after kSpinLimit
+// polls of a predecessor it records an error and returns a value past any
+// capacity so the tile writes nothing.
+__device__ __forceinline__ unsigned long long look_back(unsigned long long *status, unsigned long long t,
+                                                        unsigned long long total, int lane, int32_t *err) {
+    if (t == 0) {
+        if (lane == 0) atomicExch(status, kFlagPrefix | total);
+        return 0ull;
+    }
+    if (lane == 0) atomicExch(status + t, kFlagAgg | total);
+    unsigned long long excl = 0ull;
+    long long pred = static_cast<long long>(t) - 1;
+    bool failed = false;
+    for (;;) {
+        const long long idx = pred - lane;
+        unsigned long long word = 0ull;
+        if (idx >= 0) {
+            unsigned spins = 0;
+            word = *reinterpret_cast<volatile unsigned long long *>(status + idx);
+            while ((word >> 62) == 0ull && spins < kSpinLimit) {
+                if (spins > 32) __nanosleep(64);
+                ++spins;
+                word = *reinterpret_cast<volatile unsigned long long *>(status + idx);
+            }
+            if ((word >> 62) == 0ull) failed = true;
+        }
+        const unsigned prefix = __ballot_sync(kFull, idx >= 0 && (word & kFlagPrefix));
+        const int stop = prefix ? __ffs(prefix) - 1 : 31;
+        const unsigned long long v = (idx >= 0 && lane <= stop) ? (word & kValueMask) : 0ull;
+        excl += warp_sum_u64(v);
+        if (__any_sync(kFull, failed)) {
+            if (lane == 0) atomicExch(err, kDevLookbackTimeout);
+            return kValueMask;
+        }
+        if (prefix || pred < 32) break;
+        pred -= 32;
+    }
+    if (lane == 0) atomicExch(status + t, kFlagPrefix | (excl + total));
+    return excl;
+}
+
+// Single-pass level expansion of the device-driven path: parents are read
+// from `in` (count at *count_in), children go to `out` (capacity cap_out),
+// the child count to *count_out.  If the children do not fit, nothing past
+// the capacity is written, *count_out = 0 and *overflow = 1 (the host then
+// redoes the group with the chunked path).
+template <int W, int CT>
+__global__ void __launch_bounds__(kTpb) k_expand(TopoArgs topo, LevelView in, LevelView out, int ell, uint32_t back,
+                                                 uint32_t lo, const unsigned long long *count_in,
+                                                 unsigned long long *count_out, unsigned long long cap_out,
+                                                 unsigned int *tile_ctr, unsigned long long *status, int32_t *overflow,
+                                                 const int32_t *alpha, const int32_t *beta, int32_t *err,
+                                                 unsigned long long *stats, unsigned long long child_bytes) {
+    const SmemTopo s = stage_topology<W>(topo, true);
+    __shared__ unsigned int s_tile;
+    __shared__ int s_wtot[kWarps];
+    __shared__ unsigned long long s_excl;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const unsigned long long P = *count_in;
+    const unsigned long long ntiles = (P + kTpb - 1) / kTpb;
+    if (ntiles == 0) {
+        if (blockIdx.x == 0 && threadIdx.x == 0) *count_out = 0ull;
+        return;
+    }
+    for (;;) {
+        if (threadIdx.x == 0) s_tile = atomicAdd(tile_ctr, 1u);
+        __syncthreads();
+        const unsigned long long t = s_tile;
+        if (t >= ntiles) break;
+        const uint64_t p = t * kTpb + threadIdx.x;
+        uint32_t cand[W], B[W], R[W];
+        int32_t S = 0;
+        uint32_t r = 0;
+#pragma unroll
+        for (int w = 0; w < W; ++w) cand[w] = B[w] = R[w] = 0u;
+        if (p < P) parent_state<W>(s, in, p, back, lo, cand, B, R, S, r);
+        const int cnt = popc_mask<W>(cand);
+        const int incl = warp_incl_scan(cnt, lane);
+        const int wtot = __shfl_sync(kFull, incl, 31);
+        if (lane == 0) s_wtot[warp] = wtot;
+        __syncthreads();
+        int woff = 0, ttot = 0;
+#pragma unroll
+        for (int w2 = 0; w2 < kWarps; ++w2) {
+            const int v = s_wtot[w2];
+            woff += w2 < warp ? v : 0;
+            ttot += v;
+        }
+        if (warp == 0) {
+            const unsigned long long ex = look_back(status, t, static_cast<unsigned long long>(ttot), lane, err);
+            if (lane == 0) s_excl = ex;
+        }
+        __syncthreads();
+        const unsigned long long excl = s_excl;
+        const bool fits = excl + static_cast<unsigned long long>(ttot) <= cap_out;
+        if (threadIdx.x == 0) {
+            if (!fits) atomicExch(overflow, 1);
+            if (t == ntiles - 1) {
+                const unsigned long long total = excl + static_cast<unsigned long long>(ttot);
+                *count_out = fits ? total : 0ull;
+                if (fits && stats) {
+                    atomicAdd(stats + kStatSpill, total);
+                    atomicAdd(stats + kStatSpillBytes, 2ull * total * child_bytes);
+                }
+            }
+        }
+        if (fits)
+            emit_children<W, CT>(s, in, out, ell, t * kTpb + static_cast<uint64_t>(warp) * 32, lane, cand, B, R, S, r,
+                                 cnt, incl, wtot, excl + woff, alpha, beta);
+        __syncthreads();
+    }
+}
+
+__device__ __forceinline__ void flush_request(uint64_t *key, unsigned long long *count, uint32_t r, uint64_t k,
+                                              unsigned long long c) {
+    if (c == 0ull) return;
+    atomicMax(reinterpret_cast<unsigned long long *>(key + r), static_cast<unsigned long long>(k));
+    atomicAdd(count + r, c);
+}
+
+struct MaxLeaf {
+    int32_t smax = INT_MIN;
+    uint32_t leaves = 0;
+    __device__ __forceinline__ void add(int n) { leaves += static_cast<uint32_t>(n); }
+    template <int T>
+    __device__ __forceinline__ bool visit(int32_t sc, const int (&)[T], int) {
+        smax = max(smax, sc);
+        return true;
+    }
+};
+
+// Fused last T levels: count and argmax key per request, no frontier write.
+// Parents are handed out in tiles of kTile through *tile_ctr (dynamic load
+// balance); P is *count_in (device-driven) or count_host (host-driven).
+template <int W, int CT, int T>
+__global__ void __launch_bounds__(kTpb) k_last(TopoArgs topo, LevelView in, const unsigned long long *count_in,
+                                               unsigned long long count_host, TailArgs ta, const int32_t *alpha,
+                                               const int32_t *beta, uint64_t *key, unsigned long long *count,
+                                               unsigned int *tile_ctr, unsigned long long *stats) {
+    const SmemTopo s = stage_topology<W>(topo, true);
+    __shared__ uint32_t s_r[kWarps];
+    __shared__ unsigned long long s_key[kWarps];
+    __shared__ unsigned long long s_cnt[kWarps];
+    __shared__ unsigned long long s_nodes, s_leaves, s_parents;
+    __shared__ unsigned int s_tile;
+    if (threadIdx.x == 0) {
+        s_nodes = 0ull;
+        s_leaves = 0ull;
+        s_parents = 0ull;
+    }
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const unsigned long long P = count_in ? *count_in : count_host;
+    const unsigned long long ntiles = (P + kTile - 1) / kTile;
+    uint32_t r_cur = kNoReq;
+    unsigned long long bkey = 0ull, bcnt = 0ull, parents = 0ull, leaves_total = 0ull;
+    uint32_t nodes = 0;
+    for (;;) {
+        if (threadIdx.x == 0) s_tile = atomicAdd(tile_ctr, 1u);
+        __syncthreads();
+        const unsigned long long tile = s_tile;
+        __syncthreads();
+        if (tile >= ntiles) break;
+        const uint64_t wbase = tile * kTile + static_cast<uint64_t>(warp) * 32 * kIpt;
+        for (int j = 0; j < kIpt; ++j) {
+            const uint64_t p = wbase + j * 32 + lane;
+            if (p >= P) continue;
+            ++parents;
+            const uint32_t r = in.r[p];
+            if (r != r_cur) {
+                if (r_cur != kNoReq) flush_request(key, count, r_cur, bkey, bcnt);
+                r_cur = r;
+                bkey = 0ull;
+                bcnt = 0ull;
+            }
+            TailPre<W, T> pre;
+            tail_precompute<W, T>(in, p, ta, s.adj, pre);
+            uint32_t R[W];
+#pragma unroll
+            for (int w = 0; w < W; ++w) R[w] = in.R[w * in.cap + p];
+            const Scorer<W, CT> sc(s, alpha[r], beta[r]);
+            MaxLeaf leaf;
+            int tv[T];
+            tail_walk<W, CT, T, 0>(s, sc, ta, pre, R, in.S[p], tv, leaf, nodes);
+            if (leaf.leaves) {
+                const unsigned long long k64 = (static_cast<unsigned long long>(biased(leaf.smax)) << 32) |
+                                               (0xFFFFFFFFu - static_cast<uint32_t>(p));
+                bkey = max(bkey, k64);
+                bcnt += leaf.leaves;
+                leaves_total += leaf.leaves;
+            }
+        }
+    }
+    // warp, then block aggregation of (request, key, count)
+    const unsigned long long wn = warp_sum_u64(nodes);
+    const unsigned long long wl = warp_sum_u64(leaves_total);
+    const unsigned long long wp = warp_sum_u64(parents);
+    if (lane == 0) {
+        s_r[warp] = kNoReq;
+        if (wn) atomicAdd(&s_nodes, wn);
+        if (wl) atomicAdd(&s_leaves, wl);
+        if (wp) atomicAdd(&s_parents, wp);
+    }
+    const unsigned act = __ballot_sync(kFull, bcnt > 0ull);
+    if (act) {
+        const int lead = __ffs(act) - 1;
+        const uint32_t rl = __shfl_sync(kFull, r_cur, lead);
+        const bool uniform = __all_sync(kFull, bcnt == 0ull || r_cur == rl);
+        if (uniform) {
+            unsigned long long k = bkey, c = bcnt;
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                k = max(k, __shfl_xor_sync(kFull, k, o));
+                c += __shfl_xor_sync(kFull, c, o);
+            }
+            if (lane == 0) {
+                s_r[warp] = rl;
+                s_key[warp] = k;
+                s_cnt[warp] = c;
+            }
+        } else if (bcnt) {
+            flush_request(key, count, r_cur, bkey, bcnt);
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        uint32_t r = kNoReq;
+        unsigned long long k = 0ull, c = 0ull;
+        for (int w = 0; w < kWarps; ++w) {
+            if (s_r[w] == kNoReq) continue;
+            if (s_r[w] != r) {
+                if (r != kNoReq) flush_request(key, count, r, k, c);
+                r = s_r[w];
+                k = 0ull;
+                c = 0ull;
+            }
+            k = max(k, s_key[w]);
+            c += s_cnt[w];
+        }
+        if (r != kNoReq) flush_request(key, count, r, k, c);
+        if (stats && (s_parents || s_nodes || s_leaves)) {
+            atomicAdd(stats + kStatNodes, s_nodes);
+            atomicAdd(stats + kStatLeaves, s_leaves);
+            atomicAdd(stats + kStatParents, s_parents);
+            atomicAdd(stats + kStatOps,
+                      ta.cost_parent * s_parents + ta.cost_node * s_nodes + ta.cost_leaf * s_leaves);
+        }
+    }
+}
+
+template <int T>
+struct FindLeaf {
+    int32_t target;
+    bool found = false;
+    int tail[T];
+    __device__ __forceinline__ void add(int) {}
+    __device__ __forceinline__ bool visit(int32_t sc, const int (&tv)[T], int v) {
+        if (sc != target) return true;
+        found = true;
+#pragma unroll
+        for (int j = 0; j + 1 < T; ++j) tail[j] = tv[j];
+        tail[T - 1] = v;
+        return false;
+    }
+};
+
+// Per request present in a last-level chunk: decode the chunk's argmax key,
+// re-walk the winning parent's tail in lexicographic order to recover the
+// first tail reaching that score, and merge into the running best with a
+// strict ">" (chunks arrive in lexicographic order).
+template <int W, int CT, int T>
+__global__ void k_resolve(TopoArgs topo, LevelView in, const unsigned long long *count_in,
+                          unsigned long long count_host, TailArgs ta, GroupArgs g) {
+    const SmemTopo s = stage_topology<W>(topo, true);
+    const unsigned long long P = count_in ? *count_in : count_host;
+    if (P == 0) return;
+    const uint32_t r_lo = in.r[0], r_hi = in.r[P - 1];
+    for (uint64_t rr = r_lo + static_cast<uint64_t>(blockIdx.x) * blockDim.x + threadIdx.x; rr <= r_hi;
+         rr += static_cast<uint64_t>(gridDim.x) * blockDim.x) {
+        const uint32_t r = static_cast<uint32_t>(rr);
+        const unsigned long long k64 = g.key[r];
+        if (k64 == 0ull) continue;
+        g.key[r] = 0ull;
+        const int32_t target = unbiased(static_cast<uint32_t>(k64 >> 32));
+        const uint64_t p = 0xFFFFFFFFu - static_cast<uint32_t>(k64 & 0xFFFFFFFFull);
+        TailPre<W, T> pre;
+        tail_precompute<W, T>(in, p, ta, s.adj, pre);
+        uint32_t R[W];
+#pragma unroll
+        for (int w = 0; w < W; ++w) R[w] = in.R[w * in.cap + p];
+        const Scorer<W, CT> sc(s, g.alpha[r], g.beta[r]);
+        FindLeaf<T> leaf;
+        leaf.target = target;
+        int tv[T];
+        uint32_t nodes = 0;
+        tail_walk<W, CT, T, 0>(s, sc, ta, pre, R, in.S[p], tv, leaf, nodes);
+        if (!leaf.found) {
+            atomicExch(g.error, kDevResolveMiss);
+            continue;
+        }
+        if (g.best_valid[r] == 0 || (g.best_valid[r] == 1 && target > g.best_s[r])) {
+            g.best_s[r] = target;
+            g.best_valid[r] = 1;
+            const int nw = (ta.ell + 3) >> 2;
+            uint32_t words[8];
+#pragma unroll
+            for (int jw = 0; jw < 8; ++jw) words[jw] = jw < nw ? in.T[jw * in.cap + p] : 0u;
+#pragma unroll
+            for (int j = 0; j < T; ++j) {
+                const int pos = ta.ell + j;
+#pragma unroll
+                for (int jw = 0; jw < 8; ++jw)
+                    if (jw == (pos >> 2)) words[jw] |= static_cast<uint32_t>(leaf.tail[j]) << ((pos & 3) * 8);
+            }
+#pragma unroll
+            for (int jw = 0; jw < 8; ++jw) g.best_t[static_cast<uint64_t>(r) * 8 + jw] = words[jw];
+        }
+    }
+}
+
+__device__ __forceinline__ int32_t link_weight(const SmemTopo &s, int W, int x, int y) {
+    const uint32_t *row = s.cls + static_cast<size_t>(x) * s.C * W;
+    for (int c = 0; c < s.C; ++c)
+        if ((row[c * W + (y >> 5)] >> (y & 31)) & 1u) return s.wc[c];
+    return 0;
+}
+
+// Writes every request's result: the chosen tuple's AggBW (Eq. 1) and
+// PreservedBW (Eq. 3) recomputed from their definitions on the bitsets and
+// checked against the enumerated score.
+template <int W>
+__global__ void k_finalize(TopoArgs topo, PatternArgs pat, GroupArgs g) {
+    const SmemTopo s = stage_topology<W>(topo, true);
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < g.size; i += gridDim.x * blockDim.x) {
+        const int32_t bi = g.req_index[i];
+        const mapa_request &q = g.reqs[bi];
+        mapa_result res;
+        memset(&res, 0, sizeof(res));
+        res.k = pat.k;
+        res.count = g.count[i];
+        const int32_t state = g.best_valid[i];
+        if (state == -2) {
+            res.status = MAPA_E_RANGE;
+            res.count = 0;
+        } else if (state == -3) {
+            res.status = MAPA_E_INVALID;
+            res.count = 0;
+        } else if (q.policy.max_embeddings > 0 && res.count > q.policy.max_embeddings) {
+            res.status = MAPA_E_BUDGET;
+        } else if (state != 1) {
+            res.status = MAPA_NO_FIT;
+        } else {
+            uint8_t t[kMaxK];
+            for (int j = 0; j < pat.k; ++j)
+                t[j] = static_cast<uint8_t>((g.best_t[static_cast<uint64_t>(i) * 8 + (j >> 2)] >> ((j & 3) * 8)) & 0xFFu);
+            long long agg = 0;
+            for (int v = 0; v < pat.k; ++v) {
+                uint32_t m = pat.back[v];
+                while (m) {
+                    const int a = __ffs(m) - 1;
+                    m &= m - 1u;
+                    agg += link_weight(s, W, t[a], t[v]);
+                }
+            }
+            uint32_t rem[W];
+#pragma unroll
+            for (int w = 0; w < W; ++w) {
+                uint32_t busy = q.busy[w];
+                if (g.occupancy) busy |= g.occupancy[w];
+                rem[w] = ~busy & valid_word(s.n, w);
+            }
+            for (int j = 0; j < pat.k; ++j) clear_bit<W>(rem, t[j]);
+            long long twice = 0;
+            for (int v = 0; v < s.n; ++v) {
+                if (!((rem[v >> 5] >> (v & 31)) & 1u)) continue;
+                const uint32_t *x = s.cls + static_cast<size_t>(v) * s.C * W;
+                for (int c = 0; c < s.C; ++c) {
+                    int pc = 0;
+#pragma unroll
+                    for (int w = 0; w < W; ++w) pc += __popc(x[c * W + w] & rem[w]);
+                    twice += static_cast<long long>(s.wc[c]) * pc;
+                }
+            }
+            const long long pres = twice / 2;
+            const long long score =
+                static_cast<long long>(g.alpha[i]) * agg + static_cast<long long>(g.beta[i]) * pres;
+            if (score != g.best_s[i]) atomicExch(g.error, kDevScoreMismatch);
+            res.status = MAPA_OK;
+            res.score = g.best_s[i];
+            res.agg = static_cast<int32_t>(agg);
+            res.pres = static_cast<int32_t>(pres);
+            for (int j = 0; j < pat.k; ++j) res.verts[j] = t[j];
+        }
+        g.out[bi] = res;
+    }
+}
+
+}  // namespace mapa

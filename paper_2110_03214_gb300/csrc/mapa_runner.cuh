@@ -1,0 +1,276 @@
+// Host drivers of one request group, templated on the mask width W, the
+// weight-class count CT and the fused tail depth T.  Included by the
+// per-width translation units mapa_engine_w*.cu.
+#pragma once
+
+#include <algorithm>
+#include <vector>
+
+#include "mapa_engine.h"
+#include "mapa_kernels.cuh"
+
+namespace mapa {
+
+// Frontier arena layout of one group run.
+struct LayoutPlan {
+    int L = 0;       // last stored level (= k - T)
+    uint64_t E = 0;  // capacity of levels 1..L
+    LevelView level[kMaxK + 1];
+    // host-driven path: per-level block counts and offsets
+    uint32_t *warp_cnt[kMaxK + 1];
+    unsigned long long *blk_cnt[kMaxK + 1];
+    unsigned long long *blk_off[kMaxK + 1];
+    // device-driven path: level counts, tile tickets, look-back status words
+    unsigned long long *counts = nullptr;   // [L + 1]
+    unsigned int *tiles = nullptr;          // [L + 1]
+    unsigned long long *status[kMaxK + 1];  // [cap_l / kTpb + 1] per level l < L
+    char *ctrl = nullptr;                   // contiguous control region (zeroed per run)
+    uint64_t ctrl_bytes = 0;
+};
+
+int plan_layout(Engine *e, int32_t group_size, int k, int T, int W, bool device_mode, int n, LayoutPlan *lay,
+                std::string *err);
+void launch_scan(const unsigned long long *cnt, unsigned long long *off, uint64_t nb, cudaStream_t s);
+
+inline TailArgs make_tail_args(const PatternArgs &pat, int T, int W, int C) {
+    TailArgs ta{};
+    ta.ell = pat.k - T;
+    const uint32_t old = ta.ell == 0 ? 0u : ((ta.ell >= 32) ? ~0u : ((1u << ta.ell) - 1u));
+    uint64_t backs = 0, los = 0;
+    for (int t = 0; t < T; ++t) {
+        const int v = ta.ell + t;
+        ta.back_old[t] = pat.back[v] & old;
+        ta.lo_old[t] = pat.lo[v] & old;
+        ta.back_tail[t] = (pat.back[v] >> ta.ell) & ((1u << t) - 1u);
+        ta.lo_tail[t] = (pat.lo[v] >> ta.ell) & ((1u << t) - 1u);
+        backs += __builtin_popcount(ta.back_old[t]);
+        los += __builtin_popcount(ta.lo_old[t]);
+    }
+    const uint64_t w = static_cast<uint64_t>(W), c = static_cast<uint64_t>(C);
+    ta.cost_parent = backs * (2 + 2 * w) + 3 * los + 3 * w + 1;
+    ta.cost_node = 4 * c * w + 3 * c + 6 * w + 2;
+    ta.cost_leaf = 4 * c * w + 3 * c + 2;
+    return ta;
+}
+
+template <typename K>
+inline int blocks_per_sm(K kernel, size_t smem) {
+    int nb = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kernel, kTpb, smem) != cudaSuccess || nb < 1) nb = 1;
+    return nb;
+}
+
+template <int W, int CT, int T>
+struct Runner {
+    Engine *e;
+    const TopoDevice &t;
+    const GroupRun &gr;
+    const PatternArgs &pat;
+    GroupArgs g;
+    LayoutPlan lay;
+    TailArgs ta;
+    size_t smem_adj, smem_all;
+    std::string *err;
+
+    Runner(Engine *e_, const TopoDevice &t_, const GroupRun &gr_, std::string *err_)
+        : e(e_), t(t_), gr(gr_), pat(*gr_.pat), g(gr_.g), err(err_) {
+        smem_adj = topo_smem_bytes(t.n, W, t.C, false);
+        smem_all = topo_smem_bytes(t.n, W, t.C, true);
+        ta = make_tail_args(pat, T, W, t.C);
+    }
+
+    int allow_smem() {
+        if (smem_all <= 48 * 1024) return MAPA_OK;
+        const int b = static_cast<int>(smem_all);
+        MAPA_CUDA_TRY(cudaFuncSetAttribute(k_setup<W>, cudaFuncAttributeMaxDynamicSharedMemorySize, b));
+        MAPA_CUDA_TRY(cudaFuncSetAttribute(k_write<W, CT>, cudaFuncAttributeMaxDynamicSharedMemorySize, b));
+        MAPA_CUDA_TRY(cudaFuncSetAttribute(k_expand<W, CT>, cudaFuncAttributeMaxDynamicSharedMemorySize, b));
+        MAPA_CUDA_TRY(cudaFuncSetAttribute(k_last<W, CT, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, b));
+        MAPA_CUDA_TRY(cudaFuncSetAttribute(k_resolve<W, CT, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, b));
+        MAPA_CUDA_TRY(cudaFuncSetAttribute(k_finalize<W>, cudaFuncAttributeMaxDynamicSharedMemorySize, b));
+        return MAPA_OK;
+    }
+
+    int setup(unsigned long long *count0) {
+        const unsigned sgrid = static_cast<unsigned>(std::min<uint64_t>(ceil_div(g.size, kWarps), 4096));
+        k_setup<W><<<sgrid, kTpb, smem_all, e->stream>>>(t.args(), g, lay.level[0], count0);
+        MAPA_CUDA_TRY(cudaGetLastError());
+        e->st.kernel_launches += 1;
+        return MAPA_OK;
+    }
+
+    int finalize() {
+        const unsigned fgrid = static_cast<unsigned>(std::min<uint64_t>(ceil_div(g.size, 128), 4096));
+        k_finalize<W><<<fgrid, 128, smem_all, e->stream>>>(t.args(), pat, g);
+        MAPA_CUDA_TRY(cudaGetLastError());
+        e->st.kernel_launches += 1;
+        e->st.requests += static_cast<uint64_t>(g.size);
+        return MAPA_OK;
+    }
+
+    // Fused last levels over the stored level L (count on the device or given).
+    int last_level(const unsigned long long *count_dev, unsigned long long count_host, unsigned int *tile_ctr,
+                   uint64_t max_parents) {
+        const LevelView &in = lay.level[lay.L];
+        static int nb_last = 0;
+        if (!nb_last) nb_last = blocks_per_sm(k_last<W, CT, T>, smem_all);
+        const int per_sm = e->tail_blocks_per_sm > 0 ? e->tail_blocks_per_sm : nb_last;
+        const unsigned grid = static_cast<unsigned>(
+            std::max<uint64_t>(1, std::min<uint64_t>(ceil_div(max_parents, kTile), uint64_t(e->sm_count) * per_sm)));
+        cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+        if (e->timing) {
+            ev0 = e->next_event();
+            ev1 = e->next_event();
+            MAPA_CUDA_TRY(cudaEventRecord(ev0, e->stream));
+        }
+        k_last<W, CT, T><<<grid, kTpb, smem_all, e->stream>>>(t.args(), in, count_dev, count_host, ta, g.alpha, g.beta,
+                                                               g.key, g.count, tile_ctr, e->d_stats);
+        if (e->timing) MAPA_CUDA_TRY(cudaEventRecord(ev1, e->stream));
+        const unsigned rgrid = static_cast<unsigned>(std::min<uint64_t>(ceil_div(g.size, 256), 1024));
+        k_resolve<W, CT, T><<<rgrid, 256, smem_all, e->stream>>>(t.args(), in, count_dev, count_host, ta, g);
+        MAPA_CUDA_TRY(cudaGetLastError());
+        e->st.kernel_launches += 2;
+        e->st.tail_launches += 1;
+        return MAPA_OK;
+    }
+
+    // ---- device-driven: every launch enqueued, no host synchronisation
+    int run_device() {
+        int rc = allow_smem();
+        if (rc != MAPA_OK) return rc;
+        rc = plan_layout(e, g.size, pat.k, T, W, true, t.n, &lay, err);
+        if (rc != MAPA_OK) return rc;
+        MAPA_CUDA_TRY(cudaMemsetAsync(lay.ctrl, 0, lay.ctrl_bytes, e->stream));
+        rc = setup(lay.counts);
+        if (rc != MAPA_OK) return rc;
+        static int nb_expand = 0;
+        if (!nb_expand) nb_expand = blocks_per_sm(k_expand<W, CT>, smem_all);
+        for (int ell = 0; ell < lay.L; ++ell) {
+            const uint64_t cap_in = lay.level[ell].cap;
+            const unsigned grid = static_cast<unsigned>(std::max<uint64_t>(
+                1, std::min<uint64_t>(ceil_div(cap_in, kTpb), uint64_t(e->sm_count) * nb_expand)));
+            k_expand<W, CT><<<grid, kTpb, smem_all, e->stream>>>(
+                t.args(), lay.level[ell], lay.level[ell + 1], ell, pat.back[ell], pat.lo[ell], lay.counts + ell,
+                lay.counts + ell + 1, lay.level[ell + 1].cap, lay.tiles + ell, lay.status[ell], gr.overflow, g.alpha,
+                g.beta, e->d_error, e->d_stats, entry_bytes(ell + 1, W));
+            MAPA_CUDA_TRY(cudaGetLastError());
+            e->st.kernel_launches += 1;
+        }
+        rc = last_level(lay.counts + lay.L, 0ull, lay.tiles + lay.L, lay.level[lay.L].cap);
+        if (rc != MAPA_OK) return rc;
+        return finalize();
+    }
+
+    // ---- host-driven: counts read back per level, children produced in
+    // chunks that fit the level capacity, depth first.
+    int process(int ell, uint64_t P) {
+        if (P == 0) return MAPA_OK;
+        if (ell == lay.L) {
+            MAPA_CUDA_TRY(cudaMemsetAsync(lay.tiles, 0, sizeof(unsigned int), e->stream));
+            return last_level(nullptr, P, lay.tiles, P);
+        }
+        const LevelView &in = lay.level[ell];
+        const LevelView &out = lay.level[ell + 1];
+        const uint64_t nb = ceil_div(P, kTile);
+        k_count<W><<<static_cast<unsigned>(nb), kTpb, smem_adj, e->stream>>>(t.args(), in, P, pat.back[ell],
+                                                                             pat.lo[ell], lay.warp_cnt[ell],
+                                                                             lay.blk_cnt[ell]);
+        launch_scan(lay.blk_cnt[ell], lay.blk_off[ell], nb, e->stream);
+        MAPA_CUDA_TRY(cudaGetLastError());
+        e->st.kernel_launches += 2;
+        MAPA_CUDA_TRY(cudaMemcpyAsync(e->h_pinned, lay.blk_off[ell] + nb, sizeof(unsigned long long),
+                                      cudaMemcpyDeviceToHost, e->stream));
+        MAPA_CUDA_TRY(cudaStreamSynchronize(e->stream));
+        const unsigned long long total = e->h_pinned[0];
+        if (total == 0) return MAPA_OK;
+        std::vector<unsigned long long> off;
+        if (total > lay.E) {
+            off.resize(nb + 1);
+            MAPA_CUDA_TRY(cudaMemcpyAsync(off.data(), lay.blk_off[ell], sizeof(unsigned long long) * (nb + 1),
+                                          cudaMemcpyDeviceToHost, e->stream));
+            MAPA_CUDA_TRY(cudaStreamSynchronize(e->stream));
+        }
+        uint64_t b0 = 0;
+        while (b0 < nb) {
+            uint64_t b1 = nb;
+            if (total > lay.E) {
+                b1 = std::upper_bound(off.begin() + b0 + 1, off.end(), off[b0] + lay.E) - off.begin() - 1;
+                if (b1 <= b0) {
+                    if (err) *err = "internal: one block's children exceed the level capacity";
+                    return MAPA_E_NOMEM;
+                }
+            }
+            const uint64_t children = total > lay.E ? off[b1] - off[b0] : total;
+            k_write<W, CT><<<static_cast<unsigned>(b1 - b0), kTpb, smem_all, e->stream>>>(
+                t.args(), in, P, ell, pat.back[ell], pat.lo[ell], out, lay.warp_cnt[ell], lay.blk_off[ell], b0,
+                g.alpha, g.beta);
+            MAPA_CUDA_TRY(cudaGetLastError());
+            e->st.kernel_launches += 1;
+            e->st.spill_entries += children;
+            e->st.spill_bytes += 2 * children * entry_bytes(ell + 1, W);
+            const int rc = process(ell + 1, children);
+            if (rc != MAPA_OK) return rc;
+            b0 = b1;
+        }
+        return MAPA_OK;
+    }
+
+    int run_host() {
+        int rc = allow_smem();
+        if (rc != MAPA_OK) return rc;
+        rc = plan_layout(e, g.size, pat.k, T, W, false, t.n, &lay, err);
+        if (rc != MAPA_OK) return rc;
+        rc = setup(nullptr);
+        if (rc != MAPA_OK) return rc;
+        rc = process(0, static_cast<uint64_t>(g.size));
+        if (rc != MAPA_OK) return rc;
+        return finalize();
+    }
+};
+
+// Picks the class-count specialisation and tail depth for a group.
+template <int W, int CT>
+inline int dispatch_tail(Engine *e, const TopoDevice &t, const GroupRun &gr, bool device, std::string *err) {
+    switch (gr.tail) {
+        case 1: {
+            Runner<W, CT, 1> r(e, t, gr, err);
+            return device ? r.run_device() : r.run_host();
+        }
+        case 2: {
+            Runner<W, CT, 2> r(e, t, gr, err);
+            return device ? r.run_device() : r.run_host();
+        }
+        case 3: {
+            Runner<W, CT, 3> r(e, t, gr, err);
+            return device ? r.run_device() : r.run_host();
+        }
+        default:
+            if (err) *err = "internal: tail depth must be 1..3";
+            return MAPA_E_INVALID;
+    }
+}
+
+template <int W>
+inline int dispatch_group(Engine *e, const TopoDevice &t, const GroupRun &gr, bool device, std::string *err) {
+    if constexpr (W <= 2) {
+        switch (t.C) {
+            case 1: return dispatch_tail<W, 1>(e, t, gr, device, err);
+            case 2: return dispatch_tail<W, 2>(e, t, gr, device, err);
+            case 3: return dispatch_tail<W, 3>(e, t, gr, device, err);
+            default: break;
+        }
+    }
+    return dispatch_tail<W, 0>(e, t, gr, device, err);
+}
+
+}  // namespace mapa
+
+#define MAPA_DEFINE_W(W)                                                                                        \
+    namespace mapa {                                                                                           \
+    int run_group_device_w##W(Engine *e, const TopoDevice &t, const GroupRun &gr, std::string *err) {         \
+        return dispatch_group<W>(e, t, gr, true, err);                                                         \
+    }                                                                                                          \
+    int run_group_host_w##W(Engine *e, const TopoDevice &t, const GroupRun &gr, std::string *err) {           \
+        return dispatch_group<W>(e, t, gr, false, err);                                                        \
+    }                                                                                                          \
+    }
