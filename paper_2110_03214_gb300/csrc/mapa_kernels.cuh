@@ -690,8 +690,10 @@ struct MaxLeaf {
 };
 
 // Fused last T levels: count and argmax key per request, no frontier write.
-// Parents are handed out in tiles of kTile through *tile_ctr (dynamic load
-// balance); P is *count_in (device-driven) or count_host (host-driven).
+// Each warp takes chunks of 32 * kIpt consecutive parents from *tile_ctr
+// (dynamic load balance without block barriers: a warp whose subtrees were
+// small simply takes the next chunk); P is *count_in (device-driven) or
+// count_host (host-driven).
 template <int W, int CT, int T>
 __global__ void __launch_bounds__(kTpb) k_last(TopoArgs topo, LevelView in, const unsigned long long *count_in,
                                                unsigned long long count_host, TailArgs ta, const int32_t *alpha,
@@ -702,25 +704,25 @@ __global__ void __launch_bounds__(kTpb) k_last(TopoArgs topo, LevelView in, cons
     __shared__ unsigned long long s_key[kWarps];
     __shared__ unsigned long long s_cnt[kWarps];
     __shared__ unsigned long long s_nodes, s_leaves, s_parents;
-    __shared__ unsigned int s_tile;
     if (threadIdx.x == 0) {
         s_nodes = 0ull;
         s_leaves = 0ull;
         s_parents = 0ull;
     }
+    __syncthreads();
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const unsigned long long P = count_in ? *count_in : count_host;
-    const unsigned long long ntiles = (P + kTile - 1) / kTile;
+    constexpr unsigned kChunk = 32 * kIpt;
+    const unsigned long long nchunks = (P + kChunk - 1) / kChunk;
     uint32_t r_cur = kNoReq;
     unsigned long long bkey = 0ull, bcnt = 0ull, parents = 0ull, leaves_total = 0ull;
     uint32_t nodes = 0;
     for (;;) {
-        if (threadIdx.x == 0) s_tile = atomicAdd(tile_ctr, 1u);
-        __syncthreads();
-        const unsigned long long tile = s_tile;
-        __syncthreads();
-        if (tile >= ntiles) break;
-        const uint64_t wbase = tile * kTile + static_cast<uint64_t>(warp) * 32 * kIpt;
+        unsigned int chunk = 0;
+        if (lane == 0) chunk = atomicAdd(tile_ctr, 1u);
+        chunk = __shfl_sync(kFull, chunk, 0);
+        if (chunk >= nchunks) break;
+        const uint64_t wbase = static_cast<uint64_t>(chunk) * kChunk;
         for (int j = 0; j < kIpt; ++j) {
             const uint64_t p = wbase + j * 32 + lane;
             if (p >= P) continue;
