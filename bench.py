@@ -44,6 +44,10 @@ def _args():
     ap.add_argument("--cpu-seconds", type=float, default=15.0, help="bounded oracle sample length")
     ap.add_argument("--plain-requests", type=int, default=300, help="requests timed through the plain per-request path")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--served-sweep", action="store_true", help="rate sweep of the served loop instead")
+    ap.add_argument("--served-requests", type=int, default=3000, help="arrivals in the served comparison")
+    ap.add_argument("--served-rate", type=float, default=1e4, help="Poisson rate of the served comparison")
+    ap.add_argument("--served-kmax", type=int, default=8)
     return ap.parse_args()
 
 
@@ -226,6 +230,55 @@ def _oracle_sample(wl, budget_s: float, threads: int, start: int = 0):
             i += len(chunk)
     dt = time.perf_counter() - t0
     return emb, done, dt
+
+
+def served_measure(M, W, rate: float, count: int, max_batch: int, kmax: int = 8, seed: int = 4):
+    """Drives the served loop with a Poisson trace on the 128-vertex dragonfly;
+    returns decisions/s over the run and p50/p99 arrival-to-decision latency."""
+    import numpy as np
+
+    tr = W.served_trace(count, rate=rate, kmax_rt=kmax, seed=seed)
+    with M.Context(0) as ctx:
+        tid = ctx.topology_load(tr.topology)
+        pids = np.asarray([ctx.pattern_load(p) for p in tr.patterns], np.int32)
+        ev = M.make_events(pids[tr.pattern_index], tr.at_ns, tr.lifetime_ns)
+        srv = M.mapa_serve_open(ctx.h, tid, max_batch)
+        try:
+            M.mapa_serve_submit(srv, ev)
+            M.mapa_serve_drain(srv, timeout_ms=120_000)
+            out = M.mapa_serve_poll(srv, max_events=count + 16)
+            counters = M.mapa_serve_counters(srv)
+        finally:
+            M.mapa_serve_close(srv)
+    lat = (out["done_ns"] - out["arrive_ns"]) / 1e6
+    span = (out["done_ns"].max() - out["arrive_ns"].min()) / 1e9
+    ok = out["result"]["status"] == 0
+    return {
+        "rate_per_s": rate, "requests": int(count), "max_batch": int(max_batch),
+        "decisions_per_s": float(len(out) / span), "p50_ms": float(np.percentile(lat, 50)),
+        "p99_ms": float(np.percentile(lat, 99)), "rounds": counters["rounds"], "conflicts_redone": counters["conflicts"],
+        "placed": int(ok.sum()), "matches_scored": int(out["result"]["count"].sum()),
+        "trace_s": float((tr.at_ns[-1] - tr.at_ns[0]) / 1e9), "workload": tr.description,
+    }
+
+
+def run_served_sweep(a):
+    """Served loop: batched rounds vs one request per round over a rate sweep."""
+    import __graft_entry__
+
+    __graft_entry__.build()
+    from paper_2110_03214_gb300 import mapa as M
+    from paper_2110_03214_gb300 import workloads as W
+
+    for rate in (1e3, 1e4, 1e5, 1e6):
+        count = int(min(20000, max(2000, rate * 0.5)))
+        for mb in (4096, 1):
+            if mb == 1 and rate > 1e4:
+                count_plain = 4000
+            else:
+                count_plain = count
+            r = served_measure(M, W, rate, count if mb > 1 else count_plain, mb, kmax=a.served_kmax)
+            print(json.dumps(r), flush=True)
 
 
 def run_reference(a):
@@ -420,6 +473,12 @@ def run_ours(a):
             "e2e": e2e,
             "clocks": clk,
         }
+        if world == 1 and a.served_requests > 0:
+            sb = served_measure(M, W, a.served_rate, a.served_requests, 4096, kmax=a.served_kmax)
+            sp = served_measure(M, W, a.served_rate, a.served_requests, 1, kmax=a.served_kmax)
+            line["served"] = {"batched": sb, "plain": sp}
+            line["latency_ms"].update({"served_batched_p50": sb["p50_ms"], "served_batched_p99": sb["p99_ms"],
+                                       "served_plain_p50": sp["p50_ms"], "served_plain_p99": sp["p99_ms"]})
         if world == 1 and not a.no_cpu_baseline:
             threads = os.cpu_count() or 1
             emb, done, dt = _oracle_sample(wl, a.cpu_seconds, threads)
@@ -432,7 +491,9 @@ def run_ours(a):
 
 def main():
     a = _args()
-    if a.impl == "reference":
+    if a.served_sweep:
+        run_served_sweep(a)
+    elif a.impl == "reference":
         run_reference(a)
     else:
         run_ours(a)

@@ -189,6 +189,92 @@ int mapa_release(mapa_ctx ctx, int32_t topo_id, int64_t job_id);
 int mapa_allocate_batch(mapa_ctx ctx, int32_t topo_id, int32_t nreq, const mapa_request *reqs,
                         mapa_result *out, uint32_t flags);
 
+/* ---- serving ------------------------------------------------------------ */
+
+/* A served allocation loop on one topology (continuous batching).  A worker
+ * thread owned by the server admits every request that has arrived, up to
+ * max_batch, decides them together in one batched pass against a snapshot of
+ * the device-resident occupancy, then commits the decisions on the device in
+ * arrival order (Sec. 3.6 state management; FIFO order of Sec. 4): the
+ * longest prefix of decisions that do not overlap one another is committed,
+ * and the requests from the first overlap on are decided again in the same
+ * round, one after another against the live occupancy (a device-side chain:
+ * each is committed before the next is decided), so no request is decided
+ * more than twice.  Departures
+ * return a job's vertices before later arrivals are decided.  Requests that
+ * arrive while a round is on the GPU wait for the next round, so the device
+ * works on everything that is pending, up to an admission window that
+ * doubles after a round whose parallel decisions all committed and shrinks
+ * after one that met an overlap or a wait (at most max_batch).  max_batch = 1
+ * gives the plain per-request form (one request per round). */
+
+enum mapa_event_kind { MAPA_EVENT_ARRIVE = 0, MAPA_EVENT_DEPART = 1 };
+
+/* One event of a served trace (64 bytes).
+ *   at_ns:       arrival time in ns after mapa_serve_open (0 = immediately).
+ *                Events of one submit call must have non-decreasing at_ns.
+ *   ARRIVE:      pattern_id, policy; lifetime_ns > 0 makes the server release
+ *                the job lifetime_ns after it is committed (0 = keep until a
+ *                DEPART event names it).
+ *   DEPART:      job_id of a committed job. */
+typedef struct {
+    int64_t request_id;
+    int64_t at_ns;
+    int64_t lifetime_ns;
+    int64_t job_id;
+    int32_t kind;
+    int32_t pattern_id;
+    mapa_policy policy;
+} mapa_event;
+
+/* A finished event (144 bytes).  For ARRIVE, result is the decision (job_id
+ * set when committed).  For DEPART, result.status is MAPA_OK or MAPA_E_STATE
+ * (unknown job).  snapshot is the occupancy the decision was taken against
+ * (deciding the request alone with that busy mask gives the same result);
+ * arrive_ns / done_ns are times after mapa_serve_open; rounds counts the
+ * decisions it took (1, or 2 when it lost a conflict in its round). */
+typedef struct {
+    int64_t request_id;
+    int64_t arrive_ns;
+    int64_t done_ns;
+    int32_t kind;
+    int32_t rounds;
+    uint32_t snapshot[MAPA_MASK_WORDS];
+    mapa_result result;
+} mapa_served;
+
+typedef struct mapa_server_s *mapa_server;
+
+/* Flags of mapa_serve_open.  By default the queue is FIFO as in the paper's
+ * scheduler (Sec. 4): a request that does not fit waits at the head of the
+ * queue, with everything behind it, until a departure frees accelerators;
+ * it is answered MAPA_NO_FIT only when nothing the server holds will ever be
+ * released.  MAPA_SERVE_REJECT answers MAPA_NO_FIT at once instead. */
+#define MAPA_SERVE_REJECT 1u
+
+/* Opens a server on topo_id (max_batch >= 1 requests per round).  The
+ * server drives ctx's stream from its own thread: make no other call on ctx
+ * until mapa_serve_close returns. */
+int mapa_serve_open(mapa_ctx ctx, int32_t topo_id, int32_t max_batch, uint32_t flags, mapa_server *out);
+
+/* Queues n events (copied).  Thread safe. */
+int mapa_serve_submit(mapa_server srv, const mapa_event *events, int32_t n);
+
+/* Moves up to max finished events into out; *got receives the number.
+ * timeout_ms > 0 waits up to that long for at least one. */
+int mapa_serve_poll(mapa_server srv, mapa_served *out, int32_t max, int32_t *got, int32_t timeout_ms);
+
+/* Blocks until every submitted event has finished (timeout_ms <= 0: no limit);
+ * MAPA_E_TIMEOUT if the limit passes first. */
+int mapa_serve_drain(mapa_server srv, int32_t timeout_ms);
+
+/* Counters of the server: rounds run, decisions, decisions redone after a conflict. */
+int mapa_serve_counters(mapa_server srv, uint64_t *rounds, uint64_t *decisions, uint64_t *conflicts);
+
+/* Stops the worker (pending events are dropped) and frees the server.  The
+ * first error the worker met, if any, is returned here. */
+int mapa_serve_close(mapa_server srv);
+
 /* ---- allocation-free decisions ------------------------------------------ */
 
 /* Limits of mapa_allocate_batch_noalloc. */

@@ -14,6 +14,7 @@
 #include <utility>
 #include <vector>
 
+#include "mapa_ctx.h"
 #include "mapa_internal.h"
 
 static_assert(sizeof(mapa_policy) == 24, "mapa_policy layout");
@@ -24,26 +25,10 @@ namespace {
 
 thread_local std::string g_create_error;
 
-struct TopoEntry {
-    mapa::TopoDevice dev;
-    bool live = false;
-};
-
-struct PatternEntry {
-    mapa::PatternArgs args;
-    uint64_t aut_order = 0;
-};
+using mapa::PatternEntry;
+using mapa::TopoEntry;
 
 }  // namespace
-
-struct mapa_ctx_s {
-    mapa::Engine *engine = nullptr;
-    int device = 0;
-    std::string last_error;
-    std::vector<TopoEntry> topos;
-    std::vector<PatternEntry> patterns;
-    std::vector<mapa::PatternArgs> pattern_args;  // contiguous copy handed to the engine
-};
 
 namespace mapa {
 

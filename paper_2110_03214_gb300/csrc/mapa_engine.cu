@@ -74,8 +74,19 @@ void launch_scan(const unsigned long long *cnt, unsigned long long *off, uint64_
 }
 
 // State management (Sec. 3.6): mark the chosen vertices busy under a new job id.
-__global__ void k_commit(mapa_result *res, uint32_t *occ, int64_t *owner, unsigned long long *next_job) {
+// With `blocked` (FIFO waiting): once a request of the chain did not fit,
+// it and every later one are marked deferred (reserved = kDeferred) and
+// nothing more is committed.
+__global__ void k_commit(mapa_result *res, uint32_t *occ, int64_t *owner, unsigned long long *next_job,
+                         int32_t *blocked) {
     if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    if (blocked) {
+        if (*blocked || res->status == MAPA_NO_FIT) {
+            *blocked = 1;
+            res->reserved = kDeferred;
+            return;
+        }
+    }
     if (res->status != MAPA_OK) return;
     const long long job = static_cast<long long>(atomicAdd(next_job, 1ull)) + 1;
     for (int i = 0; i < res->k; ++i) {
@@ -93,6 +104,61 @@ __global__ void k_release(int n, long long job, uint32_t *occ, int64_t *owner, i
             owner[v] = 0;
             atomicAnd(occ + (v >> 5), ~(1u << (v & 31)));
             atomicAdd(freed, 1);
+        }
+    }
+}
+
+// Serving round commit (Sec. 3.6 state management, FIFO order of Sec. 4):
+// decisions of one round were taken against the same occupancy snapshot;
+// commit the longest prefix, in arrival order, whose decisions do not overlap
+// one another.  conflict[i] = 1 from the first overlapping decision on (the
+// server decides those again, in order, against the live occupancy);
+// with fifo_wait, conflict[i] = 2 from the first request that did not fit on
+// (it and everything behind it wait at the head of the queue).
+__global__ void k_commit_round(mapa_result *res, int32_t n, uint32_t *occ, int64_t *owner,
+                               unsigned long long *next_job, int32_t *conflict, int32_t fifo_wait) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    uint32_t cur[MAPA_MASK_WORDS];
+    for (int w = 0; w < MAPA_MASK_WORDS; ++w) cur[w] = occ[w];
+    int32_t stop = 0;
+    for (int i = 0; i < n; ++i) {
+        conflict[i] = stop;
+        if (stop) continue;
+        if (fifo_wait && res[i].status == MAPA_NO_FIT) {
+            stop = conflict[i] = 2;
+            continue;
+        }
+        if (res[i].status != MAPA_OK) continue;
+        uint32_t mask[MAPA_MASK_WORDS] = {};
+        for (int j = 0; j < res[i].k; ++j) {
+            const int v = res[i].verts[j];
+            mask[v >> 5] |= 1u << (v & 31);
+        }
+        bool clash = false;
+        for (int w = 0; w < MAPA_MASK_WORDS; ++w) clash |= (mask[w] & cur[w]) != 0u;
+        if (clash) {
+            stop = conflict[i] = 1;
+            continue;
+        }
+        const long long job = static_cast<long long>(atomicAdd(next_job, 1ull)) + 1;
+        for (int w = 0; w < MAPA_MASK_WORDS; ++w) cur[w] |= mask[w];
+        for (int j = 0; j < res[i].k; ++j) owner[res[i].verts[j]] = job;
+        res[i].job_id = job;
+    }
+    for (int w = 0; w < MAPA_MASK_WORDS; ++w) occ[w] = cur[w];
+}
+
+// Returns the vertices of several jobs to the free pool (Sec. 3.6).
+__global__ void k_release_many(int n, const int64_t *jobs, int32_t njobs, uint32_t *occ, int64_t *owner) {
+    for (int v = threadIdx.x; v < n; v += blockDim.x) {
+        const int64_t o = owner[v];
+        if (o == 0) continue;
+        for (int j = 0; j < njobs; ++j) {
+            if (o == jobs[j]) {
+                owner[v] = 0;
+                atomicAnd(occ + (v >> 5), ~(1u << (v & 31)));
+                break;
+            }
         }
     }
 }
@@ -159,6 +225,7 @@ Engine *engine_create(int device, uint64_t frontier_cap, std::string *err) {
     if (cudaStreamCreateWithFlags(&en->own_stream, cudaStreamNonBlocking) != cudaSuccess ||
         cudaMalloc(&en->d_error, sizeof(int32_t)) != cudaSuccess ||
         cudaMalloc(&en->d_stats, kStatWords * sizeof(unsigned long long)) != cudaSuccess ||
+        cudaMalloc(&en->d_blocked, sizeof(int32_t)) != cudaSuccess ||
         cudaMallocHost(&en->h_pinned, 64 * sizeof(unsigned long long)) != cudaSuccess) {
         if (err) *err = "context allocation failed";
         engine_destroy(en);
@@ -183,6 +250,7 @@ void engine_destroy(Engine *e) {
     cudaFree(e->overflow);
     cudaFree(e->d_error);
     cudaFree(e->d_stats);
+    cudaFree(e->d_blocked);
     for (cudaEvent_t ev : e->events) cudaEventDestroy(ev);
     if (e->h_pinned) cudaFreeHost(e->h_pinned);
     if (e->own_stream) cudaStreamDestroy(e->own_stream);
@@ -271,12 +339,19 @@ int plan_layout(Engine *e, int32_t group_size, int k, int T, int W, bool device_
             off_scr[ell][2] = bump((nb + 1) * 8);
         }
     }
+    // Level l of a group holds at most group_size * n^l entries (each entry
+    // has fewer than n children), and never more than its capacity.
+    lay->bound[0] = lvl0;
+    for (int ell = 1; ell <= lay->L; ++ell) {
+        const uint64_t b = lay->bound[ell - 1];
+        lay->bound[ell] = b > E / static_cast<uint64_t>(std::max(n, 1)) ? E : std::min<uint64_t>(E, b * n);
+    }
     const uint64_t ctrl_begin = total;
     const uint64_t off_counts = bump(8ull * (lay->L + 1));
     const uint64_t off_tiles = bump(4ull * (lay->L + 1));
     uint64_t off_status[kMaxK + 1];
     if (device_mode)
-        for (int ell = 0; ell < lay->L; ++ell) off_status[ell] = bump(8ull * ((ell == 0 ? lvl0 : E) / kTpb + 2));
+        for (int ell = 0; ell < lay->L; ++ell) off_status[ell] = bump(8ull * (lay->bound[ell] / kTpb + 2));
     const uint64_t ctrl_end = total;
     uint64_t have = e->arena_bytes;
     const int rc = ensure_device(&e->arena, &have, std::max<uint64_t>(total, 1), err);
@@ -308,10 +383,11 @@ int plan_layout(Engine *e, int32_t group_size, int k, int T, int W, bool device_
 // ----------------------------------------------------------------------------
 // Batch driver
 
+// Fused tail depth of a pattern.  The stored level k - T must hold more than
+// the requests' roots when k >= 2, or one thread would walk a whole request.
 static int tail_depth(const Engine *e, const PatternArgs &p) {
-    int T = e->tail_override > 0 ? e->tail_override : 2;
-    T = std::min(T, 3);
-    return std::max(1, std::min(T, p.k));
+    if (e->tail_override > 0) return std::max(1, std::min({e->tail_override, 3, p.k}));
+    return p.k >= 3 ? 2 : 1;
 }
 
 static int run_group(Engine *e, const TopoDevice &t, const GroupRun &gr, bool device, std::string *err) {
@@ -461,7 +537,7 @@ int engine_run_batch(Engine *e, const TopoDevice &t, const std::vector<PatternAr
                 rc = run_group(e, t, gr, false, err);
                 if (rc != MAPA_OK) return rc;
             }
-            k_commit<<<1, 32, 0, e->stream>>>(out_dev + i, t.occupancy, t.owner, t.next_job);
+            k_commit<<<1, 32, 0, e->stream>>>(out_dev + i, t.occupancy, t.owner, t.next_job, nullptr);
             MAPA_CUDA_TRY(cudaGetLastError());
             e->st.kernel_launches += 1;
         }
@@ -527,6 +603,80 @@ int engine_run_batch(Engine *e, const TopoDevice &t, const std::vector<PatternAr
         if (rc != MAPA_OK) return rc;
     }
     return end_batch(e, err);
+}
+
+// Decides reqs_dev[0..n) one after another against the live device
+// occupancy, committing each before the next is decided (FIFO, Sec. 3.6),
+// with every launch enqueued and a single synchronisation at the end.  A
+// request whose frontier outgrows the arena makes the call fail with
+// MAPA_E_NOMEM (its commit would not be trustworthy).
+int engine_run_chain(Engine *e, const TopoDevice &t, const std::vector<PatternArgs> &patterns, int32_t n,
+                     const int32_t *pattern_ids, const mapa_request *reqs_dev, mapa_result *out_dev, bool fifo_wait,
+                     std::string *err) {
+    MAPA_CUDA_TRY(cudaSetDevice(e->device));
+    if (n <= 0) return MAPA_OK;
+    GroupArgs g;
+    memset(&g, 0, sizeof(g));
+    g.reqs = reqs_dev;
+    g.out = out_dev;
+    g.total_weight = t.total_weight;
+    g.error = e->d_error;
+    g.occupancy = t.occupancy;
+    g.size = 1;
+    int rc = begin_batch(e, err);
+    if (rc == MAPA_OK) rc = group_arrays(e, 1, &g, err);
+    if (rc == MAPA_OK) rc = ensure_i32(&e->order, &e->order_cap, n, err);
+    if (rc == MAPA_OK) rc = ensure_i32(&e->overflow, &e->overflow_cap, n, err);
+    if (rc != MAPA_OK) return rc;
+    std::vector<int32_t> idx(n);
+    for (int32_t i = 0; i < n; ++i) idx[i] = i;
+    MAPA_CUDA_TRY(cudaMemcpyAsync(e->order, idx.data(), sizeof(int32_t) * n, cudaMemcpyHostToDevice, e->stream));
+    MAPA_CUDA_TRY(cudaMemsetAsync(e->overflow, 0, sizeof(int32_t) * n, e->stream));
+    MAPA_CUDA_TRY(cudaMemsetAsync(e->d_blocked, 0, sizeof(int32_t), e->stream));
+    const int32_t npat = static_cast<int32_t>(patterns.size());
+    for (int32_t i = 0; i < n; ++i) {
+        const int32_t pid = pattern_ids[i];
+        if (pid < 0 || pid >= npat) {
+            if (err) *err = "unknown pattern id in a served request";
+            return MAPA_E_INVALID;
+        }
+        g.req_index = e->order + i;
+        GroupRun gr{&patterns[pid], g, tail_depth(e, patterns[pid]), e->overflow + i};
+        rc = run_group(e, t, gr, true, err);
+        if (rc != MAPA_OK) return rc;
+        k_commit<<<1, 32, 0, e->stream>>>(out_dev + i, t.occupancy, t.owner, t.next_job,
+                                          fifo_wait ? e->d_blocked : nullptr);
+        MAPA_CUDA_TRY(cudaGetLastError());
+        e->st.kernel_launches += 1;
+    }
+    std::vector<int32_t> ovf(n);
+    MAPA_CUDA_TRY(cudaMemcpyAsync(ovf.data(), e->overflow, sizeof(int32_t) * n, cudaMemcpyDeviceToHost, e->stream));
+    rc = end_batch(e, err);
+    if (rc != MAPA_OK) return rc;
+    for (int32_t i = 0; i < n; ++i)
+        if (ovf[i]) {
+            if (err) *err = "a served request outgrew the frontier arena; raise frontier_mem_cap";
+            return MAPA_E_NOMEM;
+        }
+    return MAPA_OK;
+}
+
+int engine_commit_round(Engine *e, const TopoDevice &t, mapa_result *out_dev, int32_t n, int32_t *conflict_dev,
+                        bool fifo_wait, std::string *err) {
+    if (n <= 0) return MAPA_OK;
+    k_commit_round<<<1, 32, 0, e->stream>>>(out_dev, n, t.occupancy, t.owner, t.next_job, conflict_dev,
+                                            fifo_wait ? 1 : 0);
+    MAPA_CUDA_TRY(cudaGetLastError());
+    e->st.kernel_launches += 1;
+    return MAPA_OK;
+}
+
+int engine_release_many(Engine *e, const TopoDevice &t, const int64_t *jobs_dev, int32_t njobs, std::string *err) {
+    if (njobs <= 0) return MAPA_OK;
+    k_release_many<<<1, 256, 0, e->stream>>>(t.n, jobs_dev, njobs, t.occupancy, t.owner);
+    MAPA_CUDA_TRY(cudaGetLastError());
+    e->st.kernel_launches += 1;
+    return MAPA_OK;
 }
 
 int engine_release(Engine *e, const TopoDevice &t, int64_t job_id, int32_t *freed, std::string *err) {

@@ -44,6 +44,7 @@ struct Engine {
     int32_t overflow_cap = 0;
     int32_t *d_error = nullptr;
     unsigned long long *d_stats = nullptr;  // kStatWords counters of the current batch
+    int32_t *d_blocked = nullptr;           // FIFO-wait flag of a commit chain
     unsigned long long *h_pinned = nullptr;  // small pinned scratch
     mapa_stats st{};
     bool timing = false;

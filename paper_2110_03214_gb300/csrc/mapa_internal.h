@@ -121,6 +121,18 @@ int noalloc_decide(const TopoDevice &t, const PatternArgs &pat, int32_t pattern_
 
 int engine_release(Engine *e, const TopoDevice &t, int64_t job_id, int32_t *freed, std::string *err);
 
+// Serving: commit a round's decisions in order with conflict flags, and
+// release a list of jobs (device array); both enqueue only.
+// Internal mark (mapa_result.reserved) of a chain decision deferred by FIFO waiting.
+constexpr int32_t kDeferred = 2;
+
+int engine_commit_round(Engine *e, const TopoDevice &t, mapa_result *out_dev, int32_t n, int32_t *conflict_dev,
+                        bool fifo_wait, std::string *err);
+int engine_run_chain(Engine *e, const TopoDevice &t, const std::vector<PatternArgs> &patterns, int32_t n,
+                     const int32_t *pattern_ids, const mapa_request *reqs_dev, mapa_result *out_dev, bool fifo_wait,
+                     std::string *err);
+int engine_release_many(Engine *e, const TopoDevice &t, const int64_t *jobs_dev, int32_t njobs, std::string *err);
+
 // Scratch for staging host batches.
 int engine_stage(Engine *e, int32_t nreq, mapa_request **reqs_dev, mapa_result **out_dev, std::string *err);
 

@@ -611,17 +611,18 @@ __global__ void __launch_bounds__(kTpb) k_expand(TopoArgs topo, LevelView in, Le
                                                  unsigned int *tile_ctr, unsigned long long *status, int32_t *overflow,
                                                  const int32_t *alpha, const int32_t *beta, int32_t *err,
                                                  unsigned long long *stats, unsigned long long child_bytes) {
-    const SmemTopo s = stage_topology<W>(topo, true);
-    __shared__ unsigned int s_tile;
-    __shared__ int s_wtot[kWarps];
-    __shared__ unsigned long long s_excl;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const unsigned long long P = *count_in;
     const unsigned long long ntiles = (P + kTpb - 1) / kTpb;
     if (ntiles == 0) {
         if (blockIdx.x == 0 && threadIdx.x == 0) *count_out = 0ull;
         return;
     }
+    if (static_cast<unsigned long long>(blockIdx.x) >= ntiles) return;  // no tile will be left for this block
+    const SmemTopo s = stage_topology<W>(topo, true);
+    __shared__ unsigned int s_tile;
+    __shared__ int s_wtot[kWarps];
+    __shared__ unsigned long long s_excl;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     for (;;) {
         if (threadIdx.x == 0) s_tile = atomicAdd(tile_ctr, 1u);
         __syncthreads();
@@ -699,6 +700,10 @@ __global__ void __launch_bounds__(kTpb) k_last(TopoArgs topo, LevelView in, cons
                                                unsigned long long count_host, TailArgs ta, const int32_t *alpha,
                                                const int32_t *beta, uint64_t *key, unsigned long long *count,
                                                unsigned int *tile_ctr, unsigned long long *stats) {
+    {
+        const unsigned long long P0 = count_in ? *count_in : count_host;
+        if (static_cast<unsigned long long>(blockIdx.x) * kWarps * 32 * kIpt >= P0) return;  // nothing for this block
+    }
     const SmemTopo s = stage_topology<W>(topo, true);
     __shared__ uint32_t s_r[kWarps];
     __shared__ unsigned long long s_key[kWarps];

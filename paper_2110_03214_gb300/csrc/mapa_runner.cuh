@@ -23,7 +23,8 @@ struct LayoutPlan {
     // device-driven path: level counts, tile tickets, look-back status words
     unsigned long long *counts = nullptr;   // [L + 1]
     unsigned int *tiles = nullptr;          // [L + 1]
-    unsigned long long *status[kMaxK + 1];  // [cap_l / kTpb + 1] per level l < L
+    unsigned long long *status[kMaxK + 1];  // [bound_l / kTpb + 2] per level l < L
+    uint64_t bound[kMaxK + 1];              // upper bound on the entries of level l (<= its capacity)
     char *ctrl = nullptr;                   // contiguous control region (zeroed per run)
     uint64_t ctrl_bytes = 0;
 };
@@ -146,9 +147,8 @@ struct Runner {
         static int nb_expand = 0;
         if (!nb_expand) nb_expand = blocks_per_sm(k_expand<W, CT>, smem_all);
         for (int ell = 0; ell < lay.L; ++ell) {
-            const uint64_t cap_in = lay.level[ell].cap;
             const unsigned grid = static_cast<unsigned>(std::max<uint64_t>(
-                1, std::min<uint64_t>(ceil_div(cap_in, kTpb), uint64_t(e->sm_count) * nb_expand)));
+                1, std::min<uint64_t>(ceil_div(lay.bound[ell], kTpb), uint64_t(e->sm_count) * nb_expand)));
             k_expand<W, CT><<<grid, kTpb, smem_all, e->stream>>>(
                 t.args(), lay.level[ell], lay.level[ell + 1], ell, pat.back[ell], pat.lo[ell], lay.counts + ell,
                 lay.counts + ell + 1, lay.level[ell + 1].cap, lay.tiles + ell, lay.status[ell], gr.overflow, g.alpha,
@@ -156,7 +156,7 @@ struct Runner {
             MAPA_CUDA_TRY(cudaGetLastError());
             e->st.kernel_launches += 1;
         }
-        rc = last_level(lay.counts + lay.L, 0ull, lay.tiles + lay.L, lay.level[lay.L].cap);
+        rc = last_level(lay.counts + lay.L, 0ull, lay.tiles + lay.L, lay.bound[lay.L]);
         if (rc != MAPA_OK) return rc;
         return finalize();
     }

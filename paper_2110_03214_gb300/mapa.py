@@ -54,6 +54,29 @@ RESULT_DTYPE = np.dtype(
 )
 
 
+MAPA_EVENT_ARRIVE = 0
+MAPA_EVENT_DEPART = 1
+
+EVENT_DTYPE = np.dtype(
+    {
+        "names": ["request_id", "at_ns", "lifetime_ns", "job_id", "kind", "pattern_id", "alpha", "beta", "mode",
+                  "reserved", "max_embeddings"],
+        "formats": ["<i8", "<i8", "<i8", "<i8", "<i4", "<i4", "<i4", "<i4", "<i4", "<i4", "<u8"],
+        "offsets": [0, 8, 16, 24, 32, 36, 40, 44, 48, 52, 56],
+        "itemsize": 64,
+    }
+)
+
+SERVED_DTYPE = np.dtype(
+    {
+        "names": ["request_id", "arrive_ns", "done_ns", "kind", "rounds", "snapshot", "result"],
+        "formats": ["<i8", "<i8", "<i8", "<i4", "<i4", ("<u4", (8,)), RESULT_DTYPE],
+        "offsets": [0, 8, 16, 24, 28, 32, 64],
+        "itemsize": 144,
+    }
+)
+
+
 class Stats(ctypes.Structure):
     """mirror of mapa_stats"""
 
@@ -104,6 +127,13 @@ def _load() -> ctypes.CDLL:
         "mapa_stats_get": ([vp, ctypes.POINTER(Stats)], ctypes.c_int),
         "mapa_stats_reset": ([vp], ctypes.c_int),
         "mapa_ctx_set_timing": ([vp, ctypes.c_int], ctypes.c_int),
+        "mapa_serve_open": ([vp, i32, i32, u32, ctypes.POINTER(vp)], ctypes.c_int),
+        "mapa_serve_submit": ([vp, vp, i32], ctypes.c_int),
+        "mapa_serve_poll": ([vp, vp, i32, ctypes.POINTER(ctypes.c_int32), i32], ctypes.c_int),
+        "mapa_serve_drain": ([vp, i32], ctypes.c_int),
+        "mapa_serve_counters": ([vp, ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(ctypes.c_uint64),
+                                 ctypes.POINTER(ctypes.c_uint64)], ctypes.c_int),
+        "mapa_serve_close": ([vp], ctypes.c_int),
         "mapa_pattern_analyze": ([i32, i32, i32p, i32p, ctypes.POINTER(ctypes.c_uint64),
                                   ctypes.POINTER(ctypes.c_uint32), ctypes.POINTER(ctypes.c_uint32)], ctypes.c_int),
     }
@@ -121,7 +151,8 @@ SYMBOLS = (
     "mapa_ctx_create", "mapa_ctx_destroy", "mapa_ctx_set_stream", "mapa_last_error", "mapa_topology_load",
     "mapa_pattern_load", "mapa_pattern_builtin", "mapa_allocate", "mapa_release", "mapa_allocate_batch",
     "mapa_occupancy_get", "mapa_pattern_analyze", "mapa_version", "mapa_stats_get", "mapa_stats_reset",
-    "mapa_ctx_set_timing", "mapa_allocate_batch_noalloc",
+    "mapa_ctx_set_timing", "mapa_allocate_batch_noalloc", "mapa_serve_open", "mapa_serve_submit",
+    "mapa_serve_poll", "mapa_serve_drain", "mapa_serve_counters", "mapa_serve_close",
 )
 
 
@@ -243,6 +274,62 @@ def mapa_stats_reset(ctx) -> None:
 
 def mapa_ctx_set_timing(ctx, on: bool) -> None:
     _check(ctx, lib.mapa_ctx_set_timing(ctx, 1 if on else 0))
+
+
+MAPA_SERVE_REJECT = 1
+
+
+def mapa_serve_open(ctx, topo_id: int, max_batch: int, flags: int = 0):
+    h = ctypes.c_void_p()
+    _check(ctx, lib.mapa_serve_open(ctx, topo_id, max_batch, flags, ctypes.byref(h)))
+    return h
+
+
+def mapa_serve_submit(srv, events) -> None:
+    events = np.ascontiguousarray(events, dtype=EVENT_DTYPE)
+    rc = lib.mapa_serve_submit(srv, events.ctypes.data, events.shape[0])
+    if rc != MAPA_OK:
+        raise MapaError(rc, "mapa_serve_submit failed")
+
+
+def mapa_serve_poll(srv, max_events: int = 1 << 16, timeout_ms: int = 0) -> np.ndarray:
+    out = np.zeros(max_events, SERVED_DTYPE)
+    got = ctypes.c_int32()
+    rc = lib.mapa_serve_poll(srv, out.ctypes.data, max_events, ctypes.byref(got), timeout_ms)
+    if rc != MAPA_OK:
+        raise MapaError(rc, "serving loop failed")
+    return out[: got.value]
+
+
+def mapa_serve_drain(srv, timeout_ms: int = 0) -> None:
+    rc = lib.mapa_serve_drain(srv, timeout_ms)
+    if rc != MAPA_OK:
+        raise MapaError(rc, "mapa_serve_drain failed")
+
+
+def mapa_serve_counters(srv):
+    r, d, c = ctypes.c_uint64(), ctypes.c_uint64(), ctypes.c_uint64()
+    lib.mapa_serve_counters(srv, ctypes.byref(r), ctypes.byref(d), ctypes.byref(c))
+    return {"rounds": r.value, "decisions": d.value, "conflicts": c.value}
+
+
+def mapa_serve_close(srv) -> None:
+    rc = lib.mapa_serve_close(srv)
+    if rc != MAPA_OK:
+        raise MapaError(rc, "serving loop ended with an error")
+
+
+def make_events(pattern_ids, at_ns, lifetime_ns=0, alpha=1, beta=1, request_ids=None) -> np.ndarray:
+    pattern_ids = np.asarray(pattern_ids, np.int32)
+    ev = np.zeros(pattern_ids.shape[0], EVENT_DTYPE)
+    ev["request_id"] = np.arange(pattern_ids.shape[0]) if request_ids is None else request_ids
+    ev["at_ns"] = at_ns
+    ev["lifetime_ns"] = lifetime_ns
+    ev["kind"] = MAPA_EVENT_ARRIVE
+    ev["pattern_id"] = pattern_ids
+    ev["alpha"] = alpha
+    ev["beta"] = beta
+    return ev
 
 
 def mapa_pattern_analyze(k: int, a, b):

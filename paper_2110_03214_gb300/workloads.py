@@ -437,3 +437,35 @@ def arrivals(rng: Rng, count: int, rate: float, mean_k: float, n: int, occupancy
     tau = occupancy * n / (rate * mean_k)
     life = -np.log1p(-rng.uniform(count)) * tau
     return np.cumsum(gaps), life
+
+
+@dataclasses.dataclass
+class ServedTrace:
+    """A served workload: one topology and timed arrivals with lifetimes."""
+
+    topology: Topology
+    patterns: list
+    pattern_index: np.ndarray  # int32 [R]
+    at_ns: np.ndarray  # int64 [R], non-decreasing
+    lifetime_ns: np.ndarray  # int64 [R]
+    rate: float
+    description: str
+
+
+def served_trace(count: int, rate: float, kmax_rt: int = 8, clique_max: int = 4, occupancy: float = 0.6,
+                 seed: int = 4) -> ServedTrace:
+    """Poisson arrivals at `rate`/s on the 128-vertex dragonfly.
+
+    Pattern mix as in torus64 (ring/tree k uniform in 2..kmax_rt, clique k in
+    2..clique_max); exponential lifetimes with mean occupancy * n / (rate * E[k])
+    so the offered occupancy is about `occupancy` at every rate.
+    """
+    trng = Rng(seed, 1)
+    rrng = Rng(seed, 3)
+    topo = dragonfly(trng)
+    pats, index = _mix_patterns(rrng, count, kmax_rt, clique_max)
+    ks = np.asarray([pats[i].k for i in index], np.float64)
+    t, life = arrivals(rrng, count, rate, float(ks.mean()), topo.n, occupancy)
+    desc = (f"128-vertex dragonfly, ring/tree k in 2..{kmax_rt}, clique k in 2..{clique_max}, "
+            f"Poisson {rate:g}/s, offered occupancy {occupancy:g}")
+    return ServedTrace(topo, pats, index, (t * 1e9).astype(np.int64), (life * 1e9).astype(np.int64), rate, desc)
