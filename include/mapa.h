@@ -327,6 +327,16 @@ typedef struct {
     uint64_t embeddings;       /* matches scored, once per distinct subgraph */
 } mapa_stats;
 
+/* Autotuner of the batched path: for every pattern present in the host
+ * batch reqs[0..nreq), times each fused tail depth (1, 2 or 3 last pattern
+ * vertices scored in registers instead of written to a frontier) on that
+ * pattern's requests and keeps the fastest for (topo_id, pattern) in the
+ * context.  Results never change with the depth, only the time does.
+ * chosen must hold one entry per loaded pattern and receives the depth
+ * chosen for each (0 for patterns absent from the batch).  Nothing is
+ * committed. */
+int mapa_autotune(mapa_ctx ctx, int32_t topo_id, int32_t nreq, const mapa_request *reqs, int32_t *chosen);
+
 /* Copies the counters into *out. */
 int mapa_stats_get(mapa_ctx ctx, mapa_stats *out);
 

@@ -218,6 +218,7 @@ int add_pattern(mapa_ctx ctx, int32_t k, const std::vector<std::pair<int, int>> 
     std::string err;
     const int rc = mapa::analyze_pattern(k, edges, &pe.args, &pe.aut_order, &err);
     if (rc != MAPA_OK) return fail(ctx, rc, err);
+    pe.args.id = static_cast<int32_t>(ctx->patterns.size());
     ctx->patterns.push_back(pe);
     ctx->pattern_args.push_back(pe.args);
     *pattern_id = static_cast<int32_t>(ctx->patterns.size() - 1);
@@ -349,6 +350,7 @@ int mapa_topology_load(mapa_ctx ctx, int32_t n, int32_t m, const int32_t *u, con
     CTX_CUDA(ctx, cudaMemsetAsync(t.next_job, 0, sizeof(unsigned long long), st));
     CTX_CUDA(ctx, cudaStreamSynchronize(st));
     te.live = true;
+    t.id = static_cast<int32_t>(ctx->topos.size());
     ctx->topos.push_back(te);
     *topo_id = static_cast<int32_t>(ctx->topos.size() - 1);
     return MAPA_OK;
@@ -461,6 +463,20 @@ int mapa_allocate_batch_noalloc(mapa_ctx ctx, int32_t topo_id, int32_t pattern_i
     const int rc = mapa::noalloc_decide(te->dev, ctx->pattern_args[pattern_id], pattern_id, nreq, reqs_dev, out_dev,
                                         mapa::engine_stream(ctx->engine), &err);
     if (rc != MAPA_OK) return fail(ctx, rc, err);
+    return MAPA_OK;
+}
+
+int mapa_autotune(mapa_ctx ctx, int32_t topo_id, int32_t nreq, const mapa_request *reqs, int32_t *chosen) {
+    if (!ctx) return MAPA_E_INVALID;
+    TopoEntry *te = get_topo(ctx, topo_id);
+    if (!te) return fail(ctx, MAPA_E_INVALID, "unknown topology id");
+    if (nreq < 0 || (nreq > 0 && (!reqs || !chosen))) return fail(ctx, MAPA_E_INVALID, "bad arrays");
+    CTX_CUDA(ctx, cudaSetDevice(ctx->device));
+    std::vector<int32_t> tmp(ctx->pattern_args.size() + 1, 0);
+    std::string err;
+    const int rc = mapa::engine_autotune(ctx->engine, te->dev, ctx->pattern_args, nreq, reqs, tmp.data(), &err);
+    if (rc != MAPA_OK) return fail(ctx, rc, err);
+    for (size_t p = 0; p < ctx->pattern_args.size(); ++p) chosen[p] = tmp[p];
     return MAPA_OK;
 }
 

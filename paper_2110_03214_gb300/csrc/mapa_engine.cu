@@ -222,6 +222,7 @@ Engine *engine_create(int device, uint64_t frontier_cap, std::string *err) {
     if (en->sm_count < 1) en->sm_count = 1;
     if (const char *ov = std::getenv("MAPA_TAIL_DEPTH")) en->tail_override = std::atoi(ov);
     if (const char *ov = std::getenv("MAPA_TAIL_BLOCKS_PER_SM")) en->tail_blocks_per_sm = std::atoi(ov);
+    if (const char *ov = std::getenv("MAPA_GRAPHS")) en->use_graphs = std::atoi(ov) != 0;
     if (cudaStreamCreateWithFlags(&en->own_stream, cudaStreamNonBlocking) != cudaSuccess ||
         cudaMalloc(&en->d_error, sizeof(int32_t)) != cudaSuccess ||
         cudaMalloc(&en->d_stats, kStatWords * sizeof(unsigned long long)) != cudaSuccess ||
@@ -241,6 +242,7 @@ void engine_destroy(Engine *e) {
     if (!e) return;
     cudaSetDevice(e->device);
     if (e->stream) cudaStreamSynchronize(e->stream);
+    e->clear_graphs();
     cudaFree(e->arena);
     cudaFree(e->group_mem);
     cudaFree(e->stage_reqs);
@@ -354,6 +356,7 @@ int plan_layout(Engine *e, int32_t group_size, int k, int T, int W, bool device_
         for (int ell = 0; ell < lay->L; ++ell) off_status[ell] = bump(8ull * (lay->bound[ell] / kTpb + 2));
     const uint64_t ctrl_end = total;
     uint64_t have = e->arena_bytes;
+    if (have < total) e->clear_graphs();  // captured launches point into the old arena
     const int rc = ensure_device(&e->arena, &have, std::max<uint64_t>(total, 1), err);
     if (rc != MAPA_OK) return rc;
     e->arena_bytes = have;
@@ -385,8 +388,10 @@ int plan_layout(Engine *e, int32_t group_size, int k, int T, int W, bool device_
 
 // Fused tail depth of a pattern.  The stored level k - T must hold more than
 // the requests' roots when k >= 2, or one thread would walk a whole request.
-static int tail_depth(const Engine *e, const PatternArgs &p) {
+static int tail_depth(const Engine *e, const TopoDevice &t, const PatternArgs &p) {
     if (e->tail_override > 0) return std::max(1, std::min({e->tail_override, 3, p.k}));
+    const auto it = e->tail_table.find({t.id, p.id});
+    if (it != e->tail_table.end()) return std::max(1, std::min(it->second, p.k));
     return p.k >= 3 ? 2 : 1;
 }
 
@@ -407,6 +412,7 @@ static int group_arrays(Engine *e, int32_t size, GroupArgs *g, std::string *err)
     const uint64_t n = static_cast<uint64_t>(std::max(size, 1));
     const uint64_t bytes = align_up(n * 4, 256) * 4 + align_up(n * 8, 256) * 2 + align_up(n * 32, 256);
     uint64_t have = e->group_bytes;
+    if (have < bytes) e->clear_graphs();
     const int rc = ensure_device(&e->group_mem, &have, bytes, err);
     if (rc != MAPA_OK) return rc;
     e->group_bytes = have;
@@ -426,8 +432,9 @@ static int group_arrays(Engine *e, int32_t size, GroupArgs *g, std::string *err)
     return MAPA_OK;
 }
 
-static int ensure_i32(int32_t **ptr, int32_t *cap, int64_t need, std::string *err) {
+static int ensure_i32(Engine *e, int32_t **ptr, int32_t *cap, int64_t need, std::string *err) {
     uint64_t have = static_cast<uint64_t>(*cap) * 4;
+    if (have < static_cast<uint64_t>(std::max<int64_t>(need, 1)) * 4) e->clear_graphs();
     char *p = reinterpret_cast<char *>(*ptr);
     const int rc = ensure_device(&p, &have, static_cast<uint64_t>(std::max<int64_t>(need, 1)) * 4, err);
     *ptr = reinterpret_cast<int32_t *>(p);
@@ -500,9 +507,9 @@ int engine_run_batch(Engine *e, const TopoDevice &t, const std::vector<PatternAr
         // One request at a time against the device occupancy, committing each.
         rc = group_arrays(e, 1, &g, err);
         if (rc != MAPA_OK) return rc;
-        rc = ensure_i32(&e->order, &e->order_cap, nreq, err);
+        rc = ensure_i32(e, &e->order, &e->order_cap, nreq, err);
         if (rc != MAPA_OK) return rc;
-        rc = ensure_i32(&e->overflow, &e->overflow_cap, 1, err);
+        rc = ensure_i32(e, &e->overflow, &e->overflow_cap, 1, err);
         if (rc != MAPA_OK) return rc;
         std::vector<int32_t> idx(nreq);
         for (int32_t i = 0; i < nreq; ++i) idx[i] = i;
@@ -524,7 +531,7 @@ int engine_run_batch(Engine *e, const TopoDevice &t, const std::vector<PatternAr
                 continue;
             }
             g.req_index = e->order + i;
-            GroupRun gr{&patterns[pid], g, tail_depth(e, patterns[pid]), e->overflow};
+            GroupRun gr{&patterns[pid], g, tail_depth(e, t, patterns[pid]), e->overflow};
             MAPA_CUDA_TRY(cudaMemsetAsync(e->overflow, 0, sizeof(int32_t), e->stream));
             rc = run_group(e, t, gr, true, err);
             if (rc != MAPA_OK) return rc;
@@ -545,9 +552,9 @@ int engine_run_batch(Engine *e, const TopoDevice &t, const std::vector<PatternAr
     }
 
     // Independent requests: group by pattern on the device.
-    rc = ensure_i32(&e->hist, &e->hist_cap, npat + 1, err);
+    rc = ensure_i32(e, &e->hist, &e->hist_cap, npat + 1, err);
     if (rc != MAPA_OK) return rc;
-    rc = ensure_i32(&e->order, &e->order_cap, nreq, err);
+    rc = ensure_i32(e, &e->order, &e->order_cap, nreq, err);
     if (rc != MAPA_OK) return rc;
     MAPA_CUDA_TRY(cudaMemsetAsync(e->hist, 0, sizeof(int32_t) * (npat + 1), e->stream));
     const unsigned hgrid = static_cast<unsigned>(std::min<uint64_t>(ceil_div(nreq, 256), 1024));
@@ -570,16 +577,15 @@ int engine_run_batch(Engine *e, const TopoDevice &t, const std::vector<PatternAr
             gs.size = std::min(kMaxGroup, hist[p] - s0);
             gs.req_index = e->order + start[p] + s0;
             largest = std::max(largest, gs.size);
-            runs.push_back(GroupRun{&patterns[p], gs, tail_depth(e, patterns[p]), nullptr});
+            runs.push_back(GroupRun{&patterns[p], gs, tail_depth(e, t, patterns[p]), nullptr});
         }
     }
     if (runs.empty()) return end_batch(e, err);
     GroupArgs arrays;
     rc = group_arrays(e, largest, &arrays, err);
     if (rc != MAPA_OK) return rc;
-    rc = ensure_i32(&e->overflow, &e->overflow_cap, static_cast<int64_t>(runs.size()), err);
+    rc = ensure_i32(e, &e->overflow, &e->overflow_cap, static_cast<int64_t>(runs.size()), err);
     if (rc != MAPA_OK) return rc;
-    MAPA_CUDA_TRY(cudaMemsetAsync(e->overflow, 0, sizeof(int32_t) * runs.size(), e->stream));
     for (size_t i = 0; i < runs.size(); ++i) {
         GroupRun &gr = runs[i];
         gr.g.alpha = arrays.alpha;
@@ -590,8 +596,82 @@ int engine_run_batch(Engine *e, const TopoDevice &t, const std::vector<PatternAr
         gr.g.count = arrays.count;
         gr.g.best_t = arrays.best_t;
         gr.overflow = e->overflow + i;
-        rc = run_group(e, t, gr, true, err);
+    }
+    // Every group of the batch, device-driven.  A batch whose shape was seen
+    // before (same topology, buffers, per-pattern sizes and tail depths)
+    // replays its captured graph; a new shape is captured, then replayed.
+    auto enqueue_all = [&]() -> int {
+        MAPA_CUDA_TRY(cudaMemsetAsync(e->overflow, 0, sizeof(int32_t) * runs.size(), e->stream));
+        for (size_t i = 0; i < runs.size(); ++i) {
+            const int r = run_group(e, t, runs[i], true, err);
+            if (r != MAPA_OK) return r;
+        }
+        return MAPA_OK;
+    };
+    if (!e->use_graphs || e->timing) {
+        rc = enqueue_all();
         if (rc != MAPA_OK) return rc;
+    } else {
+        std::vector<int64_t> key = {t.id, reinterpret_cast<int64_t>(reqs_dev), reinterpret_cast<int64_t>(out_dev),
+                                    nreq, reinterpret_cast<int64_t>(e->arena), static_cast<int64_t>(e->arena_bytes),
+                                    reinterpret_cast<int64_t>(e->group_mem), reinterpret_cast<int64_t>(e->overflow),
+                                    reinterpret_cast<int64_t>(e->order), reinterpret_cast<int64_t>(e->stream)};
+        for (const GroupRun &gr : runs) {
+            key.push_back(gr.pat->id);
+            key.push_back(gr.g.size);
+            key.push_back(gr.tail);
+            key.push_back(gr.g.req_index - e->order);
+        }
+        auto it = e->graphs.find(key);
+        const bool repeat = it != e->graphs.end() || e->shapes_seen.count(key) > 0;
+        if (!repeat) {
+            // first sighting of this shape: run it directly, capture if it recurs
+            if (e->shapes_seen.size() >= 256) e->shapes_seen.clear();
+            e->shapes_seen[key] = 1;
+            rc = enqueue_all();
+            if (rc != MAPA_OK) return rc;
+        } else if (it == e->graphs.end()) {
+            if (e->graphs.size() >= 32) e->clear_graphs();
+            // plan every group once outside capture so no allocation happens inside it
+            for (const GroupRun &gr : runs) {
+                LayoutPlan lay;
+                rc = plan_layout(e, gr.g.size, gr.pat->k, gr.tail, t.W, true, t.n, &lay, err);
+                if (rc != MAPA_OK) return rc;
+            }
+            const mapa_stats before = e->st;
+            cudaGraph_t graph = nullptr;
+            MAPA_CUDA_TRY(cudaStreamBeginCapture(e->stream, cudaStreamCaptureModeRelaxed));
+            rc = enqueue_all();
+            const cudaError_t ce = cudaStreamEndCapture(e->stream, &graph);
+            if (rc != MAPA_OK) {
+                if (graph) cudaGraphDestroy(graph);
+                return rc;
+            }
+            Engine::GraphEntry entry;
+            cudaError_t ie = ce;
+            if (ce == cudaSuccess) ie = cudaGraphInstantiate(&entry.exec, graph, 0);
+            if (graph) cudaGraphDestroy(graph);
+            const mapa_stats delta_src = e->st;
+            e->st = before;
+            if (ie != cudaSuccess) {
+                // capture not possible here: drop graphs for this context, run directly
+                cudaGetLastError();
+                e->use_graphs = false;
+                rc = enqueue_all();
+                if (rc != MAPA_OK) return rc;
+            } else {
+                entry.delta.kernel_launches = delta_src.kernel_launches - before.kernel_launches;
+                entry.delta.tail_launches = delta_src.tail_launches - before.tail_launches;
+                entry.delta.requests = delta_src.requests - before.requests;
+                it = e->graphs.emplace(key, entry).first;
+            }
+        }
+        if (e->use_graphs && it != e->graphs.end()) {
+            MAPA_CUDA_TRY(cudaGraphLaunch(it->second.exec, e->stream));
+            e->st.kernel_launches += it->second.delta.kernel_launches;
+            e->st.tail_launches += it->second.delta.tail_launches;
+            e->st.requests += it->second.delta.requests;
+        }
     }
     std::vector<int32_t> ovf(runs.size());
     MAPA_CUDA_TRY(cudaMemcpyAsync(ovf.data(), e->overflow, sizeof(int32_t) * runs.size(), cudaMemcpyDeviceToHost,
@@ -625,8 +705,8 @@ int engine_run_chain(Engine *e, const TopoDevice &t, const std::vector<PatternAr
     g.size = 1;
     int rc = begin_batch(e, err);
     if (rc == MAPA_OK) rc = group_arrays(e, 1, &g, err);
-    if (rc == MAPA_OK) rc = ensure_i32(&e->order, &e->order_cap, n, err);
-    if (rc == MAPA_OK) rc = ensure_i32(&e->overflow, &e->overflow_cap, n, err);
+    if (rc == MAPA_OK) rc = ensure_i32(e, &e->order, &e->order_cap, n, err);
+    if (rc == MAPA_OK) rc = ensure_i32(e, &e->overflow, &e->overflow_cap, n, err);
     if (rc != MAPA_OK) return rc;
     std::vector<int32_t> idx(n);
     for (int32_t i = 0; i < n; ++i) idx[i] = i;
@@ -641,7 +721,7 @@ int engine_run_chain(Engine *e, const TopoDevice &t, const std::vector<PatternAr
             return MAPA_E_INVALID;
         }
         g.req_index = e->order + i;
-        GroupRun gr{&patterns[pid], g, tail_depth(e, patterns[pid]), e->overflow + i};
+        GroupRun gr{&patterns[pid], g, tail_depth(e, t, patterns[pid]), e->overflow + i};
         rc = run_group(e, t, gr, true, err);
         if (rc != MAPA_OK) return rc;
         k_commit<<<1, 32, 0, e->stream>>>(out_dev + i, t.occupancy, t.owner, t.next_job,
@@ -677,6 +757,69 @@ int engine_release_many(Engine *e, const TopoDevice &t, const int64_t *jobs_dev,
     MAPA_CUDA_TRY(cudaGetLastError());
     e->st.kernel_launches += 1;
     return MAPA_OK;
+}
+
+int engine_autotune(Engine *e, const TopoDevice &t, const std::vector<PatternArgs> &patterns, int32_t nreq,
+                    const mapa_request *reqs_host, int32_t *chosen, std::string *err) {
+    MAPA_CUDA_TRY(cudaSetDevice(e->device));
+    const int32_t npat = static_cast<int32_t>(patterns.size());
+    for (int32_t p = 0; p < npat; ++p) chosen[p] = 0;
+    if (e->tail_override > 0) {
+        if (err) *err = "the tail depth is fixed by MAPA_TAIL_DEPTH";
+        return MAPA_E_STATE;
+    }
+    std::vector<std::vector<mapa_request>> by_pattern(npat);
+    for (int32_t i = 0; i < nreq; ++i) {
+        const int32_t pid = reqs_host[i].pattern_id;
+        if (pid >= 0 && pid < npat) by_pattern[pid].push_back(reqs_host[i]);
+    }
+    mapa_request *d_reqs = nullptr;
+    mapa_result *d_out = nullptr;
+    int rc = engine_stage(e, std::max(nreq, 1), &d_reqs, &d_out, err);
+    if (rc != MAPA_OK) return rc;
+    cudaEvent_t ev0, ev1;
+    MAPA_CUDA_TRY(cudaEventCreate(&ev0));
+    MAPA_CUDA_TRY(cudaEventCreate(&ev1));
+    const bool timing = e->timing;
+    e->timing = false;
+    const mapa_stats saved = e->st;
+    for (int32_t p = 0; p < npat && rc == MAPA_OK; ++p) {
+        const auto &rs = by_pattern[p];
+        if (rs.empty()) continue;
+        const int32_t n = static_cast<int32_t>(rs.size());
+        rc = cudaMemcpyAsync(d_reqs, rs.data(), sizeof(mapa_request) * n, cudaMemcpyHostToDevice, e->stream) ==
+                     cudaSuccess
+                 ? MAPA_OK
+                 : MAPA_E_CUDA;
+        float best_ms = 0.f;
+        int best_t = 0;
+        for (int T = 1; T <= std::min(3, patterns[p].k) && rc == MAPA_OK; ++T) {
+            e->tail_table[{t.id, p}] = T;
+            float ms_min = 0.f;
+            for (int rep = 0; rep < 2 && rc == MAPA_OK; ++rep) {  // first pass warms the arena and caches
+                cudaEventRecord(ev0, e->stream);
+                rc = engine_run_batch(e, t, patterns, n, d_reqs, d_out, false, err);
+                cudaEventRecord(ev1, e->stream);
+                cudaEventSynchronize(ev1);
+                float ms = 0.f;
+                cudaEventElapsedTime(&ms, ev0, ev1);
+                if (rep == 1 || ms < ms_min) ms_min = ms;
+            }
+            if (rc == MAPA_OK && (best_t == 0 || ms_min < best_ms)) {
+                best_ms = ms_min;
+                best_t = T;
+            }
+        }
+        if (best_t) {
+            e->tail_table[{t.id, p}] = best_t;
+            chosen[p] = best_t;
+        }
+    }
+    e->st = saved;
+    e->timing = timing;
+    cudaEventDestroy(ev0);
+    cudaEventDestroy(ev1);
+    return rc;
 }
 
 int engine_release(Engine *e, const TopoDevice &t, int64_t job_id, int32_t *freed, std::string *err) {

@@ -5,7 +5,9 @@
 #include <cuda_runtime.h>
 
 #include <cstdint>
+#include <map>
 #include <string>
+#include <utility>
 #include <vector>
 
 #include "mapa_internal.h"
@@ -50,6 +52,21 @@ struct Engine {
     bool timing = false;
     int tail_override = 0;  // 0 = automatic tail depth
     int tail_blocks_per_sm = 0;  // 0 = from the occupancy calculator
+    std::map<std::pair<int32_t, int32_t>, int> tail_table;  // (topology, pattern) -> tuned depth
+    // Captured launch sequences of independent batches, keyed by batch shape.
+    bool use_graphs = true;
+    struct GraphEntry {
+        cudaGraphExec_t exec = nullptr;
+        mapa_stats delta{};  // host-side counters the captured launches account for
+    };
+    std::map<std::vector<int64_t>, GraphEntry> graphs;
+    std::map<std::vector<int64_t>, int> shapes_seen;  // shapes run once without a graph
+    void clear_graphs() {
+        for (auto &kv : graphs)
+            if (kv.second.exec) cudaGraphExecDestroy(kv.second.exec);
+        graphs.clear();
+        shapes_seen.clear();
+    }
     std::vector<cudaEvent_t> events;  // pairs around fused last-level launches
     size_t events_used = 0;
 

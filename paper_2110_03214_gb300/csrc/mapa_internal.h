@@ -30,6 +30,7 @@ constexpr int kMaxGroup = 1 << 20;
 // symmetry-breaking constraint phi(j) < phi(i).
 struct PatternArgs {
     int32_t k;
+    int32_t id;  // pattern id in its context (keys the tuned tail depth)
     uint32_t back[kMaxK];
     uint32_t lo[kMaxK];
 };
@@ -94,6 +95,7 @@ void engine_set_stream(Engine *e, cudaStream_t s);
 cudaStream_t engine_stream(Engine *e);
 
 struct TopoDevice {
+    int32_t id = -1;  // topology id in its context
     int32_t n = 0, W = 1, C = 0;
     int64_t total_weight = 0;
     uint32_t *adj = nullptr;
@@ -112,6 +114,12 @@ int engine_run_batch(Engine *e, const TopoDevice &t, const std::vector<PatternAr
                      const mapa_request *reqs_dev, mapa_result *out_dev, bool sequential, std::string *err);
 
 int engine_stats(Engine *e, mapa_stats *out);
+
+// Autotuner: times every fused tail depth for each pattern present in the
+// host batch reqs[0..nreq) and keeps the fastest per (topology, pattern).
+// chosen[p] receives the depth for pattern id p (0 if p is not in the batch).
+int engine_autotune(Engine *e, const TopoDevice &t, const std::vector<PatternArgs> &patterns, int32_t nreq,
+                    const mapa_request *reqs_host, int32_t *chosen, std::string *err);
 void engine_stats_reset(Engine *e);
 void engine_set_timing(Engine *e, bool on);
 

@@ -125,6 +125,7 @@ def _load() -> ctypes.CDLL:
         "mapa_allocate_batch_noalloc": ([vp, i32, i32, i32, vp, vp], ctypes.c_int),
         "mapa_occupancy_get": ([vp, i32, ctypes.POINTER(ctypes.c_uint32)], ctypes.c_int),
         "mapa_stats_get": ([vp, ctypes.POINTER(Stats)], ctypes.c_int),
+        "mapa_autotune": ([vp, i32, i32, vp, i32p], ctypes.c_int),
         "mapa_stats_reset": ([vp], ctypes.c_int),
         "mapa_ctx_set_timing": ([vp, ctypes.c_int], ctypes.c_int),
         "mapa_serve_open": ([vp, i32, i32, u32, ctypes.POINTER(vp)], ctypes.c_int),
@@ -152,7 +153,7 @@ SYMBOLS = (
     "mapa_pattern_load", "mapa_pattern_builtin", "mapa_allocate", "mapa_release", "mapa_allocate_batch",
     "mapa_occupancy_get", "mapa_pattern_analyze", "mapa_version", "mapa_stats_get", "mapa_stats_reset",
     "mapa_ctx_set_timing", "mapa_allocate_batch_noalloc", "mapa_serve_open", "mapa_serve_submit",
-    "mapa_serve_poll", "mapa_serve_drain", "mapa_serve_counters", "mapa_serve_close",
+    "mapa_serve_poll", "mapa_serve_drain", "mapa_serve_counters", "mapa_serve_close", "mapa_autotune",
 )
 
 
@@ -260,6 +261,16 @@ def mapa_occupancy_get(ctx, topo_id: int) -> np.ndarray:
     busy = np.zeros(8, np.uint32)
     _check(ctx, lib.mapa_occupancy_get(ctx, topo_id, busy.ctypes.data_as(ctypes.POINTER(ctypes.c_uint32))))
     return busy
+
+
+def mapa_autotune(ctx, topo_id: int, reqs, num_patterns: int) -> np.ndarray:
+    """Times every fused tail depth per pattern on the host batch `reqs` and
+    keeps the fastest; returns the chosen depth per pattern id (0 = absent)."""
+    reqs = np.ascontiguousarray(reqs, dtype=REQUEST_DTYPE)
+    chosen = np.zeros(max(num_patterns, 1), np.int32)
+    _check(ctx, lib.mapa_autotune(ctx, topo_id, reqs.shape[0], reqs.ctypes.data,
+                                  chosen.ctypes.data_as(ctypes.POINTER(ctypes.c_int32))))
+    return chosen[:num_patterns]
 
 
 def mapa_stats_get(ctx) -> dict:

@@ -271,3 +271,43 @@ def test_device_pointer_batch(M, ctx):
     ctx.allocate_batch_device(tid, len(reqs), dreq.data_ptr(), dout.data_ptr())
     got = dout.cpu().numpy().view(M.RESULT_DTYPE)
     assert np.array_equal(got, host)
+
+
+def test_autotune_keeps_results(M):
+    """The autotuner only changes the fused tail depth, never a result."""
+    wl = W.workload("torus64", num_requests=600)
+    ks = np.asarray([wl.requests.patterns[i].k for i in wl.requests.pattern_index])
+    reqs_w = wl.requests.subset(np.nonzero(ks <= 9)[0][:300])
+    with M.Context(0) as c:
+        tid = c.topology_load(wl.topology)
+        pids = [c.pattern_load(p) for p in reqs_w.patterns]
+        reqs = c.requests(reqs_w, pids)
+        before = c.allocate_batch(tid, reqs)
+        chosen = M.mapa_autotune(c.h, tid, reqs, len(pids))
+        after = c.allocate_batch(tid, reqs)
+    present = set(int(x) for x in reqs["pattern_id"])
+    for p in range(len(pids)):
+        if p in present:
+            assert 1 <= chosen[p] <= min(3, reqs_w.patterns[p].k)
+        else:
+            assert chosen[p] == 0
+    assert np.array_equal(before, after)
+
+
+def test_graph_replay_matches_direct_launches(M, monkeypatch):
+    """A batch shape seen twice is captured as a CUDA graph and replayed;
+    replays give the results of direct launches."""
+    wl = W.workload("regular32", num_requests=2000)
+    monkeypatch.setenv("MAPA_GRAPHS", "0")
+    with M.Context(0) as direct:
+        tid, pids = _load(direct, wl)
+        want = direct.allocate_batch(tid, direct.requests(wl.requests, pids))
+    monkeypatch.setenv("MAPA_GRAPHS", "1")
+    with M.Context(0) as graphed:
+        tid, pids = _load(graphed, wl)
+        reqs = graphed.requests(wl.requests, pids)
+        for _ in range(4):  # run, capture, replay, replay
+            got = graphed.allocate_batch(tid, reqs)
+            assert np.array_equal(got, want)
+        st = graphed.stats()
+    assert st["requests"] == 4 * 2000 and st["kernel_launches"] > 0
