@@ -313,3 +313,180 @@ int oracle_decide(int32_t n, const int32_t *wmat, const uint8_t *busy, int32_t k
     free(s);
     return st;
 }
+
+/* ------------------------------------------------------------------ */
+/* Bounded exact decision: branch and bound over the same lexicographic */
+/* enumeration (the exact argmax and tuple of oracle_decide; no count)  */
+/*
+ * A partial map of pattern vertices 0..i-1 is cut off when an upper bound on
+ * the score of every completion is <= the best score found so far.  In
+ * lexicographic order every later match is lexicographically larger, so a
+ * cut-off subtree can hold neither a larger score nor an earlier tie: the
+ * result equals oracle_decide's.
+ *
+ * The bound (alpha, beta >= 0; otherwise nothing is cut), with U the images
+ * of the m = k - i unplaced pattern vertices and R = F minus the placed
+ * images, follows from writing the final score as the partial score plus,
+ * edge by edge:
+ *   +alpha*w        for a pattern edge from a placed vertex to U,
+ *   (alpha-beta)*w  for a pattern edge inside U,
+ *   -beta*w         for every other link between U and R.
+ * Every weight lies in [wmin, wmax] (the smallest and largest link weights
+ * of G), so
+ *   B1 = alpha*wmax*e_cross + e_in*max((alpha-beta)*wmax, (alpha-beta)*wmin).
+ * Let d_u be the weight of u's links into R.  Summed over u in U, d_u counts
+ * a link inside U twice and a link from U to the rest of R once, and at most
+ * m-1 of u's links stay inside U; so the links between U and R weigh at
+ * least the sum over u in U of g(d_u) = max(d_u/2, d_u - (m-1)*wmax/2),
+ * hence at least half the sum D_m of the m smallest values 2*g(d_u) over all
+ * u in R, and
+ *   B2 = alpha*wmax*(e_cross + e_in) - beta*D_m/2.
+ * Partial score = alpha*agg(placed pattern edges) + beta*W(R), recomputed from
+ * the definitions at every node.  Fewer than m vertices left in R: no
+ * completion.
+ */
+
+typedef struct {
+    match_state ms;
+    int64_t wmax, wmin;
+    uint64_t max_nodes, nodes;
+} bb_state;
+
+static int64_t partial_score(bb_state *b, int32_t i)
+{
+    match_state *s = &b->ms;
+    int64_t agg = 0;
+    for (int32_t e = 0; e < s->m; ++e)
+        if (s->pa[e] < i && s->pb[e] < i) agg += s->wmat[s->phi[s->pa[e]] * s->n + s->phi[s->pb[e]]];
+    return s->alpha * agg + s->beta * preserved_bw(s->n, s->wmat, s->free_v, i, s->phi);
+}
+
+static int cmp_i64(const void *x, const void *y)
+{
+    int64_t a = *(const int64_t *)x, c = *(const int64_t *)y;
+    return (a > c) - (a < c);
+}
+
+/* Returns 1 when no completion of phi[0..i-1] can score above best_score. */
+static int cut_off(bb_state *b, int32_t i)
+{
+    match_state *s = &b->ms;
+    if (!s->have_best || s->alpha < 0 || s->beta < 0) return 0;
+    const int32_t m_left = s->k - i;
+    int64_t e_cross = 0, e_in = 0;
+    for (int32_t e = 0; e < s->m; ++e) {
+        int lo = s->pa[e] < s->pb[e] ? s->pa[e] : s->pb[e];
+        int hi = s->pa[e] < s->pb[e] ? s->pb[e] : s->pa[e];
+        if (lo >= i) e_in += 1;
+        else if (hi >= i) e_cross += 1;
+    }
+    int64_t deg[OR_MAX_N];
+    int32_t r = 0;
+    for (int32_t u = 0; u < s->n; ++u) {
+        if (!s->free_v[u] || s->used[u]) continue;
+        int64_t d = 0;
+        for (int32_t x = 0; x < s->n; ++x)
+            if (x != u && s->free_v[x] && !s->used[x]) d += s->wmat[u * s->n + x];
+        deg[r++] = d;
+    }
+    if (r < m_left) return 1;
+    for (int32_t j = 0; j < r; ++j) {
+        /* 2*g(d) */
+        const int64_t inside = (int64_t)(m_left - 1) * b->wmax;
+        deg[j] = 2 * deg[j] - inside > deg[j] ? 2 * deg[j] - inside : deg[j];
+    }
+    qsort(deg, (size_t)r, sizeof(int64_t), cmp_i64);
+    int64_t dm = 0;
+    for (int32_t j = 0; j < m_left; ++j) dm += deg[j];
+    const int64_t ab = s->alpha - s->beta;
+    const int64_t in_w = ab * b->wmax > ab * b->wmin ? ab * b->wmax : ab * b->wmin;
+    const int64_t b1 = s->alpha * b->wmax * e_cross + e_in * in_w;
+    /* floor(-beta*dm/2) for beta*dm >= 0 */
+    const int64_t b2 = s->alpha * b->wmax * (e_cross + e_in) - (s->beta * dm + 1) / 2;
+    const int64_t ub = partial_score(b, i) + (b1 < b2 ? b1 : b2);
+    return ub <= s->best_score;
+}
+
+static void extend_bb(bb_state *b, int32_t i)
+{
+    match_state *s = &b->ms;
+    if (s->aborted) return;
+    b->nodes += 1;
+    if (b->max_nodes && b->nodes > b->max_nodes) {
+        s->aborted = 1;
+        return;
+    }
+    if (i == s->k) {
+        visit_match(s);
+        return;
+    }
+    if (cut_off(b, i)) return;
+    for (int32_t x = 0; x < s->n; ++x) {
+        if (!s->free_v[x] || s->used[x]) continue;
+        int ok = 1;
+        for (int32_t a = 0; a < i && ok; ++a)
+            if (s->padj[a][i] && s->wmat[s->phi[a] * s->n + x] <= 0) ok = 0;
+        if (!ok) continue;
+        s->used[x] = 1;
+        s->phi[i] = x;
+        extend_bb(b, i + 1);
+        s->used[x] = 0;
+        if (s->aborted) return;
+    }
+}
+
+/* Same result fields as oracle_decide except maps/aut/classes, which stay 0;
+ * out->maps holds the search nodes visited instead.  max_nodes > 0 bounds
+ * the nodes (OR_BUDGET past it). */
+int oracle_decide_bounded(int32_t n, const int32_t *wmat, const uint8_t *busy, int32_t k, int32_t m,
+                          const int32_t *pa, const int32_t *pb, int64_t alpha, int64_t beta, uint64_t max_nodes,
+                          oracle_result *out)
+{
+    memset(out, 0, sizeof(*out));
+    out->k = k;
+    uint8_t padj[OR_MAX_K][OR_MAX_K];
+    if (n < 1 || n > OR_MAX_N || build_pattern(k, m, pa, pb, padj) != OR_OK) {
+        out->status = OR_INVALID;
+        return OR_INVALID;
+    }
+    bb_state *b = (bb_state *)calloc(1, sizeof(bb_state));
+    if (!b) {
+        out->status = OR_INVALID;
+        return OR_INVALID;
+    }
+    match_state *s = &b->ms;
+    s->n = n;
+    s->wmat = wmat;
+    for (int32_t v = 0; v < n; ++v) s->free_v[v] = busy[v] ? 0 : 1;
+    s->k = k;
+    s->m = m;
+    s->pa = pa;
+    s->pb = pb;
+    s->padj = padj;
+    s->alpha = alpha;
+    s->beta = beta;
+    b->wmax = 0;
+    b->wmin = 0;
+    for (int32_t x = 0; x < n * n; ++x) {
+        if (wmat[x] <= 0) continue;
+        if (wmat[x] > b->wmax) b->wmax = wmat[x];
+        if (b->wmin == 0 || wmat[x] < b->wmin) b->wmin = wmat[x];
+    }
+    b->max_nodes = max_nodes;
+    extend_bb(b, 0);
+    out->maps = b->nodes;
+    if (s->aborted) {
+        out->status = OR_BUDGET;
+    } else if (!s->have_best) {
+        out->status = OR_NO_MATCH;
+    } else {
+        out->status = OR_OK;
+        out->score = s->best_score;
+        out->agg = s->best_agg;
+        out->pres = s->best_pres;
+        for (int32_t i = 0; i < k; ++i) out->tuple[i] = (uint8_t)s->best_phi[i];
+    }
+    int32_t st = out->status;
+    free(b);
+    return st;
+}

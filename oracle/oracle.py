@@ -8,7 +8,9 @@ Two independent restatements of the allocation problem of Sec. 3.3-3.5
 (arXiv 2110.03214):
 
 * ``decide`` calls the plain C backtracking oracle in ``mapa_oracle.c``
-  (tier 2: any size it can finish);
+  (tier 2: any size it can finish); ``decide_bounded`` runs the same
+  lexicographic enumeration with branch-and-bound cut-offs (same decision,
+  no count) to reach larger instances;
 * ``brute_force`` is a pure-Python enumeration of every k-permutation of the
   free vertices (tier 1: tiny graphs only), scoring each with Eq. 1 and Eq. 3
   written out again from the paper.
@@ -89,6 +91,8 @@ def load(path: str | None = None):
         lib.oracle_decide.argtypes = [ctypes.c_int32, i32p, u8p, ctypes.c_int32, ctypes.c_int32, i32p, i32p,
                                       ctypes.c_int64, ctypes.c_int64, ctypes.c_uint64, ctypes.POINTER(_Result)]
         lib.oracle_decide.restype = ctypes.c_int
+        lib.oracle_decide_bounded.argtypes = lib.oracle_decide.argtypes
+        lib.oracle_decide_bounded.restype = ctypes.c_int
         if path is None:
             _lib = lib
         return lib
@@ -143,6 +147,19 @@ class Instance:
         self.lib.oracle_decide(self.n, self._wp, busy_p, int(k), len(pa_a), pa_p, pb_p, int(alpha), int(beta),
                                int(max_maps), ctypes.byref(res))
         return Decision(res.status, res.score, res.agg, res.pres, res.maps, res.aut, res.classes,
+                        tuple(res.tuple[:k]) if res.status == STATUS_OK else ())
+
+    def decide_bounded(self, busy, k: int, pa, pb, alpha: int = 1, beta: int = 1, max_nodes: int = 0) -> Decision:
+        """Branch and bound over the same lexicographic enumeration: the same
+        status, score, agg, pres and tuple as ``decide``; ``maps`` holds the
+        search nodes visited and ``aut``/``classes`` stay 0 (no count)."""
+        busy_a, busy_p = _u8(np.asarray(busy, dtype=bool))
+        pa_a, pa_p = _i32(pa)
+        pb_a, pb_p = _i32(pb)
+        res = _Result()
+        self.lib.oracle_decide_bounded(self.n, self._wp, busy_p, int(k), len(pa_a), pa_p, pb_p, int(alpha),
+                                       int(beta), int(max_nodes), ctypes.byref(res))
+        return Decision(res.status, res.score, res.agg, res.pres, res.maps, 0, 0,
                         tuple(res.tuple[:k]) if res.status == STATUS_OK else ())
 
     def score_tuple(self, busy, k: int, pa, pb, alpha: int, beta: int, tup):
