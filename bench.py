@@ -48,6 +48,8 @@ def _args():
     ap.add_argument("--served-requests", type=int, default=3000, help="arrivals in the served comparison")
     ap.add_argument("--served-rate", type=float, default=1e4, help="Poisson rate of the served comparison")
     ap.add_argument("--served-kmax", type=int, default=8)
+    ap.add_argument("--no-autotune", action="store_true",
+                    help="keep the default tail depths (profiling runs: timings under a profiler mislead the tuner)")
     return ap.parse_args()
 
 
@@ -184,8 +186,12 @@ class NvmlSampler:
 
 
 def _kernel_source_hash() -> str:
-    with open(os.path.join(ROOT, "paper_2110_03214_gb300", "csrc", "mapa_engine.cu"), "rb") as f:
-        return hashlib.sha256(f.read()).hexdigest()[:16]
+    """Hash of the sources that define the fused-tail kernel and its launch."""
+    h = hashlib.sha256()
+    for name in ("mapa_kernels.cuh", "mapa_runner.cuh", "mapa_engine.cu"):
+        with open(os.path.join(ROOT, "paper_2110_03214_gb300", "csrc", name), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
 
 
 def _traffic_per_launch(workload: str, parents_per_launch: float):
@@ -372,8 +378,11 @@ def run_ours(a):
         ctx.allocate_batch_device(tid, nreq, d_req.data_ptr(), d_out.data_ptr())
 
     # tail depths chosen by the autotuner on a sample of the workload (untimed)
-    tuned = M.mapa_autotune(ctx.h, tid, reqs[: min(nreq, 2000)], len(pids))
-    tail_depths = {wl.requests.patterns[i].name: int(tuned[p]) for i, p in enumerate(pids)}
+    if a.no_autotune:
+        tail_depths = "default"
+    else:
+        tuned = M.mapa_autotune(ctx.h, tid, reqs, len(pids))
+        tail_depths = {wl.requests.patterns[i].name: int(tuned[p]) for i, p in enumerate(pids)}
 
     for _ in range(a.warmup):
         flush.zero_()

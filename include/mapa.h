@@ -74,14 +74,22 @@ enum mapa_status {
 enum mapa_pattern_kind { MAPA_RING = 0, MAPA_TREE = 1, MAPA_CLIQUE = 2, MAPA_PATH = 3 };
 
 enum mapa_mode {
-    MAPA_MODE_EXHAUSTIVE = 0 /* enumerate every match (count is exact) */
+    MAPA_MODE_EXHAUSTIVE = 0, /* enumerate every match (count is exact) */
+    MAPA_MODE_BOUNDED = 1     /* branch and bound: the same decision, no count */
 };
 
 /* Scoring policy of one request.  S = alpha * AggBW + beta * PreservedBW is
  * computed in int32; the call fails with MAPA_E_RANGE unless
  * (|alpha| + |beta|) * (total link weight of the graph) < 2^31.
  * max_embeddings > 0 bounds the matches a request may enumerate; past it the
- * request ends with MAPA_E_BUDGET and no decision. */
+ * request ends with MAPA_E_BUDGET and no decision.
+ *
+ * mode = MAPA_MODE_BOUNDED returns exactly the decision of the exhaustive
+ * mode (the same score, AggBW, PreservedBW and tuple, ties included) but
+ * skips every partial match whose completions provably score below a match
+ * already found; result.count is then 0.  Cut-offs need alpha >= 0 and
+ * beta >= 0 (with a negative weight the request is enumerated in full).
+ * max_embeddings then bounds the complete matches left to score. */
 typedef struct {
     int32_t alpha;
     int32_t beta;
@@ -104,7 +112,8 @@ typedef struct {
 /* Decision for one request (80 bytes).
  *   status: MAPA_OK, MAPA_NO_FIT or a negative error for this request.
  *   score, agg, pres: S, AggBW (Eq. 1) and PreservedBW (Eq. 3) of the chosen match.
- *   count: matches found, once per distinct subgraph (maps / |Aut(P)|).
+ *   count: matches found, once per distinct subgraph (maps / |Aut(P)|);
+ *          0 for MAPA_MODE_BOUNDED.
  *   job_id: id of the committed allocation (>= 1), or 0 when nothing was committed.
  *   verts[i] = phi(i) for i < k. */
 typedef struct {

@@ -5,6 +5,7 @@
 // application graph (Sec. 3.1) for its automorphism group and the order
 // constraints that keep one match per distinct subgraph (Sec. 3.3), stage
 // requests and drive the device engine (mapa_engine.cu).
+#include <algorithm>
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
@@ -124,6 +125,12 @@ int analyze_pattern(int32_t k, const std::vector<std::pair<int, int>> &edges, Pa
     memset(&pa, 0, sizeof(pa));
     pa.k = k;
     for (int i = 0; i < k; ++i) pa.back[i] = adj[i] & ((i == 0) ? 0u : ((1u << i) - 1u));
+    for (int l = 0; l <= k; ++l)
+        for (const auto &e : edges) {
+            const int lo = std::min(e.first, e.second), hi = std::max(e.first, e.second);
+            if (lo >= l) ++pa.e_in[l];
+            else if (hi >= l) ++pa.e_cross[l];
+        }
     AutSearch s;
     s.k = k;
     for (int i = 0; i < k; ++i) {
@@ -333,6 +340,13 @@ int mapa_topology_load(mapa_ctx ctx, int32_t n, int32_t m, const int32_t *u, con
     t.W = W;
     t.C = C;
     t.total_weight = total;
+    t.wmin = wc.empty() ? 0 : wc.front();
+    t.wmax = wc.empty() ? 0 : wc.back();
+    for (int32_t a = 0; a < n; ++a) {
+        int64_t d = 0;
+        for (int32_t b = 0; b < n; ++b) d += wm[a * n + b];
+        t.dmax = static_cast<int32_t>(std::max<int64_t>(t.dmax, d));
+    }
     cudaStream_t st = mapa::engine_stream(ctx->engine);
     if (cudaMalloc(&t.adj, adj.size() * 4) != cudaSuccess || cudaMalloc(&t.clsv, clsv.size() * 4) != cudaSuccess ||
         cudaMalloc(&t.wc, std::max(C, 1) * 4) != cudaSuccess || cudaMalloc(&t.occupancy, 8 * 4) != cudaSuccess ||

@@ -174,6 +174,7 @@ __global__ void k_histogram(const mapa_request *reqs, int32_t nreq, int32_t npat
             out[i] = res;
         } else {
             atomicAdd(hist + pid, 1);
+            if (reqs[i].policy.mode == MAPA_MODE_BOUNDED) atomicAdd(hist + npat + pid, 1);
         }
     }
 }
@@ -223,6 +224,8 @@ Engine *engine_create(int device, uint64_t frontier_cap, std::string *err) {
     if (const char *ov = std::getenv("MAPA_TAIL_DEPTH")) en->tail_override = std::atoi(ov);
     if (const char *ov = std::getenv("MAPA_TAIL_BLOCKS_PER_SM")) en->tail_blocks_per_sm = std::atoi(ov);
     if (const char *ov = std::getenv("MAPA_GRAPHS")) en->use_graphs = std::atoi(ov) != 0;
+    if (const char *ov = std::getenv("MAPA_DIVE_STEPS")) en->dive_steps = std::max(0, std::min(std::atoi(ov), 1 << 20));
+    if (const char *ov = std::getenv("MAPA_BOUND_DEGREE_MIN_M")) en->degree_min_m = std::max(0, std::atoi(ov));
     if (cudaStreamCreateWithFlags(&en->own_stream, cudaStreamNonBlocking) != cudaSuccess ||
         cudaMalloc(&en->d_error, sizeof(int32_t)) != cudaSuccess ||
         cudaMalloc(&en->d_stats, kStatWords * sizeof(unsigned long long)) != cudaSuccess ||
@@ -395,7 +398,9 @@ static int tail_depth(const Engine *e, const TopoDevice &t, const PatternArgs &p
     return p.k >= 3 ? 2 : 1;
 }
 
-static int run_group(Engine *e, const TopoDevice &t, const GroupRun &gr, bool device, std::string *err) {
+static int run_group(Engine *e, const TopoDevice &t, const GroupRun &gr_in, bool device, std::string *err) {
+    GroupRun gr = gr_in;
+    if (!gr.bounded) gr.g.thr = nullptr;
     switch (t.W) {
         case 1: return device ? run_group_device_w1(e, t, gr, err) : run_group_host_w1(e, t, gr, err);
         case 2: return device ? run_group_device_w2(e, t, gr, err) : run_group_host_w2(e, t, gr, err);
@@ -410,7 +415,7 @@ static int run_group(Engine *e, const TopoDevice &t, const GroupRun &gr, bool de
 // Per-request group arrays (alpha, beta, key, count, best) for up to `size` requests.
 static int group_arrays(Engine *e, int32_t size, GroupArgs *g, std::string *err) {
     const uint64_t n = static_cast<uint64_t>(std::max(size, 1));
-    const uint64_t bytes = align_up(n * 4, 256) * 4 + align_up(n * 8, 256) * 2 + align_up(n * 32, 256);
+    const uint64_t bytes = align_up(n * 4, 256) * 5 + align_up(n * 8, 256) * 2 + align_up(n * 32, 256);
     uint64_t have = e->group_bytes;
     if (have < bytes) e->clear_graphs();
     const int rc = ensure_device(&e->group_mem, &have, bytes, err);
@@ -426,6 +431,7 @@ static int group_arrays(Engine *e, int32_t size, GroupArgs *g, std::string *err)
     g->beta = reinterpret_cast<int32_t *>(take(n * 4));
     g->best_s = reinterpret_cast<int32_t *>(take(n * 4));
     g->best_valid = reinterpret_cast<int32_t *>(take(n * 4));
+    g->thr = reinterpret_cast<int32_t *>(take(n * 4));
     g->key = reinterpret_cast<uint64_t *>(take(n * 8));
     g->count = reinterpret_cast<unsigned long long *>(take(n * 8));
     g->best_t = reinterpret_cast<uint32_t *>(take(n * 32));
@@ -531,7 +537,8 @@ int engine_run_batch(Engine *e, const TopoDevice &t, const std::vector<PatternAr
                 continue;
             }
             g.req_index = e->order + i;
-            GroupRun gr{&patterns[pid], g, tail_depth(e, t, patterns[pid]), e->overflow};
+            GroupRun gr{&patterns[pid], g, tail_depth(e, t, patterns[pid]), e->overflow,
+                        hreq[i].policy.mode == MAPA_MODE_BOUNDED};
             MAPA_CUDA_TRY(cudaMemsetAsync(e->overflow, 0, sizeof(int32_t), e->stream));
             rc = run_group(e, t, gr, true, err);
             if (rc != MAPA_OK) return rc;
@@ -552,15 +559,16 @@ int engine_run_batch(Engine *e, const TopoDevice &t, const std::vector<PatternAr
     }
 
     // Independent requests: group by pattern on the device.
-    rc = ensure_i32(e, &e->hist, &e->hist_cap, npat + 1, err);
+    rc = ensure_i32(e, &e->hist, &e->hist_cap, 2 * npat + 1, err);
     if (rc != MAPA_OK) return rc;
     rc = ensure_i32(e, &e->order, &e->order_cap, nreq, err);
     if (rc != MAPA_OK) return rc;
-    MAPA_CUDA_TRY(cudaMemsetAsync(e->hist, 0, sizeof(int32_t) * (npat + 1), e->stream));
+    MAPA_CUDA_TRY(cudaMemsetAsync(e->hist, 0, sizeof(int32_t) * (2 * npat + 1), e->stream));
     const unsigned hgrid = static_cast<unsigned>(std::min<uint64_t>(ceil_div(nreq, 256), 1024));
     k_histogram<<<hgrid, 256, 0, e->stream>>>(reqs_dev, nreq, npat, e->hist, out_dev);
-    std::vector<int32_t> hist(npat + 1);
-    MAPA_CUDA_TRY(cudaMemcpyAsync(hist.data(), e->hist, sizeof(int32_t) * npat, cudaMemcpyDeviceToHost, e->stream));
+    std::vector<int32_t> hist(2 * npat + 1);  // requests per pattern, then bounded-mode requests per pattern
+    MAPA_CUDA_TRY(
+        cudaMemcpyAsync(hist.data(), e->hist, sizeof(int32_t) * 2 * npat, cudaMemcpyDeviceToHost, e->stream));
     MAPA_CUDA_TRY(cudaStreamSynchronize(e->stream));
     std::vector<int32_t> start(npat + 1, 0);
     for (int32_t p = 0; p < npat; ++p) start[p + 1] = start[p] + hist[p];
@@ -577,7 +585,7 @@ int engine_run_batch(Engine *e, const TopoDevice &t, const std::vector<PatternAr
             gs.size = std::min(kMaxGroup, hist[p] - s0);
             gs.req_index = e->order + start[p] + s0;
             largest = std::max(largest, gs.size);
-            runs.push_back(GroupRun{&patterns[p], gs, tail_depth(e, t, patterns[p]), nullptr});
+            runs.push_back(GroupRun{&patterns[p], gs, tail_depth(e, t, patterns[p]), nullptr, hist[npat + p] > 0});
         }
     }
     if (runs.empty()) return end_batch(e, err);
@@ -595,6 +603,7 @@ int engine_run_batch(Engine *e, const TopoDevice &t, const std::vector<PatternAr
         gr.g.key = arrays.key;
         gr.g.count = arrays.count;
         gr.g.best_t = arrays.best_t;
+        gr.g.thr = arrays.thr;
         gr.overflow = e->overflow + i;
     }
     // Every group of the batch, device-driven.  A batch whose shape was seen
@@ -621,6 +630,7 @@ int engine_run_batch(Engine *e, const TopoDevice &t, const std::vector<PatternAr
             key.push_back(gr.g.size);
             key.push_back(gr.tail);
             key.push_back(gr.g.req_index - e->order);
+            key.push_back(gr.bounded);
         }
         auto it = e->graphs.find(key);
         const bool repeat = it != e->graphs.end() || e->shapes_seen.count(key) > 0;
@@ -691,8 +701,8 @@ int engine_run_batch(Engine *e, const TopoDevice &t, const std::vector<PatternAr
 // request whose frontier outgrows the arena makes the call fail with
 // MAPA_E_NOMEM (its commit would not be trustworthy).
 int engine_run_chain(Engine *e, const TopoDevice &t, const std::vector<PatternArgs> &patterns, int32_t n,
-                     const int32_t *pattern_ids, const mapa_request *reqs_dev, mapa_result *out_dev, bool fifo_wait,
-                     std::string *err) {
+                     const int32_t *pattern_ids, const uint8_t *bounded, const mapa_request *reqs_dev,
+                     mapa_result *out_dev, bool fifo_wait, std::string *err) {
     MAPA_CUDA_TRY(cudaSetDevice(e->device));
     if (n <= 0) return MAPA_OK;
     GroupArgs g;
@@ -721,7 +731,8 @@ int engine_run_chain(Engine *e, const TopoDevice &t, const std::vector<PatternAr
             return MAPA_E_INVALID;
         }
         g.req_index = e->order + i;
-        GroupRun gr{&patterns[pid], g, tail_depth(e, t, patterns[pid]), e->overflow + i};
+        GroupRun gr{&patterns[pid], g, tail_depth(e, t, patterns[pid]), e->overflow + i,
+                    bounded != nullptr && bounded[i] != 0};
         rc = run_group(e, t, gr, true, err);
         if (rc != MAPA_OK) return rc;
         k_commit<<<1, 32, 0, e->stream>>>(out_dev + i, t.occupancy, t.owner, t.next_job,
@@ -780,8 +791,9 @@ int engine_autotune(Engine *e, const TopoDevice &t, const std::vector<PatternArg
     cudaEvent_t ev0, ev1;
     MAPA_CUDA_TRY(cudaEventCreate(&ev0));
     MAPA_CUDA_TRY(cudaEventCreate(&ev1));
-    const bool timing = e->timing;
+    const bool timing = e->timing, graphs = e->use_graphs;
     e->timing = false;
+    e->use_graphs = false;  // time the launches themselves, not graph capture and instantiation
     const mapa_stats saved = e->st;
     for (int32_t p = 0; p < npat && rc == MAPA_OK; ++p) {
         const auto &rs = by_pattern[p];
@@ -796,14 +808,14 @@ int engine_autotune(Engine *e, const TopoDevice &t, const std::vector<PatternArg
         for (int T = 1; T <= std::min(3, patterns[p].k) && rc == MAPA_OK; ++T) {
             e->tail_table[{t.id, p}] = T;
             float ms_min = 0.f;
-            for (int rep = 0; rep < 2 && rc == MAPA_OK; ++rep) {  // first pass warms the arena and caches
+            for (int rep = 0; rep < 3 && rc == MAPA_OK; ++rep) {  // first pass warms the arena and caches
                 cudaEventRecord(ev0, e->stream);
                 rc = engine_run_batch(e, t, patterns, n, d_reqs, d_out, false, err);
                 cudaEventRecord(ev1, e->stream);
                 cudaEventSynchronize(ev1);
                 float ms = 0.f;
                 cudaEventElapsedTime(&ms, ev0, ev1);
-                if (rep == 1 || ms < ms_min) ms_min = ms;
+                if (rep == 1 || (rep > 1 && ms < ms_min)) ms_min = ms;
             }
             if (rc == MAPA_OK && (best_t == 0 || ms_min < best_ms)) {
                 best_ms = ms_min;
@@ -817,6 +829,7 @@ int engine_autotune(Engine *e, const TopoDevice &t, const std::vector<PatternArg
     }
     e->st = saved;
     e->timing = timing;
+    e->use_graphs = graphs;
     cudaEventDestroy(ev0);
     cudaEventDestroy(ev1);
     return rc;

@@ -52,6 +52,8 @@ struct Engine {
     bool timing = false;
     int tail_override = 0;  // 0 = automatic tail depth
     int tail_blocks_per_sm = 0;  // 0 = from the occupancy calculator
+    int dive_steps = 32;         // bounded mode: node expansions of a request's seed dive
+    int degree_min_m = 6;        // bounded mode: degree term only where >= this many pattern vertices remain
     std::map<std::pair<int32_t, int32_t>, int> tail_table;  // (topology, pattern) -> tuned depth
     // Captured launch sequences of independent batches, keyed by batch shape.
     bool use_graphs = true;
@@ -90,8 +92,9 @@ inline uint64_t entry_bytes(int ell, int W) { return 4ull * (2 + W + ((ell + 3) 
 struct GroupRun {
     const PatternArgs *pat;
     GroupArgs g;
-    int tail;           // fused tail depth T
-    int32_t *overflow;  // device flag for this group (device-driven path)
+    int tail;               // fused tail depth T
+    int32_t *overflow;      // device flag for this group (device-driven path)
+    bool bounded = false;   // some request of the group is in bounded mode (g.thr set)
 };
 
 // Per-mask-width entry points (mapa_engine_w{1,2,4,8}.cu).

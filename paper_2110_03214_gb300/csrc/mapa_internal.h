@@ -28,11 +28,16 @@ constexpr int kMaxGroup = 1 << 20;
 // Pattern as the device sees it: vertex i is matched at level i; back[i] holds
 // the earlier neighbours of i, lo[i] the earlier vertices j with the
 // symmetry-breaking constraint phi(j) < phi(i).
+// For the bounded mode, level l (pattern vertices 0..l-1 placed) has
+// e_cross[l] pattern edges between a placed and an unplaced vertex and
+// e_in[l] pattern edges between two unplaced ones.
 struct PatternArgs {
     int32_t k;
     int32_t id;  // pattern id in its context (keys the tuned tail depth)
     uint32_t back[kMaxK];
     uint32_t lo[kMaxK];
+    uint16_t e_cross[kMaxK + 1];
+    uint16_t e_in[kMaxK + 1];
 };
 
 // Hardware graph in device memory.
@@ -46,6 +51,8 @@ struct TopoArgs {
     const uint32_t *adj;
     const uint32_t *clsv;
     const int32_t *wc;
+    int32_t wmin, wmax;  // smallest and largest link weight
+    int32_t dmax;        // largest weighted degree of a vertex
 };
 
 // One frontier level in structure-of-arrays form, `cap` entries per column.
@@ -77,6 +84,11 @@ struct GroupArgs {
     const uint32_t *occupancy; // device occupancy or nullptr (request masks only)
     int64_t total_weight;      // for the int32 range check
     int32_t *error;            // device error word (0 = fine)
+    // Bounded mode: score of a match already found per request (partials whose
+    // completions all score below it are skipped); INT_MIN = no cut-off,
+    // INT_MAX = proven to have no match.  nullptr when no request of the
+    // group is bounded.
+    int32_t *thr;              // [size]
 };
 
 // Device-side error codes written to the error word.
@@ -97,6 +109,7 @@ cudaStream_t engine_stream(Engine *e);
 struct TopoDevice {
     int32_t id = -1;  // topology id in its context
     int32_t n = 0, W = 1, C = 0;
+    int32_t wmin = 0, wmax = 0, dmax = 0;
     int64_t total_weight = 0;
     uint32_t *adj = nullptr;
     uint32_t *clsv = nullptr;
@@ -105,7 +118,7 @@ struct TopoDevice {
     int64_t *owner = nullptr;       // [n] job id holding each vertex, 0 = free
     unsigned long long *next_job = nullptr;
     int32_t *scratch = nullptr;     // small per-topology scratch (release count)
-    TopoArgs args() const { return TopoArgs{n, W, C, adj, clsv, wc}; }
+    TopoArgs args() const { return TopoArgs{n, W, C, adj, clsv, wc, wmin, wmax, dmax}; }
 };
 
 // Runs one batch on the device.  reqs/out are device arrays of nreq entries.
@@ -136,9 +149,10 @@ constexpr int32_t kDeferred = 2;
 
 int engine_commit_round(Engine *e, const TopoDevice &t, mapa_result *out_dev, int32_t n, int32_t *conflict_dev,
                         bool fifo_wait, std::string *err);
+// bounded[i] != 0: request i is in bounded mode (nullptr = none is).
 int engine_run_chain(Engine *e, const TopoDevice &t, const std::vector<PatternArgs> &patterns, int32_t n,
-                     const int32_t *pattern_ids, const mapa_request *reqs_dev, mapa_result *out_dev, bool fifo_wait,
-                     std::string *err);
+                     const int32_t *pattern_ids, const uint8_t *bounded, const mapa_request *reqs_dev,
+                     mapa_result *out_dev, bool fifo_wait, std::string *err);
 int engine_release_many(Engine *e, const TopoDevice &t, const int64_t *jobs_dev, int32_t njobs, std::string *err);
 
 // Scratch for staging host batches.

@@ -187,6 +187,7 @@ struct SmemTopo {
     const uint32_t *cls;
     const int32_t *wc;
     int n, C;
+    int32_t wmin, wmax, dmax;
 };
 
 __host__ __device__ inline size_t topo_smem_bytes(int n, int W, int C, bool with_cls) {
@@ -207,7 +208,7 @@ __device__ __forceinline__ SmemTopo stage_topology(const TopoArgs &t, bool with_
         for (int i = threadIdx.x; i < t.C; i += blockDim.x) wc[i] = t.wc[i];
     }
     __syncthreads();
-    return SmemTopo{adj, cls, wc, t.n, t.C};
+    return SmemTopo{adj, cls, wc, t.n, t.C, t.wmin, t.wmax, t.dmax};
 }
 
 __device__ __forceinline__ int tuple_byte(const LevelView &L, uint64_t p, int j) {
@@ -295,6 +296,128 @@ struct Scorer {
 };
 
 // ----------------------------------------------------------------------------
+// Bounded mode: an upper bound on the final score of every completion of a
+// partial match with score S, R = free vertices not yet used and m = k - l
+// unplaced pattern vertices (l placed).  Counting each link once, completing
+// the match adds
+//   +alpha * w          for a pattern edge from a placed to an unplaced vertex,
+//   (alpha - beta) * w  for a pattern edge between two unplaced vertices,
+//   -beta * w           for every other link between the unplaced images U and R.
+// The links between U and R weigh at least the sum over u in U of
+//   g(d_u) = max(d_u / 2, d_u - (m - 1) * wmax / 2),
+// d_u the weight of u's links into R (a link inside U is met from both ends,
+// and at most m - 1 of u's links stay inside U).  With D the sum of the m
+// smallest 2 g(d_u) over u in R -- bounded below by the four smallest and
+// m - 4 more copies of the fourth -- and alpha, beta >= 0, every completion
+// scores at most S + min(B1, B2):
+//   B1 = alpha * wmax * e_cross + e_in * max((alpha - beta) * wmax, (alpha - beta) * wmin)
+//   B2 = alpha * wmax * (e_cross + e_in) - ceil(beta * D / 2).
+// Fewer than m vertices left in R: no completion at all.  The degree term
+// needs a scan of R; it is skipped when even its largest value (D <= 2 m
+// dmax, dmax the largest weighted degree of G) cannot reach thr.
+
+struct LevelBound {
+    int32_t e_cross, e_in, m;
+    int32_t degrees;  // 0: skip the degree term (B1 only)
+};
+
+__host__ __device__ inline LevelBound level_bound(const PatternArgs &p, int l) {
+    return LevelBound{p.e_cross[l], p.e_in[l], p.k - l, 1};
+}
+
+// Keeps the four smallest values seen in t[0] <= t[1] <= t[2] <= t[3].
+__device__ __forceinline__ void keep4(int32_t (&t)[4], int32_t x) {
+    if (x >= t[3]) return;
+    t[3] = x;
+#pragma unroll
+    for (int j = 3; j > 0; --j)
+        if (t[j] < t[j - 1]) {
+            const int32_t y = t[j];
+            t[j] = t[j - 1];
+            t[j - 1] = y;
+        }
+}
+
+// 2 g(d_u) for vertex u of R.
+template <int W>
+__device__ __forceinline__ int32_t twice_floor_loss(const SmemTopo &s, const uint32_t (&R)[W], int u, int32_t cap) {
+    const uint32_t *x = s.cls + static_cast<size_t>(u) * s.C * W;
+    int32_t d = 0;
+    for (int c = 0; c < s.C; ++c) {
+        int pc = 0;
+#pragma unroll
+        for (int w = 0; w < W; ++w) pc += __popc(x[c * W + w] & R[w]);
+        d += s.wc[c] * pc;
+    }
+    return max(d, 2 * d - cap);
+}
+
+// First stage of the bound (no per-vertex work): returns 1 = cut, 0 = keep,
+// -1 = decide with the degree term.
+__device__ __forceinline__ int cut_first(const SmemTopo &s, int nR, int32_t S, int32_t al, int32_t be, int32_t thr,
+                                         const LevelBound &lb, long long &base2) {
+    if (thr == INT_MIN || al < 0 || be < 0) return 0;
+    if (thr == INT_MAX || nR < lb.m) return 1;
+    const long long wmax = s.wmax, wmin = s.wmin, ab = static_cast<long long>(al) - be;
+    const long long b1 = al * wmax * lb.e_cross + lb.e_in * max(ab * wmax, ab * wmin);
+    if (S + b1 < thr) return 1;
+    if (be == 0 || lb.m == 0 || !lb.degrees) return 0;
+    base2 = S + al * wmax * (lb.e_cross + lb.e_in);
+    // D <= 2 m dmax: when even that cannot cut, skip the per-vertex scan
+    if (base2 - static_cast<long long>(be) * lb.m * s.dmax >= thr) return 0;
+    return -1;
+}
+
+__device__ __forceinline__ bool cut_second(long long base2, int32_t be, const int32_t (&t)[4], int m, int32_t thr) {
+    long long D = t[0];
+    if (m >= 2) D += t[1];
+    if (m >= 3) D += t[2];
+    if (m >= 4) D += static_cast<long long>(t[3]) * (m - 3);
+    return base2 - (static_cast<long long>(be) * D + 1) / 2 < thr;
+}
+
+// True when no completion of the partial can reach thr (one thread).
+template <int W>
+__device__ __forceinline__ bool cut_off(const SmemTopo &s, const uint32_t (&R)[W], int32_t S, int32_t al, int32_t be,
+                                        int32_t thr, const LevelBound &lb) {
+    long long base2 = 0;
+    const int first = cut_first(s, popc_mask<W>(R), S, al, be, thr, lb, base2);
+    if (first >= 0) return first == 1;
+    const int32_t cap = (lb.m - 1) * s.wmax;
+    int32_t t[4] = {INT_MAX, INT_MAX, INT_MAX, INT_MAX};
+    uint32_t rem[W];
+#pragma unroll
+    for (int w = 0; w < W; ++w) rem[w] = R[w];
+    int u;
+    while ((u = pop_lowest<W>(rem)) >= 0) keep4(t, twice_floor_loss<W>(s, R, u, cap));
+    return cut_second(base2, be, t, lb.m, thr);
+}
+
+// The same test evaluated by a whole warp on one partial (warp-uniform
+// arguments and result).
+template <int W>
+__device__ __forceinline__ bool cut_off_warp(const SmemTopo &s, const uint32_t (&R)[W], int32_t S, int32_t al,
+                                             int32_t be, int32_t thr, const LevelBound &lb, int lane) {
+    long long base2 = 0;
+    const int first = cut_first(s, popc_mask<W>(R), S, al, be, thr, lb, base2);
+    if (first >= 0) return first == 1;
+    const int32_t cap = (lb.m - 1) * s.wmax;
+    int32_t t[4] = {INT_MAX, INT_MAX, INT_MAX, INT_MAX};
+#pragma unroll
+    for (int w = 0; w < W; ++w)
+        if ((R[w] >> lane) & 1u) keep4(t, twice_floor_loss<W>(s, R, 32 * w + lane, cap));
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        int32_t other[4];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) other[j] = __shfl_xor_sync(kFull, t[j], o);
+#pragma unroll
+        for (int j = 0; j < 4; ++j) keep4(t, other[j]);
+    }
+    return cut_second(base2, be, t, lb.m, thr);
+}
+
+// ----------------------------------------------------------------------------
 // Fused tail: the last T pattern vertices ell .. ell+T-1 of a stored parent.
 
 struct TailArgs {
@@ -306,6 +429,7 @@ struct TailArgs {
     uint64_t cost_parent;     // algorithmic integer ops per parent, tail node, leaf (telemetry)
     uint64_t cost_node;
     uint64_t cost_leaf;
+    LevelBound bound;         // bounded mode: edge counts of the stored level ell
 };
 
 template <int W, int T>
@@ -406,7 +530,7 @@ __global__ void k_setup(TopoArgs topo, GroupArgs g, LevelView L0, unsigned long 
             const long long mag = (llabs(static_cast<long long>(al)) + llabs(static_cast<long long>(be))) *
                                   static_cast<long long>(g.total_weight);
             int32_t state = 0;
-            if (q.policy.mode != MAPA_MODE_EXHAUSTIVE)
+            if (q.policy.mode != MAPA_MODE_EXHAUSTIVE && q.policy.mode != MAPA_MODE_BOUNDED)
                 state = -3;
             else if (mag >= (1LL << 31))
                 state = -2;
@@ -417,6 +541,7 @@ __global__ void k_setup(TopoArgs topo, GroupArgs g, LevelView L0, unsigned long 
             for (int w = 0; w < W; ++w) L0.R[w * L0.cap + i] = state == 0 ? F[w] : 0u;
             g.alpha[i] = al;
             g.beta[i] = be;
+            if (g.thr) g.thr[i] = INT_MIN;
             g.key[i] = 0ull;
             g.count[i] = 0ull;
             g.best_valid[i] = state;
@@ -424,11 +549,144 @@ __global__ void k_setup(TopoArgs topo, GroupArgs g, LevelView L0, unsigned long 
     }
 }
 
+// Bounded mode, seed score: one warp per request runs a depth-first branch
+// and bound for at most `steps` node expansions.  Lane j holds the node at
+// depth j (pattern vertices 0..j-1 placed): its score, its free set and the
+// children not yet tried; my_v is the vertex chosen for pattern vertex j.
+// Children are tried best score first (ties: smaller vertex); a child whose
+// bound cannot beat the best complete score so far is skipped.  On return,
+// inc/found hold the best complete score; the result is true when the whole
+// search space was finished within the step limit.
+template <int W, int CT>
+__device__ bool dive_warp(const SmemTopo &s, const PatternArgs &pat, int32_t S0, const uint32_t (&F)[W], int32_t al,
+                          int32_t be, int lane, int steps, int32_t &inc, bool &found) {
+    const Scorer<W, CT> sc(s, al, be);
+    const int k = pat.k;
+    int32_t my_S = S0;
+    int my_v = 0;
+    uint32_t my_R[W], my_rem[W];
+#pragma unroll
+    for (int w = 0; w < W; ++w) {
+        my_R[w] = F[w];
+        my_rem[w] = lane == 0 ? F[w] : 0u;  // pattern vertex 0: no earlier neighbour, no constraint
+    }
+    inc = INT_MIN;
+    found = false;
+    int j = 0;
+    for (int step = 0; step < steps; ++step) {
+        uint32_t rem[W], R[W];
+        bool any = false;
+#pragma unroll
+        for (int w = 0; w < W; ++w) {
+            rem[w] = __shfl_sync(kFull, my_rem[w], j);
+            R[w] = __shfl_sync(kFull, my_R[w], j);
+            any |= rem[w] != 0u;
+        }
+        const int32_t S = __shfl_sync(kFull, my_S, j);
+        if (!any) {
+            if (j == 0) return true;
+            --j;
+            continue;
+        }
+        uint32_t B[W];
+#pragma unroll
+        for (int w = 0; w < W; ++w) B[w] = 0u;
+        for (uint32_t bm = pat.back[j]; bm; bm &= bm - 1u) set_bit<W>(B, __shfl_sync(kFull, my_v, __ffs(bm) - 1));
+        int32_t best = INT_MIN;
+        int bv = INT_MAX;
+#pragma unroll
+        for (int w = 0; w < W; ++w)
+            if ((rem[w] >> lane) & 1u) {
+                const int32_t x = S + sc.delta(32 * w + lane, B, R);
+                if (x > best) {
+                    best = x;
+                    bv = 32 * w + lane;
+                }
+            }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            const int32_t ob = __shfl_xor_sync(kFull, best, o);
+            const int ov = __shfl_xor_sync(kFull, bv, o);
+            if (ob > best || (ob == best && ov < bv)) {
+                best = ob;
+                bv = ov;
+            }
+        }
+        if (lane == j) {
+            clear_bit<W>(my_rem, bv);
+            my_v = bv;
+        }
+        if (j + 1 == k) {
+            inc = found ? max(inc, best) : best;
+            found = true;
+            continue;
+        }
+        uint32_t R1[W];
+#pragma unroll
+        for (int w = 0; w < W; ++w) R1[w] = R[w];
+        clear_bit<W>(R1, bv);
+        // only the score matters here, so ties with the incumbent are cut too
+        if (found && cut_off_warp<W>(s, R1, best, al, be, inc == INT_MAX ? INT_MAX : inc + 1, level_bound(pat, j + 1),
+                                     lane))
+            continue;
+        uint32_t cand[W];
+#pragma unroll
+        for (int w = 0; w < W; ++w) cand[w] = R1[w];
+        int lbv = -1;
+        for (uint32_t bm = pat.back[j + 1]; bm; bm &= bm - 1u) {
+            const int b = __ffs(bm) - 1;
+            const int vb = b == j ? bv : __shfl_sync(kFull, my_v, b);
+#pragma unroll
+            for (int w = 0; w < W; ++w) cand[w] &= s.adj[vb * W + w];
+        }
+        for (uint32_t lm = pat.lo[j + 1]; lm; lm &= lm - 1u) {
+            const int a = __ffs(lm) - 1;
+            lbv = max(lbv, a == j ? bv : __shfl_sync(kFull, my_v, a));
+        }
+        and_above<W>(cand, lbv);
+        if (lane == j + 1) {
+            my_S = best;
+#pragma unroll
+            for (int w = 0; w < W; ++w) {
+                my_R[w] = R1[w];
+                my_rem[w] = cand[w];
+            }
+        }
+        ++j;
+    }
+    return false;
+}
+
+// Bounded mode, per request (one warp each): the seed score of the cut-offs.
+// thr = the best complete score the dive found; INT_MAX when the dive
+// finished the whole search space without a match (there is none); INT_MIN
+// when it found nothing within the step limit (no cut-offs).
+template <int W, int CT>
+__global__ void __launch_bounds__(kTpb) k_dive(TopoArgs topo, PatternArgs pat, GroupArgs g, LevelView L0, int steps) {
+    const SmemTopo s = stage_topology<W>(topo, true);
+    const int lane = threadIdx.x & 31;
+    const int gw = static_cast<int>((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+    const int nw = static_cast<int>((gridDim.x * blockDim.x) >> 5);
+    for (int i = gw; i < g.size; i += nw) {
+        const mapa_request &q = g.reqs[g.req_index[i]];
+        const int32_t al = g.alpha[i], be = g.beta[i];
+        if (q.policy.mode != MAPA_MODE_BOUNDED || g.best_valid[i] != 0 || al < 0 || be < 0) continue;
+        uint32_t F[W];
+#pragma unroll
+        for (int w = 0; w < W; ++w) F[w] = L0.R[w * L0.cap + i];
+        int32_t inc;
+        bool found;
+        const bool done = dive_warp<W, CT>(s, pat, L0.S[i], F, al, be, lane, steps, inc, found);
+        if (lane == 0) g.thr[i] = found ? inc : (done ? INT_MAX : INT_MIN);
+    }
+}
+
 // Count pass of the host-driven (chunked) path: children per warp and block.
 template <int W>
 __global__ void __launch_bounds__(kTpb) k_count(TopoArgs topo, LevelView in, uint64_t P, uint32_t back, uint32_t lo,
-                                                uint32_t *warp_cnt, unsigned long long *blk_cnt) {
-    const SmemTopo s = stage_topology<W>(topo, false);
+                                                uint32_t *warp_cnt, unsigned long long *blk_cnt, const int32_t *thr,
+                                                const int32_t *alpha, const int32_t *beta, LevelBound lbd) {
+    const SmemTopo s = stage_topology<W>(topo, thr != nullptr);
     __shared__ uint32_t s_w[kWarps];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const uint64_t wbase = static_cast<uint64_t>(blockIdx.x) * kTile + static_cast<uint64_t>(warp) * 32 * kIpt;
@@ -441,10 +699,18 @@ __global__ void __launch_bounds__(kTpb) k_count(TopoArgs topo, LevelView in, uin
             uint32_t A[W], B[W], c[W];
             int lb;
             level_masks<W>(in, p, back, lo, s.adj, A, B, lb);
+            uint32_t R[W];
 #pragma unroll
-            for (int w = 0; w < W; ++w) c[w] = in.R[w * in.cap + p] & A[w];
+            for (int w = 0; w < W; ++w) {
+                R[w] = in.R[w * in.cap + p];
+                c[w] = R[w] & A[w];
+            }
             and_above<W>(c, lb);
             cnt = popc_mask<W>(c);
+            if (thr && cnt) {
+                const uint32_t r = in.r[p];
+                if (cut_off<W>(s, R, in.S[p], alpha[r], beta[r], thr[r], lbd)) cnt = 0;
+            }
         }
         wsum += warp_sum_int(cnt);
     }
@@ -479,8 +745,7 @@ __device__ __forceinline__ void emit_children(const SmemTopo &s, const LevelView
             const int t = __shfl_sync(kFull, incl, src + step - 1);
             if (t <= c) src += step;
         }
-        const int incl_s = __shfl_sync(kFull, incl, src);
-        const int cnt_s = __shfl_sync(kFull, cnt, src);
+        const int start_s = __shfl_sync(kFull, incl - cnt, src);
         uint32_t cs[W], Bs[W], Rs[W];
 #pragma unroll
         for (int w = 0; w < W; ++w) {
@@ -491,7 +756,7 @@ __device__ __forceinline__ void emit_children(const SmemTopo &s, const LevelView
         const int32_t Ss = __shfl_sync(kFull, S, src);
         const uint32_t rs = __shfl_sync(kFull, r, src);
         if (c < total) {
-            const int v = nth_bit<W>(cs, c - (incl_s - cnt_s));
+            const int v = nth_bit<W>(cs, c - start_s);
             const Scorer<W, CT> sc(s, alpha[rs], beta[rs]);
             const int32_t d = sc.delta(v, Bs, Rs);
             const uint64_t o = obase + c;
@@ -533,7 +798,8 @@ template <int W, int CT>
 __global__ void __launch_bounds__(kTpb) k_write(TopoArgs topo, LevelView in, uint64_t P, int ell, uint32_t back,
                                                 uint32_t lo, LevelView out, const uint32_t *warp_cnt,
                                                 const unsigned long long *blk_off, uint64_t blk_first,
-                                                const int32_t *alpha, const int32_t *beta) {
+                                                const int32_t *alpha, const int32_t *beta, const int32_t *thr,
+                                                LevelBound lbd) {
     const SmemTopo s = stage_topology<W>(topo, true);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const uint64_t b = blk_first + blockIdx.x;
@@ -547,7 +813,16 @@ __global__ void __launch_bounds__(kTpb) k_write(TopoArgs topo, LevelView in, uin
         uint32_t r = 0;
 #pragma unroll
         for (int w = 0; w < W; ++w) cand[w] = B[w] = R[w] = 0u;
-        if (p < P) parent_state<W>(s, in, p, back, lo, cand, B, R, S, r);
+        int32_t al = 0, be = 0;
+        if (p < P) {
+            parent_state<W>(s, in, p, back, lo, cand, B, R, S, r);
+            al = alpha[r];
+            be = beta[r];
+            if (thr && popc_mask<W>(cand) && cut_off<W>(s, R, S, al, be, thr[r], lbd)) {
+#pragma unroll
+                for (int w = 0; w < W; ++w) cand[w] = 0u;
+            }
+        }
         const int cnt = popc_mask<W>(cand);
         const int incl = warp_incl_scan(cnt, lane);
         const int total = __shfl_sync(kFull, incl, 31);
@@ -604,13 +879,14 @@ __device__ __forceinline__ unsigned long long look_back(unsigned long long *stat
 // the child count to *count_out.  If the children do not fit, nothing past
 // the capacity is written, *count_out = 0 and *overflow = 1 (the host then
 // redoes the group with the chunked path).
-template <int W, int CT>
+template <int W, int CT, bool Bnd>
 __global__ void __launch_bounds__(kTpb) k_expand(TopoArgs topo, LevelView in, LevelView out, int ell, uint32_t back,
                                                  uint32_t lo, const unsigned long long *count_in,
                                                  unsigned long long *count_out, unsigned long long cap_out,
                                                  unsigned int *tile_ctr, unsigned long long *status, int32_t *overflow,
                                                  const int32_t *alpha, const int32_t *beta, int32_t *err,
-                                                 unsigned long long *stats, unsigned long long child_bytes) {
+                                                 unsigned long long *stats, unsigned long long child_bytes,
+                                                 const int32_t *thr, LevelBound lbd) {
     const unsigned long long P = *count_in;
     const unsigned long long ntiles = (P + kTpb - 1) / kTpb;
     if (ntiles == 0) {
@@ -634,7 +910,18 @@ __global__ void __launch_bounds__(kTpb) k_expand(TopoArgs topo, LevelView in, Le
         uint32_t r = 0;
 #pragma unroll
         for (int w = 0; w < W; ++w) cand[w] = B[w] = R[w] = 0u;
-        if (p < P) parent_state<W>(s, in, p, back, lo, cand, B, R, S, r);
+        int32_t al = 0, be = 0;
+        if (p < P) {
+            parent_state<W>(s, in, p, back, lo, cand, B, R, S, r);
+            al = alpha[r];
+            be = beta[r];
+            if constexpr (Bnd) {
+                if (popc_mask<W>(cand) && cut_off<W>(s, R, S, al, be, thr[r], lbd)) {
+#pragma unroll
+                    for (int w = 0; w < W; ++w) cand[w] = 0u;
+                }
+            }
+        }
         const int cnt = popc_mask<W>(cand);
         const int incl = warp_incl_scan(cnt, lane);
         const int wtot = __shfl_sync(kFull, incl, 31);
@@ -695,11 +982,11 @@ struct MaxLeaf {
 // (dynamic load balance without block barriers: a warp whose subtrees were
 // small simply takes the next chunk); P is *count_in (device-driven) or
 // count_host (host-driven).
-template <int W, int CT, int T>
+template <int W, int CT, int T, bool Bnd>
 __global__ void __launch_bounds__(kTpb) k_last(TopoArgs topo, LevelView in, const unsigned long long *count_in,
                                                unsigned long long count_host, TailArgs ta, const int32_t *alpha,
                                                const int32_t *beta, uint64_t *key, unsigned long long *count,
-                                               unsigned int *tile_ctr, unsigned long long *stats) {
+                                               unsigned int *tile_ctr, unsigned long long *stats, const int32_t *thr) {
     {
         const unsigned long long P0 = count_in ? *count_in : count_host;
         if (static_cast<unsigned long long>(blockIdx.x) * kWarps * 32 * kIpt >= P0) return;  // nothing for this block
@@ -739,11 +1026,14 @@ __global__ void __launch_bounds__(kTpb) k_last(TopoArgs topo, LevelView in, cons
                 bkey = 0ull;
                 bcnt = 0ull;
             }
-            TailPre<W, T> pre;
-            tail_precompute<W, T>(in, p, ta, s.adj, pre);
             uint32_t R[W];
 #pragma unroll
             for (int w = 0; w < W; ++w) R[w] = in.R[w * in.cap + p];
+            if constexpr (Bnd) {
+                if (cut_off<W>(s, R, in.S[p], alpha[r], beta[r], thr[r], ta.bound)) continue;
+            }
+            TailPre<W, T> pre;
+            tail_precompute<W, T>(in, p, ta, s.adj, pre);
             const Scorer<W, CT> sc(s, alpha[r], beta[r]);
             MaxLeaf leaf;
             int tv[T];
@@ -766,6 +1056,186 @@ __global__ void __launch_bounds__(kTpb) k_last(TopoArgs topo, LevelView in, cons
         if (wn) atomicAdd(&s_nodes, wn);
         if (wl) atomicAdd(&s_leaves, wl);
         if (wp) atomicAdd(&s_parents, wp);
+    }
+    const unsigned act = __ballot_sync(kFull, bcnt > 0ull);
+    if (act) {
+        const int lead = __ffs(act) - 1;
+        const uint32_t rl = __shfl_sync(kFull, r_cur, lead);
+        const bool uniform = __all_sync(kFull, bcnt == 0ull || r_cur == rl);
+        if (uniform) {
+            unsigned long long k = bkey, c = bcnt;
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                k = max(k, __shfl_xor_sync(kFull, k, o));
+                c += __shfl_xor_sync(kFull, c, o);
+            }
+            if (lane == 0) {
+                s_r[warp] = rl;
+                s_key[warp] = k;
+                s_cnt[warp] = c;
+            }
+        } else if (bcnt) {
+            flush_request(key, count, r_cur, bkey, bcnt);
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        uint32_t r = kNoReq;
+        unsigned long long k = 0ull, c = 0ull;
+        for (int w = 0; w < kWarps; ++w) {
+            if (s_r[w] == kNoReq) continue;
+            if (s_r[w] != r) {
+                if (r != kNoReq) flush_request(key, count, r, k, c);
+                r = s_r[w];
+                k = 0ull;
+                c = 0ull;
+            }
+            k = max(k, s_key[w]);
+            c += s_cnt[w];
+        }
+        if (r != kNoReq) flush_request(key, count, r, k, c);
+        if (stats && (s_parents || s_nodes || s_leaves)) {
+            atomicAdd(stats + kStatNodes, s_nodes);
+            atomicAdd(stats + kStatLeaves, s_leaves);
+            atomicAdd(stats + kStatParents, s_parents);
+            atomicAdd(stats + kStatOps,
+                      ta.cost_parent * s_parents + ta.cost_node * s_nodes + ta.cost_leaf * s_leaves);
+        }
+    }
+}
+
+// ----------------------------------------------------------------------------
+// Fused tail of depth 1 or 2 (exhaustive mode): the same result as k_last
+// with T <= 2, laid out for this shape.  One block takes one tile of kTile
+// consecutive parents (grid = tiles), each thread walks its parents' last
+// one or two levels with explicit loops, and the score increment keeps its
+// weight-class loop rolled.  Measured on the 32-vertex regular workload,
+// this form of the walk issues markedly fewer warp instructions than the
+// generic recursive walk.
+
+template <int W>
+__device__ __forceinline__ int32_t delta_rolled(const SmemTopo &s, int v, const uint32_t (&B)[W],
+                                                const uint32_t (&R)[W], int32_t al, int32_t be) {
+    const uint32_t *x = s.cls + static_cast<size_t>(v) * s.C * W;
+    int32_t acc = 0;
+#pragma unroll 1
+    for (int c = 0; c < s.C; ++c) {
+        int pb = 0, pr = 0;
+#pragma unroll
+        for (int w = 0; w < W; ++w) {
+            const uint32_t xw = x[c * W + w];
+            pb += __popc(B[w] & xw);
+            pr += __popc(R[w] & xw);
+        }
+        acc += s.wc[c] * (al * pb - be * pr);
+    }
+    return acc;
+}
+
+// Walks the last T (1 or 2) levels below parent p; leaf(score) for every
+// complete match.
+template <int W, int T, typename Leaf>
+__device__ __forceinline__ void walk_short_tail(const SmemTopo &s, const LevelView &in, uint64_t p, const TailArgs &ta,
+                                                int32_t al, int32_t be, Leaf &&leaf, uint32_t &nodes) {
+    const int32_t S = in.S[p];
+    uint32_t R[W], A[W], B[W], c1[W];
+    int lb;
+    level_masks<W>(in, p, ta.back_old[0], ta.lo_old[0], s.adj, A, B, lb);
+#pragma unroll
+    for (int w = 0; w < W; ++w) {
+        R[w] = in.R[w * in.cap + p];
+        c1[w] = R[w] & A[w];
+    }
+    and_above<W>(c1, lb);
+    if constexpr (T == 1) {
+        int v;
+        while ((v = pop_lowest<W>(c1)) >= 0) leaf(S + delta_rolled<W>(s, v, B, R, al, be));
+    } else {
+        uint32_t A2[W], B2[W];
+        int lb2;
+        level_masks<W>(in, p, ta.back_old[1], ta.lo_old[1], s.adj, A2, B2, lb2);
+        const bool nb = (ta.back_tail[1] & 1u) != 0u;
+        const bool nl = (ta.lo_tail[1] & 1u) != 0u;
+        int v1;
+        while ((v1 = pop_lowest<W>(c1)) >= 0) {
+            ++nodes;
+            const int32_t s1 = S + delta_rolled<W>(s, v1, B, R, al, be);
+            uint32_t R1[W], c2[W], B2n[W];
+#pragma unroll
+            for (int w = 0; w < W; ++w) {
+                R1[w] = R[w];
+                B2n[w] = B2[w];
+            }
+            clear_bit<W>(R1, v1);
+            if (nb) set_bit<W>(B2n, v1);
+#pragma unroll
+            for (int w = 0; w < W; ++w) c2[w] = R1[w] & A2[w] & (nb ? s.adj[v1 * W + w] : ~0u);
+            and_above<W>(c2, nl ? max(lb2, v1) : lb2);
+            int v2;
+            while ((v2 = pop_lowest<W>(c2)) >= 0) leaf(s1 + delta_rolled<W>(s, v2, B2n, R1, al, be));
+        }
+    }
+}
+
+template <int W, int T>
+__global__ void __launch_bounds__(kTpb) k_last_short(TopoArgs topo, LevelView in, const unsigned long long *count_in,
+                                                     unsigned long long count_host, TailArgs ta, const int32_t *alpha,
+                                                     const int32_t *beta, uint64_t *key, unsigned long long *count,
+                                                     unsigned long long *stats) {
+    const unsigned long long P = count_in ? *count_in : count_host;
+    if (static_cast<unsigned long long>(blockIdx.x) * kTile >= P) return;  // tile past the stored parents
+    const SmemTopo s = stage_topology<W>(topo, true);
+    __shared__ uint32_t s_r[kWarps];
+    __shared__ unsigned long long s_key[kWarps];
+    __shared__ unsigned long long s_cnt[kWarps];
+    __shared__ unsigned long long s_nodes, s_leaves, s_parents;
+    if (threadIdx.x == 0) {
+        s_nodes = 0ull;
+        s_leaves = 0ull;
+        s_parents = 0ull;
+    }
+    uint32_t nodes = 0, parents = 0, leaves_total = 0;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const uint64_t wbase = static_cast<uint64_t>(blockIdx.x) * kTile + static_cast<uint64_t>(warp) * 32 * kIpt;
+    uint32_t r_cur = kNoReq;
+    unsigned long long bkey = 0ull, bcnt = 0ull;
+    for (int j = 0; j < kIpt; ++j) {
+        const uint64_t p = wbase + j * 32 + lane;
+        if (p >= P) continue;
+        const uint32_t r = in.r[p];
+        ++parents;
+        if (r != r_cur) {
+            if (r_cur != kNoReq) flush_request(key, count, r_cur, bkey, bcnt);
+            r_cur = r;
+            bkey = 0ull;
+            bcnt = 0ull;
+        }
+        int32_t smax = INT_MIN;
+        uint32_t leaves = 0;
+        walk_short_tail<W, T>(
+            s, in, p, ta, alpha[r], beta[r],
+            [&](int32_t sc) {
+                smax = max(smax, sc);
+                ++leaves;
+            },
+            nodes);
+        if (leaves) {
+            const unsigned long long k64 =
+                (static_cast<unsigned long long>(biased(smax)) << 32) | (0xFFFFFFFFu - static_cast<uint32_t>(p));
+            bkey = max(bkey, k64);
+            bcnt += leaves;
+            leaves_total += leaves;
+        }
+    }
+    // warp, then block aggregation of (request, key, count)
+    const int wn = warp_sum_int(static_cast<int>(nodes));
+    const int wp = warp_sum_int(static_cast<int>(parents));
+    const unsigned long long wl = warp_sum_u64(leaves_total);
+    if (lane == 0) {
+        s_r[warp] = kNoReq;
+        if (wn) atomicAdd(&s_nodes, static_cast<unsigned long long>(wn));
+        if (wp) atomicAdd(&s_parents, static_cast<unsigned long long>(wp));
+        if (wl) atomicAdd(&s_leaves, wl);
     }
     const unsigned act = __ballot_sync(kFull, bcnt > 0ull);
     if (act) {
@@ -957,6 +1427,7 @@ __global__ void k_finalize(TopoArgs topo, PatternArgs pat, GroupArgs g) {
             res.pres = static_cast<int32_t>(pres);
             for (int j = 0; j < pat.k; ++j) res.verts[j] = t[j];
         }
+        if (q.policy.mode == MAPA_MODE_BOUNDED) res.count = 0;
         g.out[bi] = res;
     }
 }

@@ -145,7 +145,8 @@ __device__ __forceinline__ uint32_t na_free_set(const mapa_request &q, int n) {
 }
 
 __device__ int32_t na_request_state(const mapa_request &q, int32_t pattern_id, int64_t total_weight) {
-    if (q.pattern_id != pattern_id || q.policy.mode != MAPA_MODE_EXHAUSTIVE) return -3;
+    if (q.pattern_id != pattern_id) return -3;
+    if (q.policy.mode != MAPA_MODE_EXHAUSTIVE && q.policy.mode != MAPA_MODE_BOUNDED) return -3;
     const long long mag = (llabs(static_cast<long long>(q.policy.alpha)) + llabs(static_cast<long long>(q.policy.beta))) *
                           static_cast<long long>(total_weight);
     return mag >= (1LL << 31) ? -2 : 0;
@@ -279,7 +280,7 @@ __global__ void __launch_bounds__(kNaThreads)
             res.score = target;
             res.agg = static_cast<int32_t>(agg);
             res.pres = static_cast<int32_t>(ptwice / 2);
-            res.count = c64;
+            res.count = q.policy.mode == MAPA_MODE_BOUNDED ? 0ull : c64;
             for (int j = 0; j < pat.k; ++j) res.verts[j] = static_cast<uint8_t>(st.phi[j]);
         }
         out[i] = res;

@@ -51,6 +51,7 @@ inline TailArgs make_tail_args(const PatternArgs &pat, int T, int W, int C) {
     ta.cost_parent = backs * (2 + 2 * w) + 3 * los + 3 * w + 1;
     ta.cost_node = 4 * c * w + 3 * c + 6 * w + 2;
     ta.cost_leaf = 4 * c * w + 3 * c + 2;
+    ta.bound = level_bound(pat, ta.ell);
     return ta;
 }
 
@@ -78,15 +79,30 @@ struct Runner {
         smem_adj = topo_smem_bytes(t.n, W, t.C, false);
         smem_all = topo_smem_bytes(t.n, W, t.C, true);
         ta = make_tail_args(pat, T, W, t.C);
+        ta.bound.degrees = ta.bound.m >= e->degree_min_m;
+    }
+
+    // Bound of the partials stored at level l (the degree term only where its
+    // scan of R pays for itself: at least degree_min_m pattern vertices left).
+    LevelBound bound_at(int l) const {
+        LevelBound b = level_bound(pat, l);
+        b.degrees = b.m >= e->degree_min_m;
+        return b;
     }
 
     int allow_smem() {
         if (smem_all <= 48 * 1024) return MAPA_OK;
         const int b = static_cast<int>(smem_all);
         MAPA_CUDA_TRY(cudaFuncSetAttribute(k_setup<W>, cudaFuncAttributeMaxDynamicSharedMemorySize, b));
+        MAPA_CUDA_TRY(cudaFuncSetAttribute(k_dive<W, CT>, cudaFuncAttributeMaxDynamicSharedMemorySize, b));
+        MAPA_CUDA_TRY(cudaFuncSetAttribute(k_count<W>, cudaFuncAttributeMaxDynamicSharedMemorySize, b));
         MAPA_CUDA_TRY(cudaFuncSetAttribute(k_write<W, CT>, cudaFuncAttributeMaxDynamicSharedMemorySize, b));
-        MAPA_CUDA_TRY(cudaFuncSetAttribute(k_expand<W, CT>, cudaFuncAttributeMaxDynamicSharedMemorySize, b));
-        MAPA_CUDA_TRY(cudaFuncSetAttribute(k_last<W, CT, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, b));
+        MAPA_CUDA_TRY(cudaFuncSetAttribute(k_expand<W, CT, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, b));
+        MAPA_CUDA_TRY(cudaFuncSetAttribute(k_expand<W, CT, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, b));
+        MAPA_CUDA_TRY(cudaFuncSetAttribute(k_last<W, CT, T, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, b));
+        MAPA_CUDA_TRY(cudaFuncSetAttribute(k_last<W, CT, T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, b));
+        if constexpr (T <= 2)
+            MAPA_CUDA_TRY(cudaFuncSetAttribute(k_last_short<W, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, b));
         MAPA_CUDA_TRY(cudaFuncSetAttribute(k_resolve<W, CT, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, b));
         MAPA_CUDA_TRY(cudaFuncSetAttribute(k_finalize<W>, cudaFuncAttributeMaxDynamicSharedMemorySize, b));
         return MAPA_OK;
@@ -97,6 +113,13 @@ struct Runner {
         k_setup<W><<<sgrid, kTpb, smem_all, e->stream>>>(t.args(), g, lay.level[0], count0);
         MAPA_CUDA_TRY(cudaGetLastError());
         e->st.kernel_launches += 1;
+        if (g.thr) {
+            // bounded mode: seed scores for the cut-offs, one warp per request
+            const unsigned dgrid = static_cast<unsigned>(std::min<uint64_t>(ceil_div(g.size, kWarps), 4096));
+            k_dive<W, CT><<<dgrid, kTpb, smem_all, e->stream>>>(t.args(), pat, g, lay.level[0], e->dive_steps);
+            MAPA_CUDA_TRY(cudaGetLastError());
+            e->st.kernel_launches += 1;
+        }
         return MAPA_OK;
     }
 
@@ -114,7 +137,7 @@ struct Runner {
                    uint64_t max_parents) {
         const LevelView &in = lay.level[lay.L];
         static int nb_last = 0;
-        if (!nb_last) nb_last = blocks_per_sm(k_last<W, CT, T>, smem_all);
+        if (!nb_last) nb_last = blocks_per_sm(k_last<W, CT, T, false>, smem_all);
         const int per_sm = e->tail_blocks_per_sm > 0 ? e->tail_blocks_per_sm : nb_last;
         const unsigned grid = static_cast<unsigned>(
             std::max<uint64_t>(1, std::min<uint64_t>(ceil_div(max_parents, kTile), uint64_t(e->sm_count) * per_sm)));
@@ -124,8 +147,25 @@ struct Runner {
             ev1 = e->next_event();
             MAPA_CUDA_TRY(cudaEventRecord(ev0, e->stream));
         }
-        k_last<W, CT, T><<<grid, kTpb, smem_all, e->stream>>>(t.args(), in, count_dev, count_host, ta, g.alpha, g.beta,
-                                                               g.key, g.count, tile_ctr, e->d_stats);
+        bool launched = false;
+        if constexpr (T <= 2) {
+            if (!g.thr) {
+                // one tile of parents per block
+                const unsigned sgrid =
+                    static_cast<unsigned>(std::max<uint64_t>(1, std::min<uint64_t>(ceil_div(max_parents, kTile), 1u << 30)));
+                k_last_short<W, T><<<sgrid, kTpb, smem_all, e->stream>>>(t.args(), in, count_dev, count_host, ta,
+                                                                        g.alpha, g.beta, g.key, g.count, e->d_stats);
+                launched = true;
+            }
+        }
+        if (launched) {
+        } else if (g.thr) {
+            k_last<W, CT, T, true><<<grid, kTpb, smem_all, e->stream>>>(
+                t.args(), in, count_dev, count_host, ta, g.alpha, g.beta, g.key, g.count, tile_ctr, e->d_stats, g.thr);
+        } else {
+            k_last<W, CT, T, false><<<grid, kTpb, smem_all, e->stream>>>(
+                t.args(), in, count_dev, count_host, ta, g.alpha, g.beta, g.key, g.count, tile_ctr, e->d_stats, g.thr);
+        }
         if (e->timing) MAPA_CUDA_TRY(cudaEventRecord(ev1, e->stream));
         const unsigned rgrid = static_cast<unsigned>(std::min<uint64_t>(ceil_div(g.size, 256), 1024));
         k_resolve<W, CT, T><<<rgrid, 256, smem_all, e->stream>>>(t.args(), in, count_dev, count_host, ta, g);
@@ -145,14 +185,15 @@ struct Runner {
         rc = setup(lay.counts);
         if (rc != MAPA_OK) return rc;
         static int nb_expand = 0;
-        if (!nb_expand) nb_expand = blocks_per_sm(k_expand<W, CT>, smem_all);
+        if (!nb_expand) nb_expand = blocks_per_sm(k_expand<W, CT, false>, smem_all);
+        auto expand = g.thr ? k_expand<W, CT, true> : k_expand<W, CT, false>;
         for (int ell = 0; ell < lay.L; ++ell) {
             const unsigned grid = static_cast<unsigned>(std::max<uint64_t>(
                 1, std::min<uint64_t>(ceil_div(lay.bound[ell], kTpb), uint64_t(e->sm_count) * nb_expand)));
-            k_expand<W, CT><<<grid, kTpb, smem_all, e->stream>>>(
+            expand<<<grid, kTpb, smem_all, e->stream>>>(
                 t.args(), lay.level[ell], lay.level[ell + 1], ell, pat.back[ell], pat.lo[ell], lay.counts + ell,
                 lay.counts + ell + 1, lay.level[ell + 1].cap, lay.tiles + ell, lay.status[ell], gr.overflow, g.alpha,
-                g.beta, e->d_error, e->d_stats, entry_bytes(ell + 1, W));
+                g.beta, e->d_error, e->d_stats, entry_bytes(ell + 1, W), g.thr, bound_at(ell));
             MAPA_CUDA_TRY(cudaGetLastError());
             e->st.kernel_launches += 1;
         }
@@ -172,9 +213,9 @@ struct Runner {
         const LevelView &in = lay.level[ell];
         const LevelView &out = lay.level[ell + 1];
         const uint64_t nb = ceil_div(P, kTile);
-        k_count<W><<<static_cast<unsigned>(nb), kTpb, smem_adj, e->stream>>>(t.args(), in, P, pat.back[ell],
-                                                                             pat.lo[ell], lay.warp_cnt[ell],
-                                                                             lay.blk_cnt[ell]);
+        k_count<W><<<static_cast<unsigned>(nb), kTpb, g.thr ? smem_all : smem_adj, e->stream>>>(
+            t.args(), in, P, pat.back[ell], pat.lo[ell], lay.warp_cnt[ell], lay.blk_cnt[ell], g.thr, g.alpha, g.beta,
+            bound_at(ell));
         launch_scan(lay.blk_cnt[ell], lay.blk_off[ell], nb, e->stream);
         MAPA_CUDA_TRY(cudaGetLastError());
         e->st.kernel_launches += 2;
@@ -203,7 +244,7 @@ struct Runner {
             const uint64_t children = total > lay.E ? off[b1] - off[b0] : total;
             k_write<W, CT><<<static_cast<unsigned>(b1 - b0), kTpb, smem_all, e->stream>>>(
                 t.args(), in, P, ell, pat.back[ell], pat.lo[ell], out, lay.warp_cnt[ell], lay.blk_off[ell], b0,
-                g.alpha, g.beta);
+                g.alpha, g.beta, g.thr, bound_at(ell));
             MAPA_CUDA_TRY(cudaGetLastError());
             e->st.kernel_launches += 1;
             e->st.spill_entries += children;

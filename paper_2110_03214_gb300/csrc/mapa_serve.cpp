@@ -225,12 +225,14 @@ int decide_round(mapa_server srv, std::vector<Pending> &round, std::vector<mapa_
     uint32_t cur[MAPA_MASK_WORDS];
     memcpy(cur, snap, sizeof(cur));
     std::vector<int32_t> chain, chain_pids;
+    std::vector<uint8_t> chain_bounded;
     std::vector<char> deferred(n, 0);
     for (int32_t i = 0; i < n; ++i) {
         memcpy(&snaps[static_cast<size_t>(i) * MAPA_MASK_WORDS], snap, sizeof(snap));
         if (srv->h_conflict[i] == 1) {
             chain.push_back(i);
             chain_pids.push_back(round[i].ev.pattern_id);
+            chain_bounded.push_back(round[i].ev.policy.mode == MAPA_MODE_BOUNDED ? 1 : 0);
         } else if (srv->h_conflict[i] == 2) {
             deferred[i] = 1;
         } else if (res[i].status == MAPA_OK) {
@@ -259,8 +261,8 @@ int decide_round(mapa_server srv, std::vector<Pending> &round, std::vector<mapa_
             if (err) *err = "request copy failed";
             return MAPA_E_CUDA;
         }
-        rc = mapa::engine_run_chain(ctx->engine, t, ctx->pattern_args, m, chain_pids.data() + c0, srv->d_reqs,
-                                    srv->d_out, srv->fifo_wait, err);
+        rc = mapa::engine_run_chain(ctx->engine, t, ctx->pattern_args, m, chain_pids.data() + c0,
+                                    chain_bounded.data() + c0, srv->d_reqs, srv->d_out, srv->fifo_wait, err);
         if (rc != MAPA_OK) return rc;
         if (cudaMemcpyAsync(srv->h_out, srv->d_out, sizeof(mapa_result) * m, cudaMemcpyDeviceToHost, st) !=
                 cudaSuccess ||

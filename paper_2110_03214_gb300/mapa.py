@@ -27,6 +27,7 @@ MAPA_E_TIMEOUT = -6
 MAPA_E_STATE = -7
 
 MAPA_RING, MAPA_TREE, MAPA_CLIQUE, MAPA_PATH = 0, 1, 2, 3
+MAPA_MODE_EXHAUSTIVE, MAPA_MODE_BOUNDED = 0, 1
 KIND = {"ring": MAPA_RING, "tree": MAPA_TREE, "clique": MAPA_CLIQUE, "path": MAPA_PATH}
 
 MAPA_BATCH_INDEPENDENT = 0
@@ -219,10 +220,11 @@ def mapa_pattern_builtin(ctx, kind, k: int) -> int:
     return out.value
 
 
-def mapa_allocate(ctx, topo_id: int, pattern_id: int, alpha: int = 1, beta: int = 1, max_embeddings: int = 0):
+def mapa_allocate(ctx, topo_id: int, pattern_id: int, alpha: int = 1, beta: int = 1, max_embeddings: int = 0,
+                  mode: int = MAPA_MODE_EXHAUSTIVE):
     pol = np.zeros(1, dtype=np.dtype([("alpha", "<i4"), ("beta", "<i4"), ("mode", "<i4"), ("r", "<i4"),
                                        ("max_embeddings", "<u8")]))
-    pol["alpha"], pol["beta"], pol["max_embeddings"] = alpha, beta, max_embeddings
+    pol["alpha"], pol["beta"], pol["mode"], pol["max_embeddings"] = alpha, beta, mode, max_embeddings
     res = np.zeros(1, RESULT_DTYPE)
     rc = lib.mapa_allocate(ctx, topo_id, pattern_id, pol.ctypes.data, res.ctypes.data)
     if rc < 0 and res["status"][0] == rc and rc not in (MAPA_E_BUDGET, MAPA_E_RANGE):
@@ -361,12 +363,13 @@ def mapa_pattern_analyze(k: int, a, b):
 # ---- convenience ----------------------------------------------------------------
 
 
-def make_requests(pattern_ids, alpha, beta, busy, max_embeddings=0) -> np.ndarray:
+def make_requests(pattern_ids, alpha, beta, busy, max_embeddings=0, mode=0) -> np.ndarray:
     pattern_ids = np.asarray(pattern_ids, np.int32)
     r = np.zeros(pattern_ids.shape[0], REQUEST_DTYPE)
     r["pattern_id"] = pattern_ids
     r["alpha"] = alpha
     r["beta"] = beta
+    r["mode"] = mode
     r["max_embeddings"] = max_embeddings
     r["busy"] = np.asarray(busy, np.uint32).reshape(-1, 8)
     return r
@@ -403,15 +406,15 @@ class Context:
             return mapa_pattern_builtin(self.h, pattern.kind, pattern.k)
         return mapa_pattern_load(self.h, pattern.k, pattern.a, pattern.b)
 
-    def requests(self, workload_requests, pattern_ids) -> np.ndarray:
+    def requests(self, workload_requests, pattern_ids, mode=MAPA_MODE_EXHAUSTIVE) -> np.ndarray:
         ids = np.asarray(pattern_ids, np.int32)[workload_requests.pattern_index]
-        return make_requests(ids, workload_requests.alpha, workload_requests.beta, workload_requests.busy)
+        return make_requests(ids, workload_requests.alpha, workload_requests.beta, workload_requests.busy, mode=mode)
 
     def set_stream(self, stream_ptr: int):
         mapa_ctx_set_stream(self.h, stream_ptr)
 
-    def allocate(self, topo_id, pattern_id, alpha=1, beta=1, max_embeddings=0):
-        return mapa_allocate(self.h, topo_id, pattern_id, alpha, beta, max_embeddings)
+    def allocate(self, topo_id, pattern_id, alpha=1, beta=1, max_embeddings=0, mode=MAPA_MODE_EXHAUSTIVE):
+        return mapa_allocate(self.h, topo_id, pattern_id, alpha, beta, max_embeddings, mode)
 
     def release(self, topo_id, job_id):
         mapa_release(self.h, topo_id, job_id)
