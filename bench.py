@@ -495,7 +495,7 @@ def run_ours(a):
                        "tail_depths": tail_depths,
                        "parallelism": f"{world} independent shards" if world > 1 else "single GPU",
                        "l2": "flushed between timed steps (256 MiB write)"},
-            "roofline": {"bound": "alu", "kernel": "k_last (fused last two levels: score, count, argmax)",
+            "roofline": {"bound": "alu", "kernel": "k_last_short (fused last two levels: score, count, argmax)",
                          "achieved": achieved_gops, "peak": peak_gops, "unit": "Gop/s",
                          "frac": achieved_gops / peak_gops if peak_gops else None, "traffic": traffic,
                          "peak_source": f"152 SMs x 128 int lanes x {sm_mhz:.0f} MHz ({peak_src} sm_max_mhz)",

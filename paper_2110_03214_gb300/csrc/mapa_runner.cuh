@@ -101,7 +101,7 @@ struct Runner {
         MAPA_CUDA_TRY(cudaFuncSetAttribute(k_expand<W, CT, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, b));
         MAPA_CUDA_TRY(cudaFuncSetAttribute(k_last<W, CT, T, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, b));
         MAPA_CUDA_TRY(cudaFuncSetAttribute(k_last<W, CT, T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, b));
-        if constexpr (T <= 2)
+        if constexpr (T <= 2 && W <= 2)
             MAPA_CUDA_TRY(cudaFuncSetAttribute(k_last_short<W, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, b));
         MAPA_CUDA_TRY(cudaFuncSetAttribute(k_resolve<W, CT, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, b));
         MAPA_CUDA_TRY(cudaFuncSetAttribute(k_finalize<W>, cudaFuncAttributeMaxDynamicSharedMemorySize, b));
@@ -148,9 +148,9 @@ struct Runner {
             MAPA_CUDA_TRY(cudaEventRecord(ev0, e->stream));
         }
         bool launched = false;
-        if constexpr (T <= 2) {
+        if constexpr (T <= 2 && W <= 2) {
             if (!g.thr) {
-                // one tile of parents per block
+                // masks of at most 64 vertices: one tile of parents per block
                 const unsigned sgrid =
                     static_cast<unsigned>(std::max<uint64_t>(1, std::min<uint64_t>(ceil_div(max_parents, kTile), 1u << 30)));
                 k_last_short<W, T><<<sgrid, kTpb, smem_all, e->stream>>>(t.args(), in, count_dev, count_host, ta,
