@@ -43,6 +43,7 @@
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
+#include <math.h>
 
 #define OR_MAX_N 256
 #define OR_MAX_K 32
@@ -485,6 +486,146 @@ int oracle_decide_bounded(int32_t n, const int32_t *wmat, const uint8_t *busy, i
         out->agg = s->best_agg;
         out->pres = s->best_pres;
         for (int32_t i = 0; i < k; ++i) out->tuple[i] = (uint8_t)s->best_phi[i];
+    }
+    int32_t st = out->status;
+    free(b);
+    return st;
+}
+
+/* ------------------------------------------------------------------ */
+/* Bandwidth-sensitive jobs: Predicted Effective Bandwidth (Eq. 2)       */
+/*
+ * Eq. 2 models the effective bandwidth of an allocation from the counts of
+ * its link types: x double NVLinks, y single NVLinks, z PCIe links, with the
+ * fourteen features of Sec. 3.4.3 and the coefficients of Table 2.  Reading:
+ * the counts are taken over the images of the pattern edges (the links the
+ * job's communication uses), a link's type being given by its peak
+ * bandwidth in Table 1: 50 = double NVLink-v2, 25 or 20 = single NVLink
+ * (v2 / v1), 12 = PCIe; links of any other weight count in none of x, y, z.
+ * Algorithm 1 gives a bandwidth-sensitive job the match with the largest
+ * predicted value (first one in lexicographic order among equals).
+ */
+
+double oracle_effbw(int64_t x, int64_t y, int64_t z)
+{
+    static const double theta[15] = {0.0,    16.396, 4.536,  1.556,   -20.694, -9.467, 7.615, -7.973,
+                                      12.733, -4.195, -8.413, 62.851, 27.418,  -5.114, -46.973};
+    const double X = (double)x, Y = (double)y, Z = (double)z;
+    double f = 0.0;
+    f += theta[1] * X + theta[2] * Y + theta[3] * Z;
+    f += theta[4] / (X + 1.0) + theta[5] / (Y + 1.0) + theta[6] / (Z + 1.0);
+    f += theta[7] * X * Y + theta[8] * Y * Z + theta[9] * Z * X;
+    f += theta[10] / (X * Y + 1.0) + theta[11] / (Y * Z + 1.0) + theta[12] / (Z * X + 1.0);
+    f += theta[13] * X * Y * Z + theta[14] / (X * Y * Z + 1.0);
+    return f;
+}
+
+static int link_type(int32_t w)
+{
+    if (w == 50) return 0;            /* double NVLink-v2 */
+    if (w == 25 || w == 20) return 1; /* single NVLink v2 / v1 */
+    if (w == 12) return 2;            /* PCIe */
+    return -1;
+}
+
+typedef struct {
+    match_state ms;
+    double best_f;
+    int64_t best_xyz[3];
+} effbw_state;
+
+static void visit_effbw(effbw_state *b)
+{
+    match_state *s = &b->ms;
+    s->maps += 1;
+    if (s->max_maps && s->maps > s->max_maps) {
+        s->aborted = 1;
+        return;
+    }
+    int64_t c[3] = {0, 0, 0};
+    for (int32_t e = 0; e < s->m; ++e) {
+        const int t = link_type(s->wmat[s->phi[s->pa[e]] * s->n + s->phi[s->pb[e]]]);
+        if (t >= 0) c[t] += 1;
+    }
+    const double f = oracle_effbw(c[0], c[1], c[2]);
+    if (!s->have_best || f > b->best_f) {
+        s->have_best = 1;
+        b->best_f = f;
+        memcpy(b->best_xyz, c, sizeof(c));
+        s->best_agg = aggregated_bw(s->n, s->wmat, s->m, s->pa, s->pb, s->phi);
+        s->best_pres = preserved_bw(s->n, s->wmat, s->free_v, s->k, s->phi);
+        memcpy(s->best_phi, s->phi, sizeof(int32_t) * (size_t)s->k);
+    }
+}
+
+static void extend_effbw(effbw_state *b, int32_t i)
+{
+    match_state *s = &b->ms;
+    if (s->aborted) return;
+    if (i == s->k) {
+        visit_effbw(b);
+        return;
+    }
+    for (int32_t x = 0; x < s->n; ++x) {
+        if (!s->free_v[x] || s->used[x]) continue;
+        int ok = 1;
+        for (int32_t a = 0; a < i && ok; ++a)
+            if (s->padj[a][i] && s->wmat[s->phi[a] * s->n + x] <= 0) ok = 0;
+        if (!ok) continue;
+        s->used[x] = 1;
+        s->phi[i] = x;
+        extend_effbw(b, i + 1);
+        s->used[x] = 0;
+        if (s->aborted) return;
+    }
+}
+
+/* Decision for a bandwidth-sensitive job.  out->score = round(1000 * EffBW)
+ * of the chosen match (milli-GB/s), out->agg / out->pres its AggBW and
+ * PreservedBW, out->classes the matches modulo Aut(P) as in oracle_decide;
+ * xyz_out (may be NULL) receives its link counts. */
+int oracle_decide_effbw(int32_t n, const int32_t *wmat, const uint8_t *busy, int32_t k, int32_t m, const int32_t *pa,
+                        const int32_t *pb, uint64_t max_maps, oracle_result *out, int64_t *xyz_out)
+{
+    memset(out, 0, sizeof(*out));
+    out->k = k;
+    uint8_t padj[OR_MAX_K][OR_MAX_K];
+    if (n < 1 || n > OR_MAX_N || build_pattern(k, m, pa, pb, padj) != OR_OK) {
+        out->status = OR_INVALID;
+        return OR_INVALID;
+    }
+    effbw_state *b = (effbw_state *)calloc(1, sizeof(effbw_state));
+    if (!b) {
+        out->status = OR_INVALID;
+        return OR_INVALID;
+    }
+    match_state *s = &b->ms;
+    s->n = n;
+    s->wmat = wmat;
+    for (int32_t v = 0; v < n; ++v) s->free_v[v] = busy[v] ? 0 : 1;
+    s->k = k;
+    s->m = m;
+    s->pa = pa;
+    s->pb = pb;
+    s->padj = padj;
+    s->max_maps = max_maps;
+    extend_effbw(b, 0);
+    out->maps = s->maps;
+    if (s->have_best && !s->aborted) out->aut = oracle_aut_count(k, m, pa, pb);
+    if (s->aborted) {
+        out->status = OR_BUDGET;
+    } else if (!s->have_best) {
+        out->status = OR_NO_MATCH;
+    } else if (out->aut == 0 || s->maps % out->aut != 0) {
+        out->status = OR_NOT_DIVISIBLE;
+    } else {
+        out->status = OR_OK;
+        out->classes = s->maps / out->aut;
+        out->score = llround(1000.0 * b->best_f);
+        out->agg = s->best_agg;
+        out->pres = s->best_pres;
+        for (int32_t i = 0; i < k; ++i) out->tuple[i] = (uint8_t)s->best_phi[i];
+        if (xyz_out) memcpy(xyz_out, b->best_xyz, sizeof(b->best_xyz));
     }
     int32_t st = out->status;
     free(b);

@@ -65,7 +65,7 @@ def build(force: bool = False, extra_flags: tuple = (), out: str | None = None) 
     target = out or _LIB
     os.makedirs(os.path.dirname(target), exist_ok=True)
     if force or not os.path.exists(target) or os.path.getmtime(target) < os.path.getmtime(_SRC):
-        cmd = ["gcc", "-O2", "-std=c11", "-shared", "-fPIC", *extra_flags, "-o", target + ".tmp", _SRC]
+        cmd = ["gcc", "-O2", "-std=c11", "-shared", "-fPIC", *extra_flags, "-o", target + ".tmp", _SRC, "-lm"]
         subprocess.check_call(cmd)
         os.replace(target + ".tmp", target)
     return target
@@ -93,6 +93,11 @@ def load(path: str | None = None):
         lib.oracle_decide.restype = ctypes.c_int
         lib.oracle_decide_bounded.argtypes = lib.oracle_decide.argtypes
         lib.oracle_decide_bounded.restype = ctypes.c_int
+        lib.oracle_effbw.argtypes = [ctypes.c_int64, ctypes.c_int64, ctypes.c_int64]
+        lib.oracle_effbw.restype = ctypes.c_double
+        lib.oracle_decide_effbw.argtypes = [ctypes.c_int32, i32p, u8p, ctypes.c_int32, ctypes.c_int32, i32p, i32p,
+                                            ctypes.c_uint64, ctypes.POINTER(_Result), i64p]
+        lib.oracle_decide_effbw.restype = ctypes.c_int
         if path is None:
             _lib = lib
         return lib
@@ -162,6 +167,21 @@ class Instance:
         return Decision(res.status, res.score, res.agg, res.pres, res.maps, 0, 0,
                         tuple(res.tuple[:k]) if res.status == STATUS_OK else ())
 
+    def decide_effbw(self, busy, k: int, pa, pb, max_maps: int = 0):
+        """Decision for a bandwidth-sensitive job (Algorithm 1's first branch):
+        the match with the largest Predicted EffBW (Eq. 2).  ``score`` is
+        round(1000 * EffBW); returns (Decision, (x, y, z))."""
+        busy_a, busy_p = _u8(np.asarray(busy, dtype=bool))
+        pa_a, pa_p = _i32(pa)
+        pb_a, pb_p = _i32(pb)
+        res = _Result()
+        xyz = (ctypes.c_int64 * 3)()
+        self.lib.oracle_decide_effbw(self.n, self._wp, busy_p, int(k), len(pa_a), pa_p, pb_p, int(max_maps),
+                                     ctypes.byref(res), xyz)
+        dec = Decision(res.status, res.score, res.agg, res.pres, res.maps, res.aut, res.classes,
+                       tuple(res.tuple[:k]) if res.status == STATUS_OK else ())
+        return dec, tuple(int(v) for v in xyz)
+
     def score_tuple(self, busy, k: int, pa, pb, alpha: int, beta: int, tup):
         """(status, agg, pres, score) of one given tuple; status 0 when it is a match."""
         busy_a, busy_p = _u8(np.asarray(busy, dtype=bool))
@@ -172,6 +192,12 @@ class Instance:
         st = self.lib.oracle_score_tuple(self.n, self._wp, busy_p, int(k), len(pa_a), pa_p, pb_p, int(alpha),
                                          int(beta), t_p, ctypes.byref(agg), ctypes.byref(pres), ctypes.byref(score))
         return st, agg.value, pres.value, score.value
+
+
+def effbw(x: int, y: int, z: int, lib=None) -> float:
+    """Predicted Effective Bandwidth (Eq. 2, Table 2) of link counts (x, y, z)."""
+    lib = lib or load()
+    return float(lib.oracle_effbw(int(x), int(y), int(z)))
 
 
 def aut_count(k: int, pa, pb, lib=None) -> int:
