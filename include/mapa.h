@@ -89,12 +89,28 @@ enum mapa_mode {
  * skips every partial match whose completions provably score below a match
  * already found; result.count is then 0.  Cut-offs need alpha >= 0 and
  * beta >= 0 (with a negative weight the request is enumerated in full).
- * max_embeddings then bounds the complete matches left to score. */
+ * max_embeddings then bounds the complete matches left to score.
+ *
+ * flags & MAPA_POLICY_BW_SENSITIVE selects the first branch of Algorithm 1
+ * (a bandwidth-sensitive job): the chosen match maximises the Predicted
+ * Effective Bandwidth of Eq. 2 (Sec. 3.4.3, coefficients of Table 2) instead
+ * of S; alpha and beta are ignored.  Its link counts x, y, z are taken over
+ * the images of the pattern edges, a link's type following its weight as a
+ * peak bandwidth (Table 1): 50 = double NVLink, 25 or 20 = single NVLink,
+ * 12 = PCIe; links of other weights count in none.  Ties go to the
+ * lexicographically smallest tuple.  result.score is then round(1000 *
+ * EffBW) (milli-GB/s; a value exactly on a half milli-GB/s, which the
+ * three-decimal coefficients allow, may round either way); agg, pres and
+ * count keep their meaning.  Patterns
+ * with more than 63 edges fail with MAPA_E_RANGE.  The bounded mode makes
+ * no cut-offs for such a request. */
+enum mapa_policy_flags { MAPA_POLICY_BW_SENSITIVE = 1u };
+
 typedef struct {
     int32_t alpha;
     int32_t beta;
     int32_t mode;
-    int32_t reserved;
+    uint32_t flags; /* mapa_policy_flags */
     uint64_t max_embeddings;
 } mapa_policy; /* 24 bytes */
 
@@ -305,8 +321,9 @@ int mapa_serve_close(mapa_server srv);
  * reqs_dev and out_dev are device pointers to nreq entries; every request
  * must carry pattern_id and is decided on its own busy mask exactly as
  * mapa_allocate_batch with MAPA_BATCH_INDEPENDENT decides it (same status,
- * score, AggBW, PreservedBW, count and tuple).  A request with another
- * pattern id gets MAPA_E_INVALID.
+ * score, AggBW, PreservedBW, count and tuple; count is 0 in bounded mode).
+ * A request with another pattern id, or a bandwidth-sensitive one, gets
+ * MAPA_E_INVALID.
  * Limits: nreq <= 4096, the topology has at most 32 vertices, the pattern at
  * most 8; beyond them the call returns MAPA_E_RANGE and launches nothing.
  * The first call on a device resolves the scratch array's device address
@@ -367,6 +384,12 @@ int mapa_occupancy_get(mapa_ctx ctx, int32_t topo_id, uint32_t *busy_out);
  * smallest.  Arrays hold k entries.  Returns MAPA_OK or an error. */
 int mapa_pattern_analyze(int32_t k, int32_t m, const int32_t *a, const int32_t *b, uint64_t *aut_order,
                          uint32_t *back_masks, uint32_t *lo_masks);
+
+/* Host-only: the Predicted Effective Bandwidth (Eq. 2, coefficients of
+ * Table 2) of an allocation with x double NVLinks, y single NVLinks and z
+ * PCIe links, in GB/s, as the library ranks bandwidth-sensitive matches.
+ * Returns MAPA_E_RANGE unless 0 <= x, y, z <= 63. */
+int mapa_effbw_predict(int32_t x, int32_t y, int32_t z, double *out);
 
 /* Library version string. */
 const char *mapa_version(void);

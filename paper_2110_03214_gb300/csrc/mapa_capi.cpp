@@ -246,6 +246,7 @@ void free_topo(mapa::TopoDevice &t) {
     cudaFree(t.owner);
     cudaFree(t.next_job);
     cudaFree(t.scratch);
+    cudaFree(t.wc_effbw);
     t = mapa::TopoDevice();
 }
 
@@ -352,13 +353,16 @@ int mapa_topology_load(mapa_ctx ctx, int32_t n, int32_t m, const int32_t *u, con
         cudaMalloc(&t.wc, std::max(C, 1) * 4) != cudaSuccess || cudaMalloc(&t.occupancy, 8 * 4) != cudaSuccess ||
         cudaMalloc(&t.owner, n * sizeof(int64_t)) != cudaSuccess ||
         cudaMalloc(&t.next_job, sizeof(unsigned long long)) != cudaSuccess ||
-        cudaMalloc(&t.scratch, 64) != cudaSuccess) {
+        cudaMalloc(&t.scratch, 64) != cudaSuccess || cudaMalloc(&t.wc_effbw, std::max(C, 1) * 4) != cudaSuccess) {
         free_topo(t);
         return fail(ctx, MAPA_E_NOMEM, "cannot allocate topology on the device");
     }
+    std::vector<int32_t> codes(wc.size());
+    for (size_t c = 0; c < wc.size(); ++c) codes[c] = mapa::effbw_class_code(wc[c]);
     CTX_CUDA(ctx, cudaMemcpyAsync(t.adj, adj.data(), adj.size() * 4, cudaMemcpyHostToDevice, st));
     CTX_CUDA(ctx, cudaMemcpyAsync(t.clsv, clsv.data(), clsv.size() * 4, cudaMemcpyHostToDevice, st));
     if (C > 0) CTX_CUDA(ctx, cudaMemcpyAsync(t.wc, wc.data(), C * 4, cudaMemcpyHostToDevice, st));
+    if (C > 0) CTX_CUDA(ctx, cudaMemcpyAsync(t.wc_effbw, codes.data(), C * 4, cudaMemcpyHostToDevice, st));
     CTX_CUDA(ctx, cudaMemsetAsync(t.occupancy, 0, 8 * 4, st));
     CTX_CUDA(ctx, cudaMemsetAsync(t.owner, 0, n * sizeof(int64_t), st));
     CTX_CUDA(ctx, cudaMemsetAsync(t.next_job, 0, sizeof(unsigned long long), st));

@@ -163,7 +163,14 @@ __global__ void k_release_many(int n, const int64_t *jobs, int32_t njobs, uint32
     }
 }
 
-// Group requests by pattern: histogram, then scatter into per-pattern runs.
+// Group key of a request: its pattern, and whether it is bandwidth-sensitive
+// (scored by Eq. 2) -- npat * 2 keys.
+__device__ __forceinline__ int32_t group_key(const mapa_request &q, int32_t npat) {
+    return q.pattern_id + ((q.policy.flags & MAPA_POLICY_BW_SENSITIVE) ? npat : 0);
+}
+
+// Group requests by key: histogram (hist[key], then bounded-mode requests at
+// hist[2 npat + key]), then scatter into per-key runs.
 __global__ void k_histogram(const mapa_request *reqs, int32_t nreq, int32_t npat, int32_t *hist, mapa_result *out) {
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nreq; i += gridDim.x * blockDim.x) {
         const int32_t pid = reqs[i].pattern_id;
@@ -173,8 +180,9 @@ __global__ void k_histogram(const mapa_request *reqs, int32_t nreq, int32_t npat
             res.status = MAPA_E_INVALID;
             out[i] = res;
         } else {
-            atomicAdd(hist + pid, 1);
-            if (reqs[i].policy.mode == MAPA_MODE_BOUNDED) atomicAdd(hist + npat + pid, 1);
+            const int32_t key = group_key(reqs[i], npat);
+            atomicAdd(hist + key, 1);
+            if (reqs[i].policy.mode == MAPA_MODE_BOUNDED) atomicAdd(hist + 2 * npat + key, 1);
         }
     }
 }
@@ -183,7 +191,7 @@ __global__ void k_scatter(const mapa_request *reqs, int32_t nreq, int32_t npat, 
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nreq; i += gridDim.x * blockDim.x) {
         const int32_t pid = reqs[i].pattern_id;
         if (pid < 0 || pid >= npat) continue;
-        order[atomicAdd(cursor + pid, 1)] = i;
+        order[atomicAdd(cursor + group_key(reqs[i], npat), 1)] = i;
     }
 }
 
@@ -256,6 +264,8 @@ void engine_destroy(Engine *e) {
     cudaFree(e->d_error);
     cudaFree(e->d_stats);
     cudaFree(e->d_blocked);
+    cudaFree(e->effbw_rank);
+    cudaFree(e->effbw_milli);
     for (cudaEvent_t ev : e->events) cudaEventDestroy(ev);
     if (e->h_pinned) cudaFreeHost(e->h_pinned);
     if (e->own_stream) cudaStreamDestroy(e->own_stream);
@@ -398,8 +408,36 @@ static int tail_depth(const Engine *e, const TopoDevice &t, const PatternArgs &p
     return p.k >= 3 ? 2 : 1;
 }
 
+static int ensure_effbw(Engine *e, std::string *err) {
+    if (e->effbw_rank) return MAPA_OK;
+    std::vector<int32_t> rank, milli;
+    effbw_tables(&rank, &milli);
+    const size_t bytes = rank.size() * sizeof(int32_t);
+    MAPA_CUDA_TRY(cudaMalloc(&e->effbw_rank, bytes));
+    MAPA_CUDA_TRY(cudaMalloc(&e->effbw_milli, bytes));
+    MAPA_CUDA_TRY(cudaMemcpyAsync(e->effbw_rank, rank.data(), bytes, cudaMemcpyHostToDevice, e->stream));
+    MAPA_CUDA_TRY(cudaMemcpyAsync(e->effbw_milli, milli.data(), bytes, cudaMemcpyHostToDevice, e->stream));
+    MAPA_CUDA_TRY(cudaStreamSynchronize(e->stream));
+    return MAPA_OK;
+}
+
 static int run_group(Engine *e, const TopoDevice &t, const GroupRun &gr_in, bool device, std::string *err) {
     GroupRun gr = gr_in;
+    gr.g.sens = 0;
+    if (gr.sens) {
+        // Eq. 2 ranks replace the score: no cut-offs, tail depth 1
+        const int rc = ensure_effbw(e, err);
+        if (rc != MAPA_OK) return rc;
+        gr.bounded = false;
+        gr.tail = 1;
+        int edges = 0;
+        for (int v = 0; v < gr.pat->k; ++v) edges += __builtin_popcount(gr.pat->back[v]);
+        gr.g.sens = 1;
+        gr.g.sens_ok = edges < kEffbwRadix;
+        gr.g.effbw_rank = e->effbw_rank;
+        gr.g.effbw_milli = e->effbw_milli;
+        gr.g.effbw_code = t.wc_effbw;
+    }
     if (!gr.bounded) gr.g.thr = nullptr;
     switch (t.W) {
         case 1: return device ? run_group_device_w1(e, t, gr, err) : run_group_host_w1(e, t, gr, err);
@@ -538,7 +576,8 @@ int engine_run_batch(Engine *e, const TopoDevice &t, const std::vector<PatternAr
             }
             g.req_index = e->order + i;
             GroupRun gr{&patterns[pid], g, tail_depth(e, t, patterns[pid]), e->overflow,
-                        hreq[i].policy.mode == MAPA_MODE_BOUNDED};
+                        hreq[i].policy.mode == MAPA_MODE_BOUNDED,
+                        (hreq[i].policy.flags & MAPA_POLICY_BW_SENSITIVE) != 0};
             MAPA_CUDA_TRY(cudaMemsetAsync(e->overflow, 0, sizeof(int32_t), e->stream));
             rc = run_group(e, t, gr, true, err);
             if (rc != MAPA_OK) return rc;
@@ -558,34 +597,38 @@ int engine_run_batch(Engine *e, const TopoDevice &t, const std::vector<PatternAr
         return end_batch(e, err);
     }
 
-    // Independent requests: group by pattern on the device.
-    rc = ensure_i32(e, &e->hist, &e->hist_cap, 2 * npat + 1, err);
+    // Independent requests: group by (pattern, sensitivity) on the device.
+    const int32_t nkey = 2 * npat;
+    rc = ensure_i32(e, &e->hist, &e->hist_cap, 2 * nkey + 1, err);
     if (rc != MAPA_OK) return rc;
     rc = ensure_i32(e, &e->order, &e->order_cap, nreq, err);
     if (rc != MAPA_OK) return rc;
-    MAPA_CUDA_TRY(cudaMemsetAsync(e->hist, 0, sizeof(int32_t) * (2 * npat + 1), e->stream));
+    MAPA_CUDA_TRY(cudaMemsetAsync(e->hist, 0, sizeof(int32_t) * (2 * nkey + 1), e->stream));
     const unsigned hgrid = static_cast<unsigned>(std::min<uint64_t>(ceil_div(nreq, 256), 1024));
     k_histogram<<<hgrid, 256, 0, e->stream>>>(reqs_dev, nreq, npat, e->hist, out_dev);
-    std::vector<int32_t> hist(2 * npat + 1);  // requests per pattern, then bounded-mode requests per pattern
+    std::vector<int32_t> hist(2 * nkey + 1);  // requests per key, then bounded-mode requests per key
     MAPA_CUDA_TRY(
-        cudaMemcpyAsync(hist.data(), e->hist, sizeof(int32_t) * 2 * npat, cudaMemcpyDeviceToHost, e->stream));
+        cudaMemcpyAsync(hist.data(), e->hist, sizeof(int32_t) * 2 * nkey, cudaMemcpyDeviceToHost, e->stream));
     MAPA_CUDA_TRY(cudaStreamSynchronize(e->stream));
-    std::vector<int32_t> start(npat + 1, 0);
-    for (int32_t p = 0; p < npat; ++p) start[p + 1] = start[p] + hist[p];
-    MAPA_CUDA_TRY(cudaMemcpyAsync(e->hist, start.data(), sizeof(int32_t) * npat, cudaMemcpyHostToDevice, e->stream));
+    std::vector<int32_t> start(nkey + 1, 0);
+    for (int32_t p = 0; p < nkey; ++p) start[p + 1] = start[p] + hist[p];
+    MAPA_CUDA_TRY(cudaMemcpyAsync(e->hist, start.data(), sizeof(int32_t) * nkey, cudaMemcpyHostToDevice, e->stream));
     k_scatter<<<hgrid, 256, 0, e->stream>>>(reqs_dev, nreq, npat, e->hist, e->order);
     MAPA_CUDA_TRY(cudaGetLastError());
     e->st.kernel_launches += 2;
 
     std::vector<GroupRun> runs;
     int32_t largest = 0;
-    for (int32_t p = 0; p < npat; ++p) {
-        for (int32_t s0 = 0; s0 < hist[p]; s0 += kMaxGroup) {
+    for (int32_t key = 0; key < nkey; ++key) {
+        const int32_t p = key % npat;
+        const bool sens = key >= npat;
+        for (int32_t s0 = 0; s0 < hist[key]; s0 += kMaxGroup) {
             GroupArgs gs = g;
-            gs.size = std::min(kMaxGroup, hist[p] - s0);
-            gs.req_index = e->order + start[p] + s0;
+            gs.size = std::min(kMaxGroup, hist[key] - s0);
+            gs.req_index = e->order + start[key] + s0;
             largest = std::max(largest, gs.size);
-            runs.push_back(GroupRun{&patterns[p], gs, tail_depth(e, t, patterns[p]), nullptr, hist[npat + p] > 0});
+            runs.push_back(GroupRun{&patterns[p], gs, tail_depth(e, t, patterns[p]), nullptr,
+                                    hist[nkey + key] > 0, sens});
         }
     }
     if (runs.empty()) return end_batch(e, err);
@@ -631,6 +674,7 @@ int engine_run_batch(Engine *e, const TopoDevice &t, const std::vector<PatternAr
             key.push_back(gr.tail);
             key.push_back(gr.g.req_index - e->order);
             key.push_back(gr.bounded);
+            key.push_back(gr.sens);
         }
         auto it = e->graphs.find(key);
         const bool repeat = it != e->graphs.end() || e->shapes_seen.count(key) > 0;
@@ -701,7 +745,7 @@ int engine_run_batch(Engine *e, const TopoDevice &t, const std::vector<PatternAr
 // request whose frontier outgrows the arena makes the call fail with
 // MAPA_E_NOMEM (its commit would not be trustworthy).
 int engine_run_chain(Engine *e, const TopoDevice &t, const std::vector<PatternArgs> &patterns, int32_t n,
-                     const int32_t *pattern_ids, const uint8_t *bounded, const mapa_request *reqs_dev,
+                     const int32_t *pattern_ids, const uint8_t *kinds, const mapa_request *reqs_dev,
                      mapa_result *out_dev, bool fifo_wait, std::string *err) {
     MAPA_CUDA_TRY(cudaSetDevice(e->device));
     if (n <= 0) return MAPA_OK;
@@ -732,7 +776,8 @@ int engine_run_chain(Engine *e, const TopoDevice &t, const std::vector<PatternAr
         }
         g.req_index = e->order + i;
         GroupRun gr{&patterns[pid], g, tail_depth(e, t, patterns[pid]), e->overflow + i,
-                    bounded != nullptr && bounded[i] != 0};
+                    kinds != nullptr && (kinds[i] & kKindBounded) != 0,
+                    kinds != nullptr && (kinds[i] & kKindSensitive) != 0};
         rc = run_group(e, t, gr, true, err);
         if (rc != MAPA_OK) return rc;
         k_commit<<<1, 32, 0, e->stream>>>(out_dev + i, t.occupancy, t.owner, t.next_job,

@@ -47,6 +47,8 @@ struct Engine {
     int32_t *d_error = nullptr;
     unsigned long long *d_stats = nullptr;  // kStatWords counters of the current batch
     int32_t *d_blocked = nullptr;           // FIFO-wait flag of a commit chain
+    int32_t *effbw_rank = nullptr;          // [kEffbwRadix^3] (built on first use)
+    int32_t *effbw_milli = nullptr;
     unsigned long long *h_pinned = nullptr;  // small pinned scratch
     mapa_stats st{};
     bool timing = false;
@@ -95,6 +97,7 @@ struct GroupRun {
     int tail;               // fused tail depth T
     int32_t *overflow;      // device flag for this group (device-driven path)
     bool bounded = false;   // some request of the group is in bounded mode (g.thr set)
+    bool sens = false;      // the group's requests are bandwidth-sensitive
 };
 
 // Per-mask-width entry points (mapa_engine_w{1,2,4,8}.cu).

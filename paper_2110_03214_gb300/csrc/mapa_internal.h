@@ -89,7 +89,22 @@ struct GroupArgs {
     // INT_MAX = proven to have no match.  nullptr when no request of the
     // group is bounded.
     int32_t *thr;              // [size]
+    // Bandwidth-sensitive group (Algorithm 1, first branch): scores are the
+    // link-count index (x * R + y) * R + z of the match, ranked through
+    // effbw_rank; sens_ok = 0 when the pattern has more edges than R - 1.
+    int32_t sens;
+    int32_t sens_ok;
+    const int32_t *effbw_rank;   // [R^3] dense rank of Eq. 2 at each index
+    const int32_t *effbw_milli;  // [R^3] round(1000 * EffBW)
+    const int32_t *effbw_code;   // [C] index weight of each link class
 };
+
+// Bandwidth-sensitive scoring (mapa_effbw.cpp): link counts per type below
+// kEffbwRadix, indexed (x * R + y) * R + z.
+constexpr int kEffbwRadix = 64;
+double effbw_predict(int x, int y, int z);
+int32_t effbw_class_code(int32_t weight);
+void effbw_tables(std::vector<int32_t> *rank, std::vector<int32_t> *milli);
 
 // Device-side error codes written to the error word.
 enum DeviceError : int32_t {
@@ -118,7 +133,10 @@ struct TopoDevice {
     int64_t *owner = nullptr;       // [n] job id holding each vertex, 0 = free
     unsigned long long *next_job = nullptr;
     int32_t *scratch = nullptr;     // small per-topology scratch (release count)
+    int32_t *wc_effbw = nullptr;    // [C] effbw_class_code of each class weight
     TopoArgs args() const { return TopoArgs{n, W, C, adj, clsv, wc, wmin, wmax, dmax}; }
+    // The same graph with the class weights replaced by the link-count codes.
+    TopoArgs args_effbw() const { return TopoArgs{n, W, C, adj, clsv, wc_effbw, 0, 0, 0}; }
 };
 
 // Runs one batch on the device.  reqs/out are device arrays of nreq entries.
@@ -149,9 +167,11 @@ constexpr int32_t kDeferred = 2;
 
 int engine_commit_round(Engine *e, const TopoDevice &t, mapa_result *out_dev, int32_t n, int32_t *conflict_dev,
                         bool fifo_wait, std::string *err);
-// bounded[i] != 0: request i is in bounded mode (nullptr = none is).
+// kinds[i]: bit 0 = request i is in bounded mode, bit 1 = bandwidth-sensitive
+// (nullptr = neither, for every request).
+constexpr uint8_t kKindBounded = 1, kKindSensitive = 2;
 int engine_run_chain(Engine *e, const TopoDevice &t, const std::vector<PatternArgs> &patterns, int32_t n,
-                     const int32_t *pattern_ids, const uint8_t *bounded, const mapa_request *reqs_dev,
+                     const int32_t *pattern_ids, const uint8_t *kinds, const mapa_request *reqs_dev,
                      mapa_result *out_dev, bool fifo_wait, std::string *err);
 int engine_release_many(Engine *e, const TopoDevice &t, const int64_t *jobs_dev, int32_t njobs, std::string *err);
 

@@ -526,13 +526,15 @@ __global__ void k_setup(TopoArgs topo, GroupArgs g, LevelView L0, unsigned long 
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(kFull, acc, o);
         if (lane == 0) {
-            const int32_t al = q.policy.alpha, be = q.policy.beta;
+            // a bandwidth-sensitive group scores link-count indices: alpha 1 on
+            // the class codes, no preserved-bandwidth term
+            const int32_t al = g.sens ? 1 : q.policy.alpha, be = g.sens ? 0 : q.policy.beta;
             const long long mag = (llabs(static_cast<long long>(al)) + llabs(static_cast<long long>(be))) *
                                   static_cast<long long>(g.total_weight);
             int32_t state = 0;
             if (q.policy.mode != MAPA_MODE_EXHAUSTIVE && q.policy.mode != MAPA_MODE_BOUNDED)
                 state = -3;
-            else if (mag >= (1LL << 31))
+            else if (g.sens ? !g.sens_ok : mag >= (1LL << 31))
                 state = -2;
             const long long wfree = acc / 2;
             L0.S[i] = state == 0 ? static_cast<int32_t>(be * wfree) : 0;
@@ -1177,11 +1179,13 @@ __device__ __forceinline__ void walk_short_tail(const SmemTopo &s, const LevelVi
     }
 }
 
-template <int W, int T>
+// Sens: the scores are link-count indices of bandwidth-sensitive requests
+// and the argmax is taken over their Eq. 2 ranks lut[score].
+template <int W, int T, bool Sens>
 __global__ void __launch_bounds__(kTpb) k_last_short(TopoArgs topo, LevelView in, const unsigned long long *count_in,
                                                      unsigned long long count_host, TailArgs ta, const int32_t *alpha,
                                                      const int32_t *beta, uint64_t *key, unsigned long long *count,
-                                                     unsigned long long *stats) {
+                                                     unsigned long long *stats, const int32_t *lut) {
     const unsigned long long P = count_in ? *count_in : count_host;
     if (static_cast<unsigned long long>(blockIdx.x) * kTile >= P) return;  // tile past the stored parents
     const SmemTopo s = stage_topology<W>(topo, true);
@@ -1215,6 +1219,7 @@ __global__ void __launch_bounds__(kTpb) k_last_short(TopoArgs topo, LevelView in
         walk_short_tail<W, T>(
             s, in, p, ta, alpha[r], beta[r],
             [&](int32_t sc) {
+                if constexpr (Sens) sc = lut[sc];
                 smax = max(smax, sc);
                 ++leaves;
             },
@@ -1287,10 +1292,12 @@ __global__ void __launch_bounds__(kTpb) k_last_short(TopoArgs topo, LevelView in
 template <int T>
 struct FindLeaf {
     int32_t target;
+    const int32_t *lut;  // bandwidth-sensitive group: compare Eq. 2 ranks
     bool found = false;
     int tail[T];
     __device__ __forceinline__ void add(int) {}
     __device__ __forceinline__ bool visit(int32_t sc, const int (&tv)[T], int v) {
+        if (lut) sc = lut[sc];
         if (sc != target) return true;
         found = true;
 #pragma unroll
@@ -1327,6 +1334,7 @@ __global__ void k_resolve(TopoArgs topo, LevelView in, const unsigned long long 
         const Scorer<W, CT> sc(s, g.alpha[r], g.beta[r]);
         FindLeaf<T> leaf;
         leaf.target = target;
+        leaf.lut = g.sens ? g.effbw_rank : nullptr;
         int tv[T];
         uint32_t nodes = 0;
         tail_walk<W, CT, T, 0>(s, sc, ta, pre, R, in.S[p], tv, leaf, nodes);
@@ -1352,6 +1360,13 @@ __global__ void k_resolve(TopoArgs topo, LevelView in, const unsigned long long 
             for (int jw = 0; jw < 8; ++jw) g.best_t[static_cast<uint64_t>(r) * 8 + jw] = words[jw];
         }
     }
+}
+
+__device__ __forceinline__ int link_class(const SmemTopo &s, int W, int x, int y) {
+    const uint32_t *row = s.cls + static_cast<size_t>(x) * s.C * W;
+    for (int c = 0; c < s.C; ++c)
+        if ((row[c * W + (y >> 5)] >> (y & 31)) & 1u) return c;
+    return -1;
 }
 
 __device__ __forceinline__ int32_t link_weight(const SmemTopo &s, int W, int x, int y) {
@@ -1418,11 +1433,24 @@ __global__ void k_finalize(TopoArgs topo, PatternArgs pat, GroupArgs g) {
                 }
             }
             const long long pres = twice / 2;
-            const long long score =
-                static_cast<long long>(g.alpha[i]) * agg + static_cast<long long>(g.beta[i]) * pres;
-            if (score != g.best_s[i]) atomicExch(g.error, kDevScoreMismatch);
             res.status = MAPA_OK;
-            res.score = g.best_s[i];
+            if (g.sens) {
+                // link-count index of the tuple from the class of every pattern
+                // edge's link; its Eq. 2 rank must be the one the tail chose
+                int32_t idx = 0;
+                for (int v = 0; v < pat.k; ++v)
+                    for (uint32_t m = pat.back[v]; m; m &= m - 1u) {
+                        const int c = link_class(s, W, t[__ffs(m) - 1], t[v]);
+                        if (c >= 0) idx += g.effbw_code[c];
+                    }
+                if (g.effbw_rank[idx] != g.best_s[i]) atomicExch(g.error, kDevScoreMismatch);
+                res.score = g.effbw_milli[idx];
+            } else {
+                const long long score =
+                    static_cast<long long>(g.alpha[i]) * agg + static_cast<long long>(g.beta[i]) * pres;
+                if (score != g.best_s[i]) atomicExch(g.error, kDevScoreMismatch);
+                res.score = g.best_s[i];
+            }
             res.agg = static_cast<int32_t>(agg);
             res.pres = static_cast<int32_t>(pres);
             for (int j = 0; j < pat.k; ++j) res.verts[j] = t[j];

@@ -145,7 +145,7 @@ __device__ __forceinline__ uint32_t na_free_set(const mapa_request &q, int n) {
 }
 
 __device__ int32_t na_request_state(const mapa_request &q, int32_t pattern_id, int64_t total_weight) {
-    if (q.pattern_id != pattern_id) return -3;
+    if (q.pattern_id != pattern_id || (q.policy.flags & MAPA_POLICY_BW_SENSITIVE)) return -3;
     if (q.policy.mode != MAPA_MODE_EXHAUSTIVE && q.policy.mode != MAPA_MODE_BOUNDED) return -3;
     const long long mag = (llabs(static_cast<long long>(q.policy.alpha)) + llabs(static_cast<long long>(q.policy.beta))) *
                           static_cast<long long>(total_weight);

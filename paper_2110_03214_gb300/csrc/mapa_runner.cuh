@@ -69,13 +69,14 @@ struct Runner {
     const GroupRun &gr;
     const PatternArgs &pat;
     GroupArgs g;
+    TopoArgs targs;  // the graph as the scoring kernels see it (class codes for a sensitive group)
     LayoutPlan lay;
     TailArgs ta;
     size_t smem_adj, smem_all;
     std::string *err;
 
     Runner(Engine *e_, const TopoDevice &t_, const GroupRun &gr_, std::string *err_)
-        : e(e_), t(t_), gr(gr_), pat(*gr_.pat), g(gr_.g), err(err_) {
+        : e(e_), t(t_), gr(gr_), pat(*gr_.pat), g(gr_.g), targs(gr_.sens ? t_.args_effbw() : t_.args()), err(err_) {
         smem_adj = topo_smem_bytes(t.n, W, t.C, false);
         smem_all = topo_smem_bytes(t.n, W, t.C, true);
         ta = make_tail_args(pat, T, W, t.C);
@@ -102,7 +103,11 @@ struct Runner {
         MAPA_CUDA_TRY(cudaFuncSetAttribute(k_last<W, CT, T, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, b));
         MAPA_CUDA_TRY(cudaFuncSetAttribute(k_last<W, CT, T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, b));
         if constexpr (T <= 2 && W <= 2)
-            MAPA_CUDA_TRY(cudaFuncSetAttribute(k_last_short<W, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, b));
+            MAPA_CUDA_TRY(
+                cudaFuncSetAttribute(k_last_short<W, T, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, b));
+        if constexpr (T == 1)
+            MAPA_CUDA_TRY(
+                cudaFuncSetAttribute(k_last_short<W, 1, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, b));
         MAPA_CUDA_TRY(cudaFuncSetAttribute(k_resolve<W, CT, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, b));
         MAPA_CUDA_TRY(cudaFuncSetAttribute(k_finalize<W>, cudaFuncAttributeMaxDynamicSharedMemorySize, b));
         return MAPA_OK;
@@ -110,13 +115,13 @@ struct Runner {
 
     int setup(unsigned long long *count0) {
         const unsigned sgrid = static_cast<unsigned>(std::min<uint64_t>(ceil_div(g.size, kWarps), 4096));
-        k_setup<W><<<sgrid, kTpb, smem_all, e->stream>>>(t.args(), g, lay.level[0], count0);
+        k_setup<W><<<sgrid, kTpb, smem_all, e->stream>>>(targs, g, lay.level[0], count0);
         MAPA_CUDA_TRY(cudaGetLastError());
         e->st.kernel_launches += 1;
         if (g.thr) {
             // bounded mode: seed scores for the cut-offs, one warp per request
             const unsigned dgrid = static_cast<unsigned>(std::min<uint64_t>(ceil_div(g.size, kWarps), 4096));
-            k_dive<W, CT><<<dgrid, kTpb, smem_all, e->stream>>>(t.args(), pat, g, lay.level[0], e->dive_steps);
+            k_dive<W, CT><<<dgrid, kTpb, smem_all, e->stream>>>(targs, pat, g, lay.level[0], e->dive_steps);
             MAPA_CUDA_TRY(cudaGetLastError());
             e->st.kernel_launches += 1;
         }
@@ -125,7 +130,7 @@ struct Runner {
 
     int finalize() {
         const unsigned fgrid = static_cast<unsigned>(std::min<uint64_t>(ceil_div(g.size, 128), 4096));
-        k_finalize<W><<<fgrid, 128, smem_all, e->stream>>>(t.args(), pat, g);
+        k_finalize<W><<<fgrid, 128, smem_all, e->stream>>>(t.args(), pat, g);  // real weights: AggBW, PreservedBW
         MAPA_CUDA_TRY(cudaGetLastError());
         e->st.kernel_launches += 1;
         e->st.requests += static_cast<uint64_t>(g.size);
@@ -148,27 +153,35 @@ struct Runner {
             MAPA_CUDA_TRY(cudaEventRecord(ev0, e->stream));
         }
         bool launched = false;
+        const unsigned sgrid =
+            static_cast<unsigned>(std::max<uint64_t>(1, std::min<uint64_t>(ceil_div(max_parents, kTile), 1u << 30)));
+        if constexpr (T == 1) {
+            if (g.sens) {
+                // bandwidth-sensitive group: argmax over Eq. 2 ranks
+                k_last_short<W, 1, true><<<sgrid, kTpb, smem_all, e->stream>>>(
+                    targs, in, count_dev, count_host, ta, g.alpha, g.beta, g.key, g.count, e->d_stats, g.effbw_rank);
+                launched = true;
+            }
+        }
         if constexpr (T <= 2 && W <= 2) {
-            if (!g.thr) {
+            if (!g.thr && !launched) {
                 // masks of at most 64 vertices: one tile of parents per block
-                const unsigned sgrid =
-                    static_cast<unsigned>(std::max<uint64_t>(1, std::min<uint64_t>(ceil_div(max_parents, kTile), 1u << 30)));
-                k_last_short<W, T><<<sgrid, kTpb, smem_all, e->stream>>>(t.args(), in, count_dev, count_host, ta,
-                                                                        g.alpha, g.beta, g.key, g.count, e->d_stats);
+                k_last_short<W, T, false><<<sgrid, kTpb, smem_all, e->stream>>>(
+                    targs, in, count_dev, count_host, ta, g.alpha, g.beta, g.key, g.count, e->d_stats, nullptr);
                 launched = true;
             }
         }
         if (launched) {
         } else if (g.thr) {
             k_last<W, CT, T, true><<<grid, kTpb, smem_all, e->stream>>>(
-                t.args(), in, count_dev, count_host, ta, g.alpha, g.beta, g.key, g.count, tile_ctr, e->d_stats, g.thr);
+                targs, in, count_dev, count_host, ta, g.alpha, g.beta, g.key, g.count, tile_ctr, e->d_stats, g.thr);
         } else {
             k_last<W, CT, T, false><<<grid, kTpb, smem_all, e->stream>>>(
-                t.args(), in, count_dev, count_host, ta, g.alpha, g.beta, g.key, g.count, tile_ctr, e->d_stats, g.thr);
+                targs, in, count_dev, count_host, ta, g.alpha, g.beta, g.key, g.count, tile_ctr, e->d_stats, g.thr);
         }
         if (e->timing) MAPA_CUDA_TRY(cudaEventRecord(ev1, e->stream));
         const unsigned rgrid = static_cast<unsigned>(std::min<uint64_t>(ceil_div(g.size, 256), 1024));
-        k_resolve<W, CT, T><<<rgrid, 256, smem_all, e->stream>>>(t.args(), in, count_dev, count_host, ta, g);
+        k_resolve<W, CT, T><<<rgrid, 256, smem_all, e->stream>>>(targs, in, count_dev, count_host, ta, g);
         MAPA_CUDA_TRY(cudaGetLastError());
         e->st.kernel_launches += 2;
         e->st.tail_launches += 1;
@@ -191,7 +204,7 @@ struct Runner {
             const unsigned grid = static_cast<unsigned>(std::max<uint64_t>(
                 1, std::min<uint64_t>(ceil_div(lay.bound[ell], kTpb), uint64_t(e->sm_count) * nb_expand)));
             expand<<<grid, kTpb, smem_all, e->stream>>>(
-                t.args(), lay.level[ell], lay.level[ell + 1], ell, pat.back[ell], pat.lo[ell], lay.counts + ell,
+                targs, lay.level[ell], lay.level[ell + 1], ell, pat.back[ell], pat.lo[ell], lay.counts + ell,
                 lay.counts + ell + 1, lay.level[ell + 1].cap, lay.tiles + ell, lay.status[ell], gr.overflow, g.alpha,
                 g.beta, e->d_error, e->d_stats, entry_bytes(ell + 1, W), g.thr, bound_at(ell));
             MAPA_CUDA_TRY(cudaGetLastError());
@@ -214,7 +227,7 @@ struct Runner {
         const LevelView &out = lay.level[ell + 1];
         const uint64_t nb = ceil_div(P, kTile);
         k_count<W><<<static_cast<unsigned>(nb), kTpb, g.thr ? smem_all : smem_adj, e->stream>>>(
-            t.args(), in, P, pat.back[ell], pat.lo[ell], lay.warp_cnt[ell], lay.blk_cnt[ell], g.thr, g.alpha, g.beta,
+            targs, in, P, pat.back[ell], pat.lo[ell], lay.warp_cnt[ell], lay.blk_cnt[ell], g.thr, g.alpha, g.beta,
             bound_at(ell));
         launch_scan(lay.blk_cnt[ell], lay.blk_off[ell], nb, e->stream);
         MAPA_CUDA_TRY(cudaGetLastError());
@@ -243,7 +256,7 @@ struct Runner {
             }
             const uint64_t children = total > lay.E ? off[b1] - off[b0] : total;
             k_write<W, CT><<<static_cast<unsigned>(b1 - b0), kTpb, smem_all, e->stream>>>(
-                t.args(), in, P, ell, pat.back[ell], pat.lo[ell], out, lay.warp_cnt[ell], lay.blk_off[ell], b0,
+                targs, in, P, ell, pat.back[ell], pat.lo[ell], out, lay.warp_cnt[ell], lay.blk_off[ell], b0,
                 g.alpha, g.beta, g.thr, bound_at(ell));
             MAPA_CUDA_TRY(cudaGetLastError());
             e->st.kernel_launches += 1;

@@ -232,7 +232,9 @@ int decide_round(mapa_server srv, std::vector<Pending> &round, std::vector<mapa_
         if (srv->h_conflict[i] == 1) {
             chain.push_back(i);
             chain_pids.push_back(round[i].ev.pattern_id);
-            chain_bounded.push_back(round[i].ev.policy.mode == MAPA_MODE_BOUNDED ? 1 : 0);
+            chain_bounded.push_back(static_cast<uint8_t>(
+                (round[i].ev.policy.mode == MAPA_MODE_BOUNDED ? mapa::kKindBounded : 0) |
+                ((round[i].ev.policy.flags & MAPA_POLICY_BW_SENSITIVE) ? mapa::kKindSensitive : 0)));
         } else if (srv->h_conflict[i] == 2) {
             deferred[i] = 1;
         } else if (res[i].status == MAPA_OK) {

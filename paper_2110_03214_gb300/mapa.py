@@ -28,6 +28,7 @@ MAPA_E_STATE = -7
 
 MAPA_RING, MAPA_TREE, MAPA_CLIQUE, MAPA_PATH = 0, 1, 2, 3
 MAPA_MODE_EXHAUSTIVE, MAPA_MODE_BOUNDED = 0, 1
+MAPA_POLICY_BW_SENSITIVE = 1
 KIND = {"ring": MAPA_RING, "tree": MAPA_TREE, "clique": MAPA_CLIQUE, "path": MAPA_PATH}
 
 MAPA_BATCH_INDEPENDENT = 0
@@ -38,7 +39,7 @@ MAX_K = 32
 
 REQUEST_DTYPE = np.dtype(
     {
-        "names": ["pattern_id", "reserved", "alpha", "beta", "mode", "reserved1", "max_embeddings", "busy"],
+        "names": ["pattern_id", "reserved", "alpha", "beta", "mode", "flags", "max_embeddings", "busy"],
         "formats": ["<i4", "<i4", "<i4", "<i4", "<i4", "<i4", "<u8", ("<u4", (8,))],
         "offsets": [0, 4, 8, 12, 16, 20, 24, 32],
         "itemsize": 64,
@@ -61,7 +62,7 @@ MAPA_EVENT_DEPART = 1
 EVENT_DTYPE = np.dtype(
     {
         "names": ["request_id", "at_ns", "lifetime_ns", "job_id", "kind", "pattern_id", "alpha", "beta", "mode",
-                  "reserved", "max_embeddings"],
+                  "flags", "max_embeddings"],
         "formats": ["<i8", "<i8", "<i8", "<i8", "<i4", "<i4", "<i4", "<i4", "<i4", "<i4", "<u8"],
         "offsets": [0, 8, 16, 24, 32, 36, 40, 44, 48, 52, 56],
         "itemsize": 64,
@@ -138,6 +139,7 @@ def _load() -> ctypes.CDLL:
         "mapa_serve_close": ([vp], ctypes.c_int),
         "mapa_pattern_analyze": ([i32, i32, i32p, i32p, ctypes.POINTER(ctypes.c_uint64),
                                   ctypes.POINTER(ctypes.c_uint32), ctypes.POINTER(ctypes.c_uint32)], ctypes.c_int),
+        "mapa_effbw_predict": ([i32, i32, i32, ctypes.POINTER(ctypes.c_double)], ctypes.c_int),
     }
     for name, (args, res) in sig.items():
         fn = getattr(lib, name)
@@ -155,6 +157,7 @@ SYMBOLS = (
     "mapa_occupancy_get", "mapa_pattern_analyze", "mapa_version", "mapa_stats_get", "mapa_stats_reset",
     "mapa_ctx_set_timing", "mapa_allocate_batch_noalloc", "mapa_serve_open", "mapa_serve_submit",
     "mapa_serve_poll", "mapa_serve_drain", "mapa_serve_counters", "mapa_serve_close", "mapa_autotune",
+    "mapa_effbw_predict",
 )
 
 
@@ -345,6 +348,15 @@ def make_events(pattern_ids, at_ns, lifetime_ns=0, alpha=1, beta=1, request_ids=
     return ev
 
 
+def mapa_effbw_predict(x: int, y: int, z: int) -> float:
+    """Host-only: Predicted Effective Bandwidth (Eq. 2) as the library ranks it."""
+    out = ctypes.c_double()
+    rc = lib.mapa_effbw_predict(int(x), int(y), int(z), ctypes.byref(out))
+    if rc != MAPA_OK:
+        raise MapaError(rc, "link counts out of range")
+    return out.value
+
+
 def mapa_pattern_analyze(k: int, a, b):
     """Host-only: (|Aut(P)|, back_masks[k], lo_masks[k])."""
     aa, ap = _i32(a)
@@ -363,13 +375,14 @@ def mapa_pattern_analyze(k: int, a, b):
 # ---- convenience ----------------------------------------------------------------
 
 
-def make_requests(pattern_ids, alpha, beta, busy, max_embeddings=0, mode=0) -> np.ndarray:
+def make_requests(pattern_ids, alpha, beta, busy, max_embeddings=0, mode=0, flags=0) -> np.ndarray:
     pattern_ids = np.asarray(pattern_ids, np.int32)
     r = np.zeros(pattern_ids.shape[0], REQUEST_DTYPE)
     r["pattern_id"] = pattern_ids
     r["alpha"] = alpha
     r["beta"] = beta
     r["mode"] = mode
+    r["flags"] = flags
     r["max_embeddings"] = max_embeddings
     r["busy"] = np.asarray(busy, np.uint32).reshape(-1, 8)
     return r

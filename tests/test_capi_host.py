@@ -134,3 +134,35 @@ def test_invalid_patterns_rejected(M):
         M.mapa_pattern_analyze(33, [], [])
     with pytest.raises(M.MapaError):
         M.mapa_pattern_analyze(3, [0], [5])
+
+
+def _dense_rank(values):
+    order = np.argsort(values, kind="stable")
+    ranks = np.empty(len(values), np.int64)
+    r = 0
+    for i, idx in enumerate(order):
+        if i > 0 and values[idx] != values[order[i - 1]]:
+            r += 1
+        ranks[idx] = r
+    return ranks
+
+
+def test_effbw_ranking_equals_oracle(M):
+    # The library ranks bandwidth-sensitive matches by its own evaluation of
+    # Eq. 2; over every link-count triple it handles, the values agree with
+    # the oracle's to 1e-9 and induce exactly the same order, so the device
+    # argmax over ranks takes the oracle's decisions.
+    R = 64
+    lib_f = np.empty(R ** 3)
+    ora_f = np.empty(R ** 3)
+    oracle_lib = O.load()
+    for x in range(R):
+        for y in range(R):
+            for z in range(R):
+                i = (x * R + y) * R + z
+                lib_f[i] = M.mapa_effbw_predict(x, y, z)
+                ora_f[i] = O.effbw(x, y, z, lib=oracle_lib)
+    assert np.max(np.abs(lib_f - ora_f)) < 1e-9
+    assert np.array_equal(_dense_rank(lib_f), _dense_rank(ora_f))
+    with pytest.raises(M.MapaError):
+        M.mapa_effbw_predict(64, 0, 0)
