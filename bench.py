@@ -48,6 +48,8 @@ def _args():
     ap.add_argument("--served-requests", type=int, default=3000, help="arrivals in the served comparison")
     ap.add_argument("--served-rate", type=float, default=1e4, help="Poisson rate of the served comparison")
     ap.add_argument("--served-kmax", type=int, default=8)
+    ap.add_argument("--sim-jobs", type=int, default=300,
+                    help="jobs of the simulator leg (Sec. 6 job file; 0 = skip)")
     ap.add_argument("--no-autotune", action="store_true",
                     help="keep the default tail depths (profiling runs: timings under a profiler mislead the tuner)")
     return ap.parse_args()
@@ -287,6 +289,38 @@ def served_measure(M, W, rate: float, count: int, max_batch: int, kmax: int = 8,
     }
 
 
+def simulator_measure(M, W, jobs_count: int, seed: int = 6):
+    """The simulator of Sec. 6 (mapa_simulate) on the 8-GPU fixture and the two
+    16-GPU stand-ins: per policy, the quartiles of the logged Predicted EffBW
+    of bandwidth-sensitive and -insensitive jobs, the makespan in cycles, and
+    the decisions per second of the run (every non-Baseline decision on the
+    GPU)."""
+    names = {M.MAPA_SIM_BASELINE: "baseline", M.MAPA_SIM_GREEDY: "greedy", M.MAPA_SIM_PRESERVE: "preserve",
+             M.MAPA_SIM_EFFBW: "effbw"}
+    jobs = W.sim_jobs(jobs_count, seed=seed)
+    out = {"jobs": jobs_count, "job_file": "uniform mix of Sec. 5 workloads, 1-5 GPUs, ring pattern, "
+                                           "durations U[100,1000] cycles, all in the file at cycle 0"}
+    for topo in (W.dgx_fixture(), W.torus2d16(), W.cubemesh16()):
+        per = {}
+        with M.Context(0) as c:
+            tid = c.topology_load(topo)
+            pids = np.asarray([c.pattern_load(p) for p in jobs.patterns], np.int32)
+            table = M.make_sim_jobs(pids[jobs.pattern_index], jobs.arrive, jobs.duration, jobs.sensitive)
+            for pol, name in names.items():
+                t0 = time.perf_counter()
+                rec = M.mapa_simulate(c.h, tid, pol, table)
+                dt = time.perf_counter() - t0
+                ok = rec["status"] == M.MAPA_OK
+                q = {}
+                for label, sel in (("sensitive", jobs.sensitive == 1), ("insensitive", jobs.sensitive == 0)):
+                    e = rec["effbw_milli"][ok & sel] / 1000.0
+                    q[label] = [round(float(np.percentile(e, p)), 3) for p in (25, 50, 75)] if len(e) else None
+                per[name] = {"effbw_quartiles_gbps": q, "makespan_cycles": int(rec["end"].max()),
+                             "decisions_per_s": round(jobs_count / dt, 1)}
+        out[topo.name] = per
+    return out
+
+
 def run_served_sweep(a):
     """Served loop: batched rounds vs one request per round over a rate sweep."""
     import __graft_entry__
@@ -511,6 +545,8 @@ def run_ours(a):
             sb = served_measure(M, W, a.served_rate, a.served_requests, 4096, kmax=a.served_kmax)
             sp = served_measure(M, W, a.served_rate, a.served_requests, 1, kmax=a.served_kmax)
             line["served"] = {"batched": sb, "plain": sp}
+        if world == 1 and a.sim_jobs > 0:
+            line["simulator"] = simulator_measure(M, W, a.sim_jobs)
             line["latency_ms"].update({"served_batched_p50": sb["p50_ms"], "served_batched_p99": sb["p99_ms"],
                                        "served_plain_p50": sp["p50_ms"], "served_plain_p99": sp["p99_ms"]})
         if world == 1 and not a.no_cpu_baseline:

@@ -385,6 +385,60 @@ int mapa_occupancy_get(mapa_ctx ctx, int32_t topo_id, uint32_t *busy_out);
 int mapa_pattern_analyze(int32_t k, int32_t m, const int32_t *a, const int32_t *b, uint64_t *aut_order,
                          uint32_t *back_masks, uint32_t *lo_masks);
 
+/* ---- simulator (Sec. 6) ---------------------------------------------------- */
+
+/* Allocation policies of the simulator (Sec. 5 and Sec. 6).
+ *   BASELINE: the lowest free accelerator ids, pattern vertex i on the i-th
+ *             (how container runtimes allocate); no matching.
+ *   GREEDY:   the match with the largest AggBW (alpha 1, beta 0).
+ *   PRESERVE: Algorithm 1 -- largest Predicted EffBW for a bandwidth-
+ *             sensitive job, largest PreservedBW (alpha 0, beta 1) otherwise.
+ *   EFFBW:    largest Predicted EffBW for every job. */
+enum mapa_sim_policy { MAPA_SIM_BASELINE = 0, MAPA_SIM_GREEDY = 1, MAPA_SIM_PRESERVE = 2, MAPA_SIM_EFFBW = 3 };
+
+/* One row of a job file (32 bytes).  Jobs enter the FIFO queue at `arrive`
+ * (cycles, non-decreasing along the file) and run for `duration` cycles
+ * once allocated. */
+typedef struct {
+    int64_t job_id;
+    int64_t arrive;
+    int64_t duration;
+    int32_t pattern_id;
+    int32_t sensitive; /* 1 = bandwidth-sensitive */
+} mapa_sim_job;
+
+/* The logger's record of one job (80 bytes).  status MAPA_OK, or MAPA_NO_FIT
+ * when the job cannot be placed even on the idle machine (then start = end =
+ * the cycle it reached the queue head).  effbw_milli = round(1000 * Eq. 2)
+ * over the link types of the images of the pattern edges; agg = AggBW (Eq.
+ * 1); pres = PreservedBW (Eq. 3) of the free accelerators left at
+ * allocation time; verts[i] = the accelerator of pattern vertex i. */
+typedef struct {
+    int64_t job_id;
+    int64_t start;
+    int64_t end;
+    int32_t status;
+    int32_t effbw_milli;
+    int32_t agg;
+    int32_t pres;
+    int32_t k;
+    int32_t reserved;
+    uint8_t verts[MAPA_MAX_K];
+} mapa_sim_record;
+
+/* Runs a job file through the simulator of Sec. 6 on topology topo_id (which
+ * must have at most 256 accelerators): a dispatcher puts the jobs in a FIFO
+ * queue; a cycle-based engine, at each cycle where something happens, first
+ * frees the accelerators of the jobs that finished, then allocates the queue
+ * head while it fits under `policy` (a head that does not fit waits for a
+ * job to finish: no reordering); every decision other than BASELINE is taken
+ * by the GPU path (one request against the current occupancy).  The
+ * topology's device occupancy is neither read nor changed.  out[i] answers
+ * jobs[i].  Returns MAPA_OK, or an error for the call as a whole
+ * (MAPA_E_INVALID for unknown ids or arrivals out of order). */
+int mapa_simulate(mapa_ctx ctx, int32_t topo_id, int32_t policy, int32_t njobs, const mapa_sim_job *jobs,
+                  mapa_sim_record *out);
+
 /* Host-only: the Predicted Effective Bandwidth (Eq. 2, coefficients of
  * Table 2) of an allocation with x double NVLinks, y single NVLinks and z
  * PCIe links, in GB/s, as the library ranks bandwidth-sensitive matches.

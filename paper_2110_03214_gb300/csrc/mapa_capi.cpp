@@ -368,6 +368,7 @@ int mapa_topology_load(mapa_ctx ctx, int32_t n, int32_t m, const int32_t *u, con
     CTX_CUDA(ctx, cudaMemsetAsync(t.next_job, 0, sizeof(unsigned long long), st));
     CTX_CUDA(ctx, cudaStreamSynchronize(st));
     te.live = true;
+    te.wm = std::move(wm);
     t.id = static_cast<int32_t>(ctx->topos.size());
     ctx->topos.push_back(te);
     *topo_id = static_cast<int32_t>(ctx->topos.size() - 1);

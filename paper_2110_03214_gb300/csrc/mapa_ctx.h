@@ -11,6 +11,7 @@ namespace mapa {
 
 struct TopoEntry {
     TopoDevice dev;
+    std::vector<int32_t> wm;  // host copy of the n x n link weights (fill applied), for the simulator's logger
     bool live = false;
 };
 

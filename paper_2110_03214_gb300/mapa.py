@@ -69,6 +69,26 @@ EVENT_DTYPE = np.dtype(
     }
 )
 
+MAPA_SIM_BASELINE, MAPA_SIM_GREEDY, MAPA_SIM_PRESERVE, MAPA_SIM_EFFBW = 0, 1, 2, 3
+
+SIM_JOB_DTYPE = np.dtype(
+    {
+        "names": ["job_id", "arrive", "duration", "pattern_id", "sensitive"],
+        "formats": ["<i8", "<i8", "<i8", "<i4", "<i4"],
+        "offsets": [0, 8, 16, 24, 28],
+        "itemsize": 32,
+    }
+)
+
+SIM_RECORD_DTYPE = np.dtype(
+    {
+        "names": ["job_id", "start", "end", "status", "effbw_milli", "agg", "pres", "k", "reserved", "verts"],
+        "formats": ["<i8", "<i8", "<i8", "<i4", "<i4", "<i4", "<i4", "<i4", "<i4", ("u1", (32,))],
+        "offsets": [0, 8, 16, 24, 28, 32, 36, 40, 44, 48],
+        "itemsize": 80,
+    }
+)
+
 SERVED_DTYPE = np.dtype(
     {
         "names": ["request_id", "arrive_ns", "done_ns", "kind", "rounds", "snapshot", "result"],
@@ -140,6 +160,7 @@ def _load() -> ctypes.CDLL:
         "mapa_pattern_analyze": ([i32, i32, i32p, i32p, ctypes.POINTER(ctypes.c_uint64),
                                   ctypes.POINTER(ctypes.c_uint32), ctypes.POINTER(ctypes.c_uint32)], ctypes.c_int),
         "mapa_effbw_predict": ([i32, i32, i32, ctypes.POINTER(ctypes.c_double)], ctypes.c_int),
+        "mapa_simulate": ([vp, i32, i32, i32, vp, vp], ctypes.c_int),
     }
     for name, (args, res) in sig.items():
         fn = getattr(lib, name)
@@ -157,7 +178,7 @@ SYMBOLS = (
     "mapa_occupancy_get", "mapa_pattern_analyze", "mapa_version", "mapa_stats_get", "mapa_stats_reset",
     "mapa_ctx_set_timing", "mapa_allocate_batch_noalloc", "mapa_serve_open", "mapa_serve_submit",
     "mapa_serve_poll", "mapa_serve_drain", "mapa_serve_counters", "mapa_serve_close", "mapa_autotune",
-    "mapa_effbw_predict",
+    "mapa_effbw_predict", "mapa_simulate",
 )
 
 
@@ -346,6 +367,25 @@ def make_events(pattern_ids, at_ns, lifetime_ns=0, alpha=1, beta=1, request_ids=
     ev["alpha"] = alpha
     ev["beta"] = beta
     return ev
+
+
+def mapa_simulate(ctx, topo_id: int, policy: int, jobs: np.ndarray) -> np.ndarray:
+    """Runs a job file (SIM_JOB_DTYPE) through the simulator; one record per job."""
+    jobs = np.ascontiguousarray(jobs, dtype=SIM_JOB_DTYPE)
+    out = np.zeros(len(jobs), SIM_RECORD_DTYPE)
+    _check(ctx, lib.mapa_simulate(ctx, topo_id, policy, len(jobs), jobs.ctypes.data, out.ctypes.data))
+    return out
+
+
+def make_sim_jobs(pattern_ids, arrive, duration, sensitive, job_ids=None) -> np.ndarray:
+    pattern_ids = np.asarray(pattern_ids, np.int32)
+    j = np.zeros(pattern_ids.shape[0], SIM_JOB_DTYPE)
+    j["job_id"] = np.arange(pattern_ids.shape[0]) if job_ids is None else job_ids
+    j["arrive"] = arrive
+    j["duration"] = duration
+    j["pattern_id"] = pattern_ids
+    j["sensitive"] = sensitive
+    return j
 
 
 def mapa_effbw_predict(x: int, y: int, z: int) -> float:

@@ -291,6 +291,34 @@ def dgx_fixture() -> Topology:
     return Topology("dgx-fixture-8", 8, u, v, w, fill_weight=12)
 
 
+def torus2d16(w_x: int = 50, w_y: int = 25, fill: int = 12) -> Topology:
+    """16 accelerators on a 4x4 torus (id 4x + y): double NVLinks (w_x) along
+    x, single NVLinks (w_y) along y, PCIe (fill) between every other pair.
+    A stand-in for the Torus-2d of Sec. 6 with its three link types (the
+    paper's wiring figure is not available)."""
+    pairs = {}
+    for x in range(4):
+        for y in range(4):
+            s = 4 * x + y
+            for t, wt in ((4 * ((x + 1) % 4) + y, w_x), (4 * x + (y + 1) % 4, w_y)):
+                pairs[(min(s, t), max(s, t))] = wt
+    order = sorted(pairs)
+    u, v = _edges(order)
+    return Topology("torus2d-16", 16, u, v, np.asarray([pairs[e] for e in order], np.int32), fill_weight=fill)
+
+
+def cubemesh16(link: int = 25, fill: int = 12) -> Topology:
+    """Two 8-accelerator boards with the NVLink layout of dgx_fixture (ids
+    0-7 and 8-15) joined by one single NVLink (link) between corresponding
+    accelerators, PCIe (fill) elsewhere.  A stand-in for the Cube-mesh of
+    Sec. 6 (wiring figure not available)."""
+    board = dgx_fixture()
+    u = np.concatenate([board.u, board.u + 8, np.arange(8, dtype=np.int32)]).astype(np.int32)
+    v = np.concatenate([board.v, board.v + 8, np.arange(8, 16, dtype=np.int32)]).astype(np.int32)
+    w = np.concatenate([board.w, board.w, np.full(8, link, np.int32)]).astype(np.int32)
+    return Topology("cubemesh-16", 16, u, v, w, fill_weight=fill)
+
+
 # --------------------------------------------------------------------------
 # Requests
 
@@ -469,3 +497,46 @@ def served_trace(count: int, rate: float, kmax_rt: int = 8, clique_max: int = 4,
     desc = (f"128-vertex dragonfly, ring/tree k in 2..{kmax_rt}, clique k in 2..{clique_max}, "
             f"Poisson {rate:g}/s, offered occupancy {occupancy:g}")
     return ServedTrace(topo, pats, index, (t * 1e9).astype(np.int64), (life * 1e9).astype(np.int64), rate, desc)
+
+
+# --------------------------------------------------------------------------
+# Simulator job files (Sec. 5 and Sec. 6)
+
+#: Workloads of the evaluation and their bandwidth sensitivity as Sec. 2.3
+#: and Sec. 5 classify them.
+SIM_NETWORKS = (("AlexNet", True), ("VGG-16", True), ("ResNet-50", True), ("Inception-v3", True),
+                ("GoogleNet", False), ("CaffeNet", False), ("Cusimann", False), ("GMM", False), ("Jacobi", False))
+
+
+@dataclasses.dataclass
+class SimJobs:
+    """A job file: job i runs network[i] on the pattern patterns[pattern_index[i]]."""
+
+    patterns: list
+    pattern_index: np.ndarray  # int32 [J]
+    arrive: np.ndarray  # int64 [J], non-decreasing cycles
+    duration: np.ndarray  # int64 [J] cycles
+    sensitive: np.ndarray  # int32 [J]
+    network: list
+
+    def __len__(self) -> int:
+        return int(self.pattern_index.shape[0])
+
+
+def sim_jobs(count: int = 300, seed: int = 6, max_gpus: int = 5, duration=(100, 1000), arrival_gap: int = 0) -> SimJobs:
+    """Job file in the manner of Sec. 5: a uniform mix of the workloads in
+    SIM_NETWORKS, GPUs per job uniform in 1..max_gpus, each job's pattern the
+    ring over its GPUs (the NCCL ring of Sec. 3.1; 1 GPU = one vertex, 2 =
+    one edge), durations uniform in `duration` cycles.  With arrival_gap = 0
+    every job is in the file at cycle 0 (the dispatcher reads it whole);
+    otherwise job i arrives at i * arrival_gap.  Durations and the network mix
+    are synthetic stand-ins for the measured execution times of the paper's
+    runs, which are not available."""
+    rng = Rng(seed, 11)
+    pats = [pattern("ring", k) for k in range(1, max_gpus + 1)]
+    gpus = rng.integers(1, max_gpus, count)
+    net = rng.integers(0, len(SIM_NETWORKS) - 1, count)
+    dur = rng.integers(int(duration[0]), int(duration[1]), count).astype(np.int64)
+    arrive = np.arange(count, dtype=np.int64) * int(arrival_gap)
+    sens = np.asarray([1 if SIM_NETWORKS[i][1] else 0 for i in net], np.int32)
+    return SimJobs(pats, (gpus - 1).astype(np.int32), arrive, dur, sens, [SIM_NETWORKS[i][0] for i in net])
