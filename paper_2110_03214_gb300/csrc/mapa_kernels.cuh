@@ -1107,8 +1107,9 @@ __global__ void __launch_bounds__(kTpb) k_last(TopoArgs topo, LevelView in, cons
 }
 
 // ----------------------------------------------------------------------------
-// Fused tail of depth 1 or 2 (exhaustive mode): the same result as k_last
-// with T <= 2, laid out for this shape.  One block takes one tile of kTile
+// Fused tail of depth 1, 2 or 3 (exhaustive mode; masks of at most 64
+// vertices, and every bandwidth-sensitive group): the same result as k_last,
+// laid out for these shapes.  One block takes one tile of kTile
 // consecutive parents (grid = tiles), each thread walks its parents' last
 // one or two levels with explicit loops, and the score increment keeps its
 // weight-class loop rolled.  Measured on the 32-vertex regular workload,
@@ -1134,7 +1135,7 @@ __device__ __forceinline__ int32_t delta_rolled(const SmemTopo &s, int v, const 
     return acc;
 }
 
-// Walks the last T (1 or 2) levels below parent p; leaf(score) for every
+// Walks the last T (1, 2 or 3) levels below parent p; leaf(score) for every
 // complete match.
 template <int W, int T, typename Leaf>
 __device__ __forceinline__ void walk_short_tail(const SmemTopo &s, const LevelView &in, uint64_t p, const TailArgs &ta,
@@ -1152,6 +1153,53 @@ __device__ __forceinline__ void walk_short_tail(const SmemTopo &s, const LevelVi
     if constexpr (T == 1) {
         int v;
         while ((v = pop_lowest<W>(c1)) >= 0) leaf(S + delta_rolled<W>(s, v, B, R, al, be));
+    } else if constexpr (T == 3) {
+        uint32_t A2[W], B2[W], A3[W], B3[W];
+        int lb2, lb3;
+        level_masks<W>(in, p, ta.back_old[1], ta.lo_old[1], s.adj, A2, B2, lb2);
+        level_masks<W>(in, p, ta.back_old[2], ta.lo_old[2], s.adj, A3, B3, lb3);
+        const bool nb21 = (ta.back_tail[1] & 1u) != 0u, nl21 = (ta.lo_tail[1] & 1u) != 0u;
+        const bool nb31 = (ta.back_tail[2] & 1u) != 0u, nl31 = (ta.lo_tail[2] & 1u) != 0u;
+        const bool nb32 = (ta.back_tail[2] & 2u) != 0u, nl32 = (ta.lo_tail[2] & 2u) != 0u;
+        int v1;
+        while ((v1 = pop_lowest<W>(c1)) >= 0) {
+            ++nodes;
+            const int32_t s1 = S + delta_rolled<W>(s, v1, B, R, al, be);
+            uint32_t R1[W], c2[W], B2n[W];
+#pragma unroll
+            for (int w = 0; w < W; ++w) {
+                R1[w] = R[w];
+                B2n[w] = B2[w];
+            }
+            clear_bit<W>(R1, v1);
+            if (nb21) set_bit<W>(B2n, v1);
+#pragma unroll
+            for (int w = 0; w < W; ++w) c2[w] = R1[w] & A2[w] & (nb21 ? s.adj[v1 * W + w] : ~0u);
+            and_above<W>(c2, nl21 ? max(lb2, v1) : lb2);
+            int v2;
+            while ((v2 = pop_lowest<W>(c2)) >= 0) {
+                ++nodes;
+                const int32_t s2 = s1 + delta_rolled<W>(s, v2, B2n, R1, al, be);
+                uint32_t R2[W], c3[W], B3n[W];
+#pragma unroll
+                for (int w = 0; w < W; ++w) {
+                    R2[w] = R1[w];
+                    B3n[w] = B3[w];
+                }
+                clear_bit<W>(R2, v2);
+                if (nb31) set_bit<W>(B3n, v1);
+                if (nb32) set_bit<W>(B3n, v2);
+#pragma unroll
+                for (int w = 0; w < W; ++w)
+                    c3[w] = R2[w] & A3[w] & (nb31 ? s.adj[v1 * W + w] : ~0u) & (nb32 ? s.adj[v2 * W + w] : ~0u);
+                int lb = lb3;
+                if (nl31) lb = max(lb, v1);
+                if (nl32) lb = max(lb, v2);
+                and_above<W>(c3, lb);
+                int v3;
+                while ((v3 = pop_lowest<W>(c3)) >= 0) leaf(s2 + delta_rolled<W>(s, v3, B3n, R2, al, be));
+            }
+        }
     } else {
         uint32_t A2[W], B2[W];
         int lb2;

@@ -102,7 +102,7 @@ struct Runner {
         MAPA_CUDA_TRY(cudaFuncSetAttribute(k_expand<W, CT, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, b));
         MAPA_CUDA_TRY(cudaFuncSetAttribute(k_last<W, CT, T, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, b));
         MAPA_CUDA_TRY(cudaFuncSetAttribute(k_last<W, CT, T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, b));
-        if constexpr (T <= 2 && W <= 2)
+        if constexpr (W <= 2)
             MAPA_CUDA_TRY(
                 cudaFuncSetAttribute(k_last_short<W, T, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, b));
         if constexpr (T == 1)
@@ -163,7 +163,7 @@ struct Runner {
                 launched = true;
             }
         }
-        if constexpr (T <= 2 && W <= 2) {
+        if constexpr (W <= 2) {
             if (!g.thr && !launched) {
                 // masks of at most 64 vertices: one tile of parents per block
                 k_last_short<W, T, false><<<sgrid, kTpb, smem_all, e->stream>>>(

@@ -7,6 +7,8 @@ launch configuration the benchmark times, with a seeded sample compared to
 the oracle one by one and every result re-scored from its tuple.
 """
 
+import dataclasses
+
 import numpy as np
 import pytest
 
@@ -311,3 +313,26 @@ def test_graph_replay_matches_direct_launches(M, monkeypatch):
             assert np.array_equal(got, want)
         st = graphed.stats()
     assert st["requests"] == 4 * 2000 and st["kernel_launches"] > 0
+
+
+@pytest.mark.parametrize("name,num", [("regular32", 3000), ("torus64", 800)])
+def test_every_tail_depth_gives_the_same_results(M, monkeypatch, name, num):
+    # depth 1, 2, 3 run different fused-tail forms (and 32- and 64-vertex
+    # masks the short one); every result must be the same, and equal to the
+    # oracle on a sample
+    wl = W.workload(name, num_requests=num)
+    if name == "torus64":
+        ks = np.asarray([wl.requests.patterns[i].k for i in wl.requests.pattern_index])
+        wl = dataclasses.replace(wl, requests=wl.requests.subset(np.nonzero(ks <= 9)[0]))
+    out = {}
+    for depth in (1, 2, 3):
+        monkeypatch.setenv("MAPA_TAIL_DEPTH", str(depth))
+        with M.Context(0) as c:
+            tid = c.topology_load(wl.topology)
+            pids = [c.pattern_load(p) for p in wl.requests.patterns]
+            out[depth] = c.allocate_batch(tid, c.requests(wl.requests, pids))
+    assert np.array_equal(out[1], out[2]) and np.array_equal(out[2], out[3])
+    inst = O.Instance.from_topology(wl.topology)
+    idx = list(range(0, len(wl.requests), max(1, len(wl.requests) // 40)))
+    for i, d in zip(idx, oracle_decisions(inst, wl.topology.n, wl.requests, idx)):
+        assert_same(out[3][i], d, wl.requests.patterns[wl.requests.pattern_index[i]].k, where=f"request {i}")
