@@ -1107,7 +1107,7 @@ __global__ void __launch_bounds__(kTpb) k_last(TopoArgs topo, LevelView in, cons
 }
 
 // ----------------------------------------------------------------------------
-// Fused tail of depth 1, 2 or 3 (exhaustive mode; masks of at most 64
+// Fused tail of depth 1 or 2 (exhaustive mode; masks of at most 64
 // vertices, and every bandwidth-sensitive group): the same result as k_last,
 // laid out for these shapes.  One block takes one tile of kTile
 // consecutive parents (grid = tiles), each thread walks its parents' last
@@ -1135,7 +1135,7 @@ __device__ __forceinline__ int32_t delta_rolled(const SmemTopo &s, int v, const 
     return acc;
 }
 
-// Walks the last T (1, 2 or 3) levels below parent p; leaf(score) for every
+// Walks the last T (1 or 2) levels below parent p; leaf(score) for every
 // complete match.
 template <int W, int T, typename Leaf>
 __device__ __forceinline__ void walk_short_tail(const SmemTopo &s, const LevelView &in, uint64_t p, const TailArgs &ta,
@@ -1153,53 +1153,6 @@ __device__ __forceinline__ void walk_short_tail(const SmemTopo &s, const LevelVi
     if constexpr (T == 1) {
         int v;
         while ((v = pop_lowest<W>(c1)) >= 0) leaf(S + delta_rolled<W>(s, v, B, R, al, be));
-    } else if constexpr (T == 3) {
-        uint32_t A2[W], B2[W], A3[W], B3[W];
-        int lb2, lb3;
-        level_masks<W>(in, p, ta.back_old[1], ta.lo_old[1], s.adj, A2, B2, lb2);
-        level_masks<W>(in, p, ta.back_old[2], ta.lo_old[2], s.adj, A3, B3, lb3);
-        const bool nb21 = (ta.back_tail[1] & 1u) != 0u, nl21 = (ta.lo_tail[1] & 1u) != 0u;
-        const bool nb31 = (ta.back_tail[2] & 1u) != 0u, nl31 = (ta.lo_tail[2] & 1u) != 0u;
-        const bool nb32 = (ta.back_tail[2] & 2u) != 0u, nl32 = (ta.lo_tail[2] & 2u) != 0u;
-        int v1;
-        while ((v1 = pop_lowest<W>(c1)) >= 0) {
-            ++nodes;
-            const int32_t s1 = S + delta_rolled<W>(s, v1, B, R, al, be);
-            uint32_t R1[W], c2[W], B2n[W];
-#pragma unroll
-            for (int w = 0; w < W; ++w) {
-                R1[w] = R[w];
-                B2n[w] = B2[w];
-            }
-            clear_bit<W>(R1, v1);
-            if (nb21) set_bit<W>(B2n, v1);
-#pragma unroll
-            for (int w = 0; w < W; ++w) c2[w] = R1[w] & A2[w] & (nb21 ? s.adj[v1 * W + w] : ~0u);
-            and_above<W>(c2, nl21 ? max(lb2, v1) : lb2);
-            int v2;
-            while ((v2 = pop_lowest<W>(c2)) >= 0) {
-                ++nodes;
-                const int32_t s2 = s1 + delta_rolled<W>(s, v2, B2n, R1, al, be);
-                uint32_t R2[W], c3[W], B3n[W];
-#pragma unroll
-                for (int w = 0; w < W; ++w) {
-                    R2[w] = R1[w];
-                    B3n[w] = B3[w];
-                }
-                clear_bit<W>(R2, v2);
-                if (nb31) set_bit<W>(B3n, v1);
-                if (nb32) set_bit<W>(B3n, v2);
-#pragma unroll
-                for (int w = 0; w < W; ++w)
-                    c3[w] = R2[w] & A3[w] & (nb31 ? s.adj[v1 * W + w] : ~0u) & (nb32 ? s.adj[v2 * W + w] : ~0u);
-                int lb = lb3;
-                if (nl31) lb = max(lb, v1);
-                if (nl32) lb = max(lb, v2);
-                and_above<W>(c3, lb);
-                int v3;
-                while ((v3 = pop_lowest<W>(c3)) >= 0) leaf(s2 + delta_rolled<W>(s, v3, B3n, R2, al, be));
-            }
-        }
     } else {
         uint32_t A2[W], B2[W];
         int lb2;
@@ -1335,6 +1288,226 @@ __global__ void __launch_bounds__(kTpb) k_last_short(TopoArgs topo, LevelView in
                       ta.cost_parent * s_parents + ta.cost_node * s_nodes + ta.cost_leaf * s_leaves);
         }
     }
+}
+
+// ----------------------------------------------------------------------------
+// Fused tail of depth 3 with a cooperative first level (exhaustive mode,
+// masks of at most 64 vertices).  A warp takes 32 stored parents (level l),
+// counts their children at level l+1 and hands the children out across its
+// lanes the way k_expand emits them (lane c takes child c of the round), but
+// keeps them in registers instead of writing a level; each lane then walks the
+// last two levels below its child.  The work per lane is that of the depth-2
+// tail, balanced per child instead of per parent, and level l+1 never goes
+// through memory.
+
+struct TailShared {
+    uint32_t r[kWarps];
+    unsigned long long key[kWarps];
+    unsigned long long cnt[kWarps];
+    unsigned long long nodes, leaves, parents;
+};
+
+// End of a fused-tail block: each warp merges its threads' (request, key,
+// count) when they all hold the same request (else flushes per thread), the
+// block merges its warps, and the telemetry counters are added once.
+__device__ __forceinline__ void tail_block_end(TailShared &sh, int lane, int warp, uint32_t r_cur,
+                                               unsigned long long bkey, unsigned long long bcnt,
+                                               unsigned long long nodes, unsigned long long parents,
+                                               unsigned long long leaves, uint64_t *key, unsigned long long *count,
+                                               unsigned long long *stats, const TailArgs &ta) {
+    const unsigned long long wn = warp_sum_u64(nodes), wp = warp_sum_u64(parents), wl = warp_sum_u64(leaves);
+    if (lane == 0) {
+        sh.r[warp] = kNoReq;
+        if (wn) atomicAdd(&sh.nodes, wn);
+        if (wp) atomicAdd(&sh.parents, wp);
+        if (wl) atomicAdd(&sh.leaves, wl);
+    }
+    const unsigned act = __ballot_sync(kFull, bcnt > 0ull);
+    if (act) {
+        const uint32_t rl = __shfl_sync(kFull, r_cur, __ffs(act) - 1);
+        if (__all_sync(kFull, bcnt == 0ull || r_cur == rl)) {
+            unsigned long long k = bkey, c = bcnt;
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                k = max(k, __shfl_xor_sync(kFull, k, o));
+                c += __shfl_xor_sync(kFull, c, o);
+            }
+            if (lane == 0) {
+                sh.r[warp] = rl;
+                sh.key[warp] = k;
+                sh.cnt[warp] = c;
+            }
+        } else if (bcnt) {
+            flush_request(key, count, r_cur, bkey, bcnt);
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        uint32_t r = kNoReq;
+        unsigned long long k = 0ull, c = 0ull;
+        for (int w = 0; w < kWarps; ++w) {
+            if (sh.r[w] == kNoReq) continue;
+            if (sh.r[w] != r) {
+                if (r != kNoReq) flush_request(key, count, r, k, c);
+                r = sh.r[w];
+                k = 0ull;
+                c = 0ull;
+            }
+            k = max(k, sh.key[w]);
+            c += sh.cnt[w];
+        }
+        if (r != kNoReq) flush_request(key, count, r, k, c);
+        if (stats && (sh.parents || sh.nodes || sh.leaves)) {
+            atomicAdd(stats + kStatNodes, sh.nodes);
+            atomicAdd(stats + kStatLeaves, sh.leaves);
+            atomicAdd(stats + kStatParents, sh.parents);
+            atomicAdd(stats + kStatOps, ta.cost_parent * sh.parents + ta.cost_node * sh.nodes + ta.cost_leaf * sh.leaves);
+        }
+    }
+}
+
+template <int W>
+__global__ void __launch_bounds__(kTpb) k_last_coop3(TopoArgs topo, LevelView in, const unsigned long long *count_in,
+                                                     unsigned long long count_host, TailArgs ta, const int32_t *alpha,
+                                                     const int32_t *beta, uint64_t *key, unsigned long long *count,
+                                                     unsigned int *tile_ctr, unsigned long long *stats) {
+    const unsigned long long P = count_in ? *count_in : count_host;
+    if (static_cast<unsigned long long>(blockIdx.x) * kWarps * 32 >= P) return;  // nothing for this block
+    const SmemTopo s = stage_topology<W>(topo, true);
+    __shared__ TailShared sh;
+    if (threadIdx.x == 0) {
+        sh.nodes = 0ull;
+        sh.leaves = 0ull;
+        sh.parents = 0ull;
+    }
+    __syncthreads();
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const unsigned long long nchunks = (P + 31) / 32;
+    const bool nb21 = (ta.back_tail[1] & 1u) != 0u, nl21 = (ta.lo_tail[1] & 1u) != 0u;
+    const bool nb31 = (ta.back_tail[2] & 1u) != 0u, nl31 = (ta.lo_tail[2] & 1u) != 0u;
+    const bool nb32 = (ta.back_tail[2] & 2u) != 0u, nl32 = (ta.lo_tail[2] & 2u) != 0u;
+    uint32_t r_cur = kNoReq;
+    unsigned long long bkey = 0ull, bcnt = 0ull, parents = 0ull, leaves_total = 0ull, nodes = 0ull;
+    for (;;) {
+        unsigned int chunk = 0;
+        if (lane == 0) chunk = atomicAdd(tile_ctr, 1u);
+        chunk = __shfl_sync(kFull, chunk, 0);
+        if (chunk >= nchunks) break;
+        // lane = one stored parent: its candidates at level l and the masks
+        // of levels l+1 and l+2 from its stored vertices
+        const uint64_t p = static_cast<uint64_t>(chunk) * 32 + lane;
+        uint32_t c1[W], B1[W], R[W], A2[W], B2[W], A3[W], B3[W];
+        int lb2 = -1, lb3 = -1;
+        int32_t S = 0, al = 0, be = 0;
+        uint32_t r = 0;
+#pragma unroll
+        for (int w = 0; w < W; ++w) c1[w] = B1[w] = R[w] = A2[w] = B2[w] = A3[w] = B3[w] = 0u;
+        if (p < P) {
+            ++parents;
+            uint32_t A1[W];
+            int lb1;
+            level_masks<W>(in, p, ta.back_old[0], ta.lo_old[0], s.adj, A1, B1, lb1);
+            level_masks<W>(in, p, ta.back_old[1], ta.lo_old[1], s.adj, A2, B2, lb2);
+            level_masks<W>(in, p, ta.back_old[2], ta.lo_old[2], s.adj, A3, B3, lb3);
+#pragma unroll
+            for (int w = 0; w < W; ++w) {
+                R[w] = in.R[w * in.cap + p];
+                c1[w] = R[w] & A1[w];
+            }
+            and_above<W>(c1, lb1);
+            S = in.S[p];
+            r = in.r[p];
+            al = alpha[r];
+            be = beta[r];
+        }
+        const int cnt = popc_mask<W>(c1);
+        const int incl = warp_incl_scan(cnt, lane);
+        const int total = __shfl_sync(kFull, incl, 31);
+        for (int c0 = 0; c0 < total; c0 += 32) {
+            // lane c takes child c of the round: its parent by binary search
+            const int c = c0 + lane;
+            int src = 0;
+#pragma unroll
+            for (int step = 16; step >= 1; step >>= 1) {
+                const int t = __shfl_sync(kFull, incl, src + step - 1);
+                if (t <= c) src += step;
+            }
+            const int start = __shfl_sync(kFull, incl - cnt, src);
+            uint32_t cs[W], Bs[W], Rs[W], A2s[W], B2s[W], A3s[W], B3s[W];
+#pragma unroll
+            for (int w = 0; w < W; ++w) {
+                cs[w] = __shfl_sync(kFull, c1[w], src);
+                Bs[w] = __shfl_sync(kFull, B1[w], src);
+                Rs[w] = __shfl_sync(kFull, R[w], src);
+                A2s[w] = __shfl_sync(kFull, A2[w], src);
+                B2s[w] = __shfl_sync(kFull, B2[w], src);
+                A3s[w] = __shfl_sync(kFull, A3[w], src);
+                B3s[w] = __shfl_sync(kFull, B3[w], src);
+            }
+            const int32_t Ss = __shfl_sync(kFull, S, src), als = __shfl_sync(kFull, al, src),
+                          bes = __shfl_sync(kFull, be, src);
+            const uint32_t rs = __shfl_sync(kFull, r, src);
+            const int lb2s = __shfl_sync(kFull, lb2, src), lb3s = __shfl_sync(kFull, lb3, src);
+            if (c >= total) continue;
+            const uint64_t ps = static_cast<uint64_t>(chunk) * 32 + src;
+            if (rs != r_cur) {
+                if (r_cur != kNoReq) flush_request(key, count, r_cur, bkey, bcnt);
+                r_cur = rs;
+                bkey = 0ull;
+                bcnt = 0ull;
+            }
+            const int v1 = nth_bit<W>(cs, c - start);
+            ++nodes;
+            const int32_t s1 = Ss + delta_rolled<W>(s, v1, Bs, Rs, als, bes);
+            uint32_t R1[W], c2[W], B2n[W];
+#pragma unroll
+            for (int w = 0; w < W; ++w) {
+                R1[w] = Rs[w];
+                B2n[w] = B2s[w];
+            }
+            clear_bit<W>(R1, v1);
+            if (nb21) set_bit<W>(B2n, v1);
+#pragma unroll
+            for (int w = 0; w < W; ++w) c2[w] = R1[w] & A2s[w] & (nb21 ? s.adj[v1 * W + w] : ~0u);
+            and_above<W>(c2, nl21 ? max(lb2s, v1) : lb2s);
+            int32_t smax = INT_MIN;
+            uint32_t leaves = 0;
+            int v2;
+            while ((v2 = pop_lowest<W>(c2)) >= 0) {
+                ++nodes;
+                const int32_t s2 = s1 + delta_rolled<W>(s, v2, B2n, R1, als, bes);
+                uint32_t R2[W], c3[W], B3n[W];
+#pragma unroll
+                for (int w = 0; w < W; ++w) {
+                    R2[w] = R1[w];
+                    B3n[w] = B3s[w];
+                }
+                clear_bit<W>(R2, v2);
+                if (nb31) set_bit<W>(B3n, v1);
+                if (nb32) set_bit<W>(B3n, v2);
+#pragma unroll
+                for (int w = 0; w < W; ++w)
+                    c3[w] = R2[w] & A3s[w] & (nb31 ? s.adj[v1 * W + w] : ~0u) & (nb32 ? s.adj[v2 * W + w] : ~0u);
+                int lb = lb3s;
+                if (nl31) lb = max(lb, v1);
+                if (nl32) lb = max(lb, v2);
+                and_above<W>(c3, lb);
+                int v3;
+                while ((v3 = pop_lowest<W>(c3)) >= 0) {
+                    smax = max(smax, s2 + delta_rolled<W>(s, v3, B3n, R2, als, bes));
+                    ++leaves;
+                }
+            }
+            if (leaves) {
+                const unsigned long long k64 =
+                    (static_cast<unsigned long long>(biased(smax)) << 32) | (0xFFFFFFFFu - static_cast<uint32_t>(ps));
+                bkey = max(bkey, k64);
+                bcnt += leaves;
+                leaves_total += leaves;
+            }
+        }
+    }
+    tail_block_end(sh, lane, warp, r_cur, bkey, bcnt, nodes, parents, leaves_total, key, count, stats, ta);
 }
 
 template <int T>

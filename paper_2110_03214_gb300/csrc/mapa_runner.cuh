@@ -102,9 +102,11 @@ struct Runner {
         MAPA_CUDA_TRY(cudaFuncSetAttribute(k_expand<W, CT, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, b));
         MAPA_CUDA_TRY(cudaFuncSetAttribute(k_last<W, CT, T, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, b));
         MAPA_CUDA_TRY(cudaFuncSetAttribute(k_last<W, CT, T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, b));
-        if constexpr (W <= 2)
+        if constexpr (T <= 2 && W <= 2)
             MAPA_CUDA_TRY(
                 cudaFuncSetAttribute(k_last_short<W, T, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, b));
+        if constexpr (T == 3 && W <= 2)
+            MAPA_CUDA_TRY(cudaFuncSetAttribute(k_last_coop3<W>, cudaFuncAttributeMaxDynamicSharedMemorySize, b));
         if constexpr (T == 1)
             MAPA_CUDA_TRY(
                 cudaFuncSetAttribute(k_last_short<W, 1, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, b));
@@ -163,7 +165,19 @@ struct Runner {
                 launched = true;
             }
         }
-        if constexpr (W <= 2) {
+        if constexpr (T == 3 && W <= 2) {
+            if (!g.thr && !launched) {
+                // depth 3: the first tail level handed out across lanes
+                static int nb3 = 0;
+                if (!nb3) nb3 = blocks_per_sm(k_last_coop3<W>, smem_all);
+                const unsigned cgrid = static_cast<unsigned>(std::max<uint64_t>(
+                    1, std::min<uint64_t>(ceil_div(max_parents, kTpb), uint64_t(e->sm_count) * nb3)));
+                k_last_coop3<W><<<cgrid, kTpb, smem_all, e->stream>>>(targs, in, count_dev, count_host, ta, g.alpha,
+                                                                     g.beta, g.key, g.count, tile_ctr, e->d_stats);
+                launched = true;
+            }
+        }
+        if constexpr (T <= 2 && W <= 2) {
             if (!g.thr && !launched) {
                 // masks of at most 64 vertices: one tile of parents per block
                 k_last_short<W, T, false><<<sgrid, kTpb, smem_all, e->stream>>>(
