@@ -324,7 +324,7 @@ int plan_layout(Engine *e, int32_t group_size, int k, int T, int W, bool device_
             return MAPA_E_NOMEM;
         }
         E = (cap - fixed) * 1024 / (per_entry * 1024 + scr_x1024 * lay->L + 1);
-        E = std::min<uint64_t>(E, 1ull << 31);
+        E = std::min<uint64_t>(E, kMaxLevelEntries);
         E = E / kTile * kTile;
         if (E < static_cast<uint64_t>(kTile) * static_cast<uint64_t>(n)) {
             if (err) *err = "frontier memory cap too small (needs room for one tile of children per level)";

@@ -25,6 +25,11 @@ constexpr int kTile = kTpb * kIpt;
 // Largest request group enumerated together (larger groups are sliced).
 constexpr int kMaxGroup = 1 << 20;
 
+// Capacity limit of a stored level: with at most 8 columns per field, every
+// column offset j * cap + p stays below 2^31 (kernels index in 32 bits).
+// Larger frontiers are produced in chunks.
+constexpr uint64_t kMaxLevelEntries = 1ull << 28;
+
 // Pattern as the device sees it: vertex i is matched at level i; back[i] holds
 // the earlier neighbours of i, lo[i] the earlier vertices j with the
 // symmetry-breaking constraint phi(j) < phi(i).

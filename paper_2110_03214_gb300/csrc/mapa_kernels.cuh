@@ -211,14 +211,20 @@ __device__ __forceinline__ SmemTopo stage_topology(const TopoArgs &t, bool with_
     return SmemTopo{adj, cls, wc, t.n, t.C, t.wmin, t.wmax, t.dmax};
 }
 
-__device__ __forceinline__ int tuple_byte(const LevelView &L, uint64_t p, int j) {
-    return static_cast<int>((L.T[static_cast<uint64_t>(j >> 2) * L.cap + p] >> ((j & 3) * 8)) & 0xFFu);
+// Offset of entry p in column j of a level: capacities are at most
+// kMaxLevelEntries and fields at most 8 columns wide, so it fits 32 bits.
+__device__ __forceinline__ uint32_t col_at(const LevelView &L, uint32_t j, uint32_t p) {
+    return j * static_cast<uint32_t>(L.cap) + p;
+}
+
+__device__ __forceinline__ int tuple_byte(const LevelView &L, uint32_t p, int j) {
+    return static_cast<int>((L.T[col_at(L, static_cast<uint32_t>(j >> 2), p)] >> ((j & 3) * 8)) & 0xFFu);
 }
 
 // Intersection of the adjacency rows of placed back-neighbours (A), the set of
 // their images (B) and the lower bound from the order constraints (lb).
 template <int W>
-__device__ __forceinline__ void level_masks(const LevelView &L, uint64_t p, uint32_t back, uint32_t lo,
+__device__ __forceinline__ void level_masks(const LevelView &L, uint32_t p, uint32_t back, uint32_t lo,
                                             const uint32_t *s_adj, uint32_t (&A)[W], uint32_t (&B)[W], int &lb) {
 #pragma unroll
     for (int w = 0; w < W; ++w) {
@@ -761,25 +767,25 @@ __device__ __forceinline__ void emit_children(const SmemTopo &s, const LevelView
             const int v = nth_bit<W>(cs, c - start_s);
             const Scorer<W, CT> sc(s, alpha[rs], beta[rs]);
             const int32_t d = sc.delta(v, Bs, Rs);
-            const uint64_t o = obase + c;
-            const uint64_t ps = p_first + src;
+            const uint32_t o = static_cast<uint32_t>(obase) + static_cast<uint32_t>(c);
+            const uint32_t ps = static_cast<uint32_t>(p_first) + static_cast<uint32_t>(src);
             out.S[o] = Ss + d;
             out.r[o] = rs;
             clear_bit<W>(Rs, v);
 #pragma unroll
-            for (int w = 0; w < W; ++w) out.R[w * out.cap + o] = Rs[w];
+            for (int w = 0; w < W; ++w) out.R[col_at(out, w, o)] = Rs[w];
             for (int jw = 0; jw < nw_in; ++jw) {
-                uint32_t word = in.T[jw * in.cap + ps];
+                uint32_t word = in.T[col_at(in, jw, ps)];
                 if (jw == new_word) word |= static_cast<uint32_t>(v) << new_shift;
-                out.T[jw * out.cap + o] = word;
+                out.T[col_at(out, jw, o)] = word;
             }
-            if (new_shift == 0) out.T[new_word * out.cap + o] = static_cast<uint32_t>(v);
+            if (new_shift == 0) out.T[col_at(out, new_word, o)] = static_cast<uint32_t>(v);
         }
     }
 }
 
 template <int W>
-__device__ __forceinline__ void parent_state(const SmemTopo &s, const LevelView &in, uint64_t p, uint32_t back,
+__device__ __forceinline__ void parent_state(const SmemTopo &s, const LevelView &in, uint32_t p, uint32_t back,
                                              uint32_t lo, uint32_t (&cand)[W], uint32_t (&B)[W], uint32_t (&R)[W],
                                              int32_t &S, uint32_t &r) {
     uint32_t A[W];
@@ -787,7 +793,7 @@ __device__ __forceinline__ void parent_state(const SmemTopo &s, const LevelView 
     level_masks<W>(in, p, back, lo, s.adj, A, B, lb);
 #pragma unroll
     for (int w = 0; w < W; ++w) {
-        R[w] = in.R[w * in.cap + p];
+        R[w] = in.R[col_at(in, w, p)];
         cand[w] = R[w] & A[w];
     }
     and_above<W>(cand, lb);
@@ -1138,7 +1144,7 @@ __device__ __forceinline__ int32_t delta_rolled(const SmemTopo &s, int v, const 
 // Walks the last T (1 or 2) levels below parent p; leaf(score) for every
 // complete match.
 template <int W, int T, typename Leaf>
-__device__ __forceinline__ void walk_short_tail(const SmemTopo &s, const LevelView &in, uint64_t p, const TailArgs &ta,
+__device__ __forceinline__ void walk_short_tail(const SmemTopo &s, const LevelView &in, uint32_t p, const TailArgs &ta,
                                                 int32_t al, int32_t be, Leaf &&leaf, uint32_t &nodes) {
     const int32_t S = in.S[p];
     uint32_t R[W], A[W], B[W], c1[W];
@@ -1146,7 +1152,7 @@ __device__ __forceinline__ void walk_short_tail(const SmemTopo &s, const LevelVi
     level_masks<W>(in, p, ta.back_old[0], ta.lo_old[0], s.adj, A, B, lb);
 #pragma unroll
     for (int w = 0; w < W; ++w) {
-        R[w] = in.R[w * in.cap + p];
+        R[w] = in.R[col_at(in, w, p)];
         c1[w] = R[w] & A[w];
     }
     and_above<W>(c1, lb);
@@ -1205,8 +1211,9 @@ __global__ void __launch_bounds__(kTpb) k_last_short(TopoArgs topo, LevelView in
     uint32_t r_cur = kNoReq;
     unsigned long long bkey = 0ull, bcnt = 0ull;
     for (int j = 0; j < kIpt; ++j) {
-        const uint64_t p = wbase + j * 32 + lane;
-        if (p >= P) continue;
+        const uint64_t p64 = wbase + j * 32 + lane;
+        if (p64 >= P) continue;
+        const uint32_t p = static_cast<uint32_t>(p64);
         const uint32_t r = in.r[p];
         ++parents;
         if (r != r_cur) {
@@ -1411,7 +1418,7 @@ __global__ void __launch_bounds__(kTpb) k_last_coop3(TopoArgs topo, LevelView in
             level_masks<W>(in, p, ta.back_old[2], ta.lo_old[2], s.adj, A3, B3, lb3);
 #pragma unroll
             for (int w = 0; w < W; ++w) {
-                R[w] = in.R[w * in.cap + p];
+                R[w] = in.R[col_at(in, w, static_cast<uint32_t>(p))];
                 c1[w] = R[w] & A1[w];
             }
             and_above<W>(c1, lb1);
