@@ -254,8 +254,14 @@ void engine_destroy(Engine *e) {
     cudaSetDevice(e->device);
     if (e->stream) cudaStreamSynchronize(e->stream);
     e->clear_graphs();
-    cudaFree(e->arena);
-    cudaFree(e->group_mem);
+    for (Slot &sl : e->slots) {
+        if (sl.stream) cudaStreamSynchronize(sl.stream);
+        cudaFree(sl.arena);
+        cudaFree(sl.group_mem);
+        if (sl.done) cudaEventDestroy(sl.done);
+        if (sl.stream) cudaStreamDestroy(sl.stream);
+    }
+    if (e->fork) cudaEventDestroy(e->fork);
     cudaFree(e->stage_reqs);
     cudaFree(e->stage_out);
     cudaFree(e->order);
@@ -308,8 +314,8 @@ int engine_stage(Engine *e, int32_t nreq, mapa_request **reqs_dev, mapa_result *
 // Frontier arena: levels 0..L carved from one allocation of frontier_cap
 // bytes.  Level 0 holds the group's roots; levels 1..L share capacity E.
 
-int plan_layout(Engine *e, int32_t group_size, int k, int T, int W, bool device_mode, int n, LayoutPlan *lay,
-                std::string *err) {
+int plan_layout(Engine *e, int slot, int32_t group_size, int k, int T, int W, bool device_mode, int n,
+                LayoutPlan *lay, std::string *err) {
     lay->L = k - T;
     const uint64_t cap = e->frontier_cap;
     const uint64_t lvl0 = static_cast<uint64_t>(std::max(group_size, 1));
@@ -368,12 +374,13 @@ int plan_layout(Engine *e, int32_t group_size, int k, int T, int W, bool device_
     if (device_mode)
         for (int ell = 0; ell < lay->L; ++ell) off_status[ell] = bump(8ull * (lay->bound[ell] / kTpb + 2));
     const uint64_t ctrl_end = total;
-    uint64_t have = e->arena_bytes;
+    Slot &sl = e->slots[slot];
+    uint64_t have = sl.arena_bytes;
     if (have < total) e->clear_graphs();  // captured launches point into the old arena
-    const int rc = ensure_device(&e->arena, &have, std::max<uint64_t>(total, 1), err);
+    const int rc = ensure_device(&sl.arena, &have, std::max<uint64_t>(total, 1), err);
     if (rc != MAPA_OK) return rc;
-    e->arena_bytes = have;
-    char *base = e->arena;
+    sl.arena_bytes = have;
+    char *base = sl.arena;
     for (int ell = 0; ell <= lay->L; ++ell) {
         LevelView &lv = lay->level[ell];
         lv.cap = ell == 0 ? lvl0 : E;
@@ -450,16 +457,18 @@ static int run_group(Engine *e, const TopoDevice &t, const GroupRun &gr_in, bool
     }
 }
 
-// Per-request group arrays (alpha, beta, key, count, best) for up to `size` requests.
-static int group_arrays(Engine *e, int32_t size, GroupArgs *g, std::string *err) {
+// Per-request group arrays (alpha, beta, key, count, best) of a slot for up
+// to `size` requests.
+static int group_arrays(Engine *e, int slot, int32_t size, GroupArgs *g, std::string *err) {
     const uint64_t n = static_cast<uint64_t>(std::max(size, 1));
     const uint64_t bytes = align_up(n * 4, 256) * 5 + align_up(n * 8, 256) * 2 + align_up(n * 32, 256);
-    uint64_t have = e->group_bytes;
+    Slot &sl = e->slots[slot];
+    uint64_t have = sl.group_bytes;
     if (have < bytes) e->clear_graphs();
-    const int rc = ensure_device(&e->group_mem, &have, bytes, err);
+    const int rc = ensure_device(&sl.group_mem, &have, bytes, err);
     if (rc != MAPA_OK) return rc;
-    e->group_bytes = have;
-    char *p = e->group_mem;
+    sl.group_bytes = have;
+    char *p = sl.group_mem;
     auto take = [&](uint64_t b) {
         char *q = p;
         p += align_up(b, 256);
@@ -549,7 +558,7 @@ int engine_run_batch(Engine *e, const TopoDevice &t, const std::vector<PatternAr
 
     if (sequential) {
         // One request at a time against the device occupancy, committing each.
-        rc = group_arrays(e, 1, &g, err);
+        rc = group_arrays(e, 0, 1, &g, err);
         if (rc != MAPA_OK) return rc;
         rc = ensure_i32(e, &e->order, &e->order_cap, nreq, err);
         if (rc != MAPA_OK) return rc;
@@ -632,21 +641,42 @@ int engine_run_batch(Engine *e, const TopoDevice &t, const std::vector<PatternAr
         }
     }
     if (runs.empty()) return end_batch(e, err);
-    GroupArgs arrays;
-    rc = group_arrays(e, largest, &arrays, err);
-    if (rc != MAPA_OK) return rc;
+    // The groups are independent: they run concurrently, one per slot (own
+    // stream, arena and group arrays; round robin beyond kSlots), so one
+    // group's small early levels overlap another's large ones.
+    // With per-kernel timing on, groups run one after another so each timed
+    // kernel has the GPU to itself.
+    (void)largest;
+    const int nslots = e->timing ? 1 : static_cast<int>(std::min<size_t>(kSlots, runs.size()));
+    int32_t largest_in[kSlots] = {0, 0, 0, 0};
+    for (size_t i = 0; i < runs.size(); ++i)
+        largest_in[i % nslots] = std::max(largest_in[i % nslots], runs[i].g.size);
+    GroupArgs arrays[kSlots];
+    for (int s = 0; s < nslots; ++s) {
+        rc = group_arrays(e, s, largest_in[s], &arrays[s], err);
+        if (rc != MAPA_OK) return rc;
+        Slot &sl = e->slots[s];
+        if (nslots > 1 && !sl.stream) {
+            MAPA_CUDA_TRY(cudaStreamCreateWithFlags(&sl.stream, cudaStreamNonBlocking));
+            MAPA_CUDA_TRY(cudaEventCreateWithFlags(&sl.done, cudaEventDisableTiming));
+        }
+    }
+    if (nslots > 1 && !e->fork) MAPA_CUDA_TRY(cudaEventCreateWithFlags(&e->fork, cudaEventDisableTiming));
     rc = ensure_i32(e, &e->overflow, &e->overflow_cap, static_cast<int64_t>(runs.size()), err);
     if (rc != MAPA_OK) return rc;
     for (size_t i = 0; i < runs.size(); ++i) {
         GroupRun &gr = runs[i];
-        gr.g.alpha = arrays.alpha;
-        gr.g.beta = arrays.beta;
-        gr.g.best_s = arrays.best_s;
-        gr.g.best_valid = arrays.best_valid;
-        gr.g.key = arrays.key;
-        gr.g.count = arrays.count;
-        gr.g.best_t = arrays.best_t;
-        gr.g.thr = arrays.thr;
+        gr.slot = static_cast<int>(i % nslots);
+        gr.stream = nslots > 1 ? e->slots[gr.slot].stream : nullptr;
+        const GroupArgs &a = arrays[gr.slot];
+        gr.g.alpha = a.alpha;
+        gr.g.beta = a.beta;
+        gr.g.best_s = a.best_s;
+        gr.g.best_valid = a.best_valid;
+        gr.g.key = a.key;
+        gr.g.count = a.count;
+        gr.g.best_t = a.best_t;
+        gr.g.thr = a.thr;
         gr.overflow = e->overflow + i;
     }
     // Every group of the batch, device-driven.  A batch whose shape was seen
@@ -654,9 +684,19 @@ int engine_run_batch(Engine *e, const TopoDevice &t, const std::vector<PatternAr
     // replays its captured graph; a new shape is captured, then replayed.
     auto enqueue_all = [&]() -> int {
         MAPA_CUDA_TRY(cudaMemsetAsync(e->overflow, 0, sizeof(int32_t) * runs.size(), e->stream));
+        if (nslots > 1) {
+            MAPA_CUDA_TRY(cudaEventRecord(e->fork, e->stream));
+            for (int s = 0; s < nslots; ++s) MAPA_CUDA_TRY(cudaStreamWaitEvent(e->slots[s].stream, e->fork, 0));
+        }
         for (size_t i = 0; i < runs.size(); ++i) {
             const int r = run_group(e, t, runs[i], true, err);
             if (r != MAPA_OK) return r;
+        }
+        if (nslots > 1) {
+            for (int s = 0; s < nslots; ++s) {
+                MAPA_CUDA_TRY(cudaEventRecord(e->slots[s].done, e->slots[s].stream));
+                MAPA_CUDA_TRY(cudaStreamWaitEvent(e->stream, e->slots[s].done, 0));
+            }
         }
         return MAPA_OK;
     };
@@ -665,9 +705,15 @@ int engine_run_batch(Engine *e, const TopoDevice &t, const std::vector<PatternAr
         if (rc != MAPA_OK) return rc;
     } else {
         std::vector<int64_t> key = {t.id, reinterpret_cast<int64_t>(reqs_dev), reinterpret_cast<int64_t>(out_dev),
-                                    nreq, reinterpret_cast<int64_t>(e->arena), static_cast<int64_t>(e->arena_bytes),
-                                    reinterpret_cast<int64_t>(e->group_mem), reinterpret_cast<int64_t>(e->overflow),
-                                    reinterpret_cast<int64_t>(e->order), reinterpret_cast<int64_t>(e->stream)};
+                                    nreq, reinterpret_cast<int64_t>(e->overflow), reinterpret_cast<int64_t>(e->order),
+                                    reinterpret_cast<int64_t>(e->stream), nslots};
+        for (int s = 0; s < nslots; ++s) {
+            const Slot &sl = e->slots[s];
+            key.push_back(reinterpret_cast<int64_t>(sl.arena));
+            key.push_back(static_cast<int64_t>(sl.arena_bytes));
+            key.push_back(reinterpret_cast<int64_t>(sl.group_mem));
+            key.push_back(reinterpret_cast<int64_t>(sl.stream));
+        }
         for (const GroupRun &gr : runs) {
             key.push_back(gr.pat->id);
             key.push_back(gr.g.size);
@@ -689,7 +735,7 @@ int engine_run_batch(Engine *e, const TopoDevice &t, const std::vector<PatternAr
             // plan every group once outside capture so no allocation happens inside it
             for (const GroupRun &gr : runs) {
                 LayoutPlan lay;
-                rc = plan_layout(e, gr.g.size, gr.pat->k, gr.tail, t.W, true, t.n, &lay, err);
+                rc = plan_layout(e, gr.slot, gr.g.size, gr.pat->k, gr.tail, t.W, true, t.n, &lay, err);
                 if (rc != MAPA_OK) return rc;
             }
             const mapa_stats before = e->st;
@@ -733,7 +779,11 @@ int engine_run_batch(Engine *e, const TopoDevice &t, const std::vector<PatternAr
     MAPA_CUDA_TRY(cudaStreamSynchronize(e->stream));
     for (size_t i = 0; i < runs.size(); ++i) {
         if (!ovf[i]) continue;
-        rc = run_group(e, t, runs[i], false, err);
+        // redo on the engine's stream (the slot's memory is free by now), so
+        // its results are in place before anything later on that stream
+        GroupRun redo = runs[i];
+        redo.stream = nullptr;
+        rc = run_group(e, t, redo, false, err);
         if (rc != MAPA_OK) return rc;
     }
     return end_batch(e, err);
@@ -758,7 +808,7 @@ int engine_run_chain(Engine *e, const TopoDevice &t, const std::vector<PatternAr
     g.occupancy = t.occupancy;
     g.size = 1;
     int rc = begin_batch(e, err);
-    if (rc == MAPA_OK) rc = group_arrays(e, 1, &g, err);
+    if (rc == MAPA_OK) rc = group_arrays(e, 0, 1, &g, err);
     if (rc == MAPA_OK) rc = ensure_i32(e, &e->order, &e->order_cap, n, err);
     if (rc == MAPA_OK) rc = ensure_i32(e, &e->overflow, &e->overflow_cap, n, err);
     if (rc != MAPA_OK) return rc;

@@ -25,16 +25,27 @@ namespace mapa {
 
 constexpr int kStatWords = 8;
 
+// Memory and stream of one request group in flight.  The groups of an
+// independent batch run concurrently, one per slot (round robin beyond
+// kSlots); every other path uses slot 0 on the engine's stream.
+struct Slot {
+    char *arena = nullptr;      // frontier levels and their control words
+    uint64_t arena_bytes = 0;
+    char *group_mem = nullptr;  // per-request group arrays
+    uint64_t group_bytes = 0;
+    cudaStream_t stream = nullptr;  // concurrent groups (created on first use)
+    cudaEvent_t done = nullptr;
+};
+constexpr int kSlots = 4;
+
 struct Engine {
     int device = 0;
     int sm_count = 0;
     cudaStream_t own_stream = nullptr;
     cudaStream_t stream = nullptr;
     uint64_t frontier_cap = 0;
-    char *arena = nullptr;        // frontier levels and their control words
-    uint64_t arena_bytes = 0;
-    char *group_mem = nullptr;    // per-request group arrays
-    uint64_t group_bytes = 0;
+    Slot slots[kSlots];
+    cudaEvent_t fork = nullptr;  // start of the concurrent groups of a batch
     mapa_request *stage_reqs = nullptr;
     mapa_result *stage_out = nullptr;
     int32_t stage_cap = 0;
@@ -98,6 +109,8 @@ struct GroupRun {
     int32_t *overflow;      // device flag for this group (device-driven path)
     bool bounded = false;   // some request of the group is in bounded mode (g.thr set)
     bool sens = false;      // the group's requests are bandwidth-sensitive
+    int slot = 0;           // arena of the group
+    cudaStream_t stream = nullptr;  // stream of its launches (nullptr = the engine's)
 };
 
 // Per-mask-width entry points (mapa_engine_w{1,2,4,8}.cu).

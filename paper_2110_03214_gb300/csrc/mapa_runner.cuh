@@ -29,8 +29,8 @@ struct LayoutPlan {
     uint64_t ctrl_bytes = 0;
 };
 
-int plan_layout(Engine *e, int32_t group_size, int k, int T, int W, bool device_mode, int n, LayoutPlan *lay,
-                std::string *err);
+int plan_layout(Engine *e, int slot, int32_t group_size, int k, int T, int W, bool device_mode, int n,
+                LayoutPlan *lay, std::string *err);
 void launch_scan(const unsigned long long *cnt, unsigned long long *off, uint64_t nb, cudaStream_t s);
 
 inline TailArgs make_tail_args(const PatternArgs &pat, int T, int W, int C) {
@@ -70,13 +70,15 @@ struct Runner {
     const PatternArgs &pat;
     GroupArgs g;
     TopoArgs targs;  // the graph as the scoring kernels see it (class codes for a sensitive group)
+    cudaStream_t st;  // stream of the group's launches
     LayoutPlan lay;
     TailArgs ta;
     size_t smem_adj, smem_all;
     std::string *err;
 
     Runner(Engine *e_, const TopoDevice &t_, const GroupRun &gr_, std::string *err_)
-        : e(e_), t(t_), gr(gr_), pat(*gr_.pat), g(gr_.g), targs(gr_.sens ? t_.args_effbw() : t_.args()), err(err_) {
+        : e(e_), t(t_), gr(gr_), pat(*gr_.pat), g(gr_.g), targs(gr_.sens ? t_.args_effbw() : t_.args()),
+          st(gr_.stream ? gr_.stream : e_->stream), err(err_) {
         smem_adj = topo_smem_bytes(t.n, W, t.C, false);
         smem_all = topo_smem_bytes(t.n, W, t.C, true);
         ta = make_tail_args(pat, T, W, t.C);
@@ -117,13 +119,13 @@ struct Runner {
 
     int setup(unsigned long long *count0) {
         const unsigned sgrid = static_cast<unsigned>(std::min<uint64_t>(ceil_div(g.size, kWarps), 4096));
-        k_setup<W><<<sgrid, kTpb, smem_all, e->stream>>>(targs, g, lay.level[0], count0);
+        k_setup<W><<<sgrid, kTpb, smem_all, st>>>(targs, g, lay.level[0], count0);
         MAPA_CUDA_TRY(cudaGetLastError());
         e->st.kernel_launches += 1;
         if (g.thr) {
             // bounded mode: seed scores for the cut-offs, one warp per request
             const unsigned dgrid = static_cast<unsigned>(std::min<uint64_t>(ceil_div(g.size, kWarps), 4096));
-            k_dive<W, CT><<<dgrid, kTpb, smem_all, e->stream>>>(targs, pat, g, lay.level[0], e->dive_steps);
+            k_dive<W, CT><<<dgrid, kTpb, smem_all, st>>>(targs, pat, g, lay.level[0], e->dive_steps);
             MAPA_CUDA_TRY(cudaGetLastError());
             e->st.kernel_launches += 1;
         }
@@ -132,7 +134,7 @@ struct Runner {
 
     int finalize() {
         const unsigned fgrid = static_cast<unsigned>(std::min<uint64_t>(ceil_div(g.size, 128), 4096));
-        k_finalize<W><<<fgrid, 128, smem_all, e->stream>>>(t.args(), pat, g);  // real weights: AggBW, PreservedBW
+        k_finalize<W><<<fgrid, 128, smem_all, st>>>(t.args(), pat, g);  // real weights: AggBW, PreservedBW
         MAPA_CUDA_TRY(cudaGetLastError());
         e->st.kernel_launches += 1;
         e->st.requests += static_cast<uint64_t>(g.size);
@@ -152,7 +154,7 @@ struct Runner {
         if (e->timing) {
             ev0 = e->next_event();
             ev1 = e->next_event();
-            MAPA_CUDA_TRY(cudaEventRecord(ev0, e->stream));
+            MAPA_CUDA_TRY(cudaEventRecord(ev0, st));
         }
         bool launched = false;
         const unsigned sgrid =
@@ -160,7 +162,7 @@ struct Runner {
         if constexpr (T == 1) {
             if (g.sens) {
                 // bandwidth-sensitive group: argmax over Eq. 2 ranks
-                k_last_short<W, 1, true><<<sgrid, kTpb, smem_all, e->stream>>>(
+                k_last_short<W, 1, true><<<sgrid, kTpb, smem_all, st>>>(
                     targs, in, count_dev, count_host, ta, g.alpha, g.beta, g.key, g.count, e->d_stats, g.effbw_rank);
                 launched = true;
             }
@@ -172,7 +174,7 @@ struct Runner {
                 if (!nb3) nb3 = blocks_per_sm(k_last_coop3<W>, smem_all);
                 const unsigned cgrid = static_cast<unsigned>(std::max<uint64_t>(
                     1, std::min<uint64_t>(ceil_div(max_parents, kTpb), uint64_t(e->sm_count) * nb3)));
-                k_last_coop3<W><<<cgrid, kTpb, smem_all, e->stream>>>(targs, in, count_dev, count_host, ta, g.alpha,
+                k_last_coop3<W><<<cgrid, kTpb, smem_all, st>>>(targs, in, count_dev, count_host, ta, g.alpha,
                                                                      g.beta, g.key, g.count, tile_ctr, e->d_stats);
                 launched = true;
             }
@@ -180,22 +182,22 @@ struct Runner {
         if constexpr (T <= 2 && W <= 2) {
             if (!g.thr && !launched) {
                 // masks of at most 64 vertices: one tile of parents per block
-                k_last_short<W, T, false><<<sgrid, kTpb, smem_all, e->stream>>>(
+                k_last_short<W, T, false><<<sgrid, kTpb, smem_all, st>>>(
                     targs, in, count_dev, count_host, ta, g.alpha, g.beta, g.key, g.count, e->d_stats, nullptr);
                 launched = true;
             }
         }
         if (launched) {
         } else if (g.thr) {
-            k_last<W, CT, T, true><<<grid, kTpb, smem_all, e->stream>>>(
+            k_last<W, CT, T, true><<<grid, kTpb, smem_all, st>>>(
                 targs, in, count_dev, count_host, ta, g.alpha, g.beta, g.key, g.count, tile_ctr, e->d_stats, g.thr);
         } else {
-            k_last<W, CT, T, false><<<grid, kTpb, smem_all, e->stream>>>(
+            k_last<W, CT, T, false><<<grid, kTpb, smem_all, st>>>(
                 targs, in, count_dev, count_host, ta, g.alpha, g.beta, g.key, g.count, tile_ctr, e->d_stats, g.thr);
         }
-        if (e->timing) MAPA_CUDA_TRY(cudaEventRecord(ev1, e->stream));
+        if (e->timing) MAPA_CUDA_TRY(cudaEventRecord(ev1, st));
         const unsigned rgrid = static_cast<unsigned>(std::min<uint64_t>(ceil_div(g.size, 256), 1024));
-        k_resolve<W, CT, T><<<rgrid, 256, smem_all, e->stream>>>(targs, in, count_dev, count_host, ta, g);
+        k_resolve<W, CT, T><<<rgrid, 256, smem_all, st>>>(targs, in, count_dev, count_host, ta, g);
         MAPA_CUDA_TRY(cudaGetLastError());
         e->st.kernel_launches += 2;
         e->st.tail_launches += 1;
@@ -206,9 +208,9 @@ struct Runner {
     int run_device() {
         int rc = allow_smem();
         if (rc != MAPA_OK) return rc;
-        rc = plan_layout(e, g.size, pat.k, T, W, true, t.n, &lay, err);
+        rc = plan_layout(e, gr.slot, g.size, pat.k, T, W, true, t.n, &lay, err);
         if (rc != MAPA_OK) return rc;
-        MAPA_CUDA_TRY(cudaMemsetAsync(lay.ctrl, 0, lay.ctrl_bytes, e->stream));
+        MAPA_CUDA_TRY(cudaMemsetAsync(lay.ctrl, 0, lay.ctrl_bytes, st));
         rc = setup(lay.counts);
         if (rc != MAPA_OK) return rc;
         static int nb_expand = 0;
@@ -217,7 +219,7 @@ struct Runner {
         for (int ell = 0; ell < lay.L; ++ell) {
             const unsigned grid = static_cast<unsigned>(std::max<uint64_t>(
                 1, std::min<uint64_t>(ceil_div(lay.bound[ell], kTpb), uint64_t(e->sm_count) * nb_expand)));
-            expand<<<grid, kTpb, smem_all, e->stream>>>(
+            expand<<<grid, kTpb, smem_all, st>>>(
                 targs, lay.level[ell], lay.level[ell + 1], ell, pat.back[ell], pat.lo[ell], lay.counts + ell,
                 lay.counts + ell + 1, lay.level[ell + 1].cap, lay.tiles + ell, lay.status[ell], gr.overflow, g.alpha,
                 g.beta, e->d_error, e->d_stats, entry_bytes(ell + 1, W), g.thr, bound_at(ell));
@@ -234,29 +236,29 @@ struct Runner {
     int process(int ell, uint64_t P) {
         if (P == 0) return MAPA_OK;
         if (ell == lay.L) {
-            MAPA_CUDA_TRY(cudaMemsetAsync(lay.tiles, 0, sizeof(unsigned int), e->stream));
+            MAPA_CUDA_TRY(cudaMemsetAsync(lay.tiles, 0, sizeof(unsigned int), st));
             return last_level(nullptr, P, lay.tiles, P);
         }
         const LevelView &in = lay.level[ell];
         const LevelView &out = lay.level[ell + 1];
         const uint64_t nb = ceil_div(P, kTile);
-        k_count<W><<<static_cast<unsigned>(nb), kTpb, g.thr ? smem_all : smem_adj, e->stream>>>(
+        k_count<W><<<static_cast<unsigned>(nb), kTpb, g.thr ? smem_all : smem_adj, st>>>(
             targs, in, P, pat.back[ell], pat.lo[ell], lay.warp_cnt[ell], lay.blk_cnt[ell], g.thr, g.alpha, g.beta,
             bound_at(ell));
-        launch_scan(lay.blk_cnt[ell], lay.blk_off[ell], nb, e->stream);
+        launch_scan(lay.blk_cnt[ell], lay.blk_off[ell], nb, st);
         MAPA_CUDA_TRY(cudaGetLastError());
         e->st.kernel_launches += 2;
         MAPA_CUDA_TRY(cudaMemcpyAsync(e->h_pinned, lay.blk_off[ell] + nb, sizeof(unsigned long long),
-                                      cudaMemcpyDeviceToHost, e->stream));
-        MAPA_CUDA_TRY(cudaStreamSynchronize(e->stream));
+                                      cudaMemcpyDeviceToHost, st));
+        MAPA_CUDA_TRY(cudaStreamSynchronize(st));
         const unsigned long long total = e->h_pinned[0];
         if (total == 0) return MAPA_OK;
         std::vector<unsigned long long> off;
         if (total > lay.E) {
             off.resize(nb + 1);
             MAPA_CUDA_TRY(cudaMemcpyAsync(off.data(), lay.blk_off[ell], sizeof(unsigned long long) * (nb + 1),
-                                          cudaMemcpyDeviceToHost, e->stream));
-            MAPA_CUDA_TRY(cudaStreamSynchronize(e->stream));
+                                          cudaMemcpyDeviceToHost, st));
+            MAPA_CUDA_TRY(cudaStreamSynchronize(st));
         }
         uint64_t b0 = 0;
         while (b0 < nb) {
@@ -269,7 +271,7 @@ struct Runner {
                 }
             }
             const uint64_t children = total > lay.E ? off[b1] - off[b0] : total;
-            k_write<W, CT><<<static_cast<unsigned>(b1 - b0), kTpb, smem_all, e->stream>>>(
+            k_write<W, CT><<<static_cast<unsigned>(b1 - b0), kTpb, smem_all, st>>>(
                 targs, in, P, ell, pat.back[ell], pat.lo[ell], out, lay.warp_cnt[ell], lay.blk_off[ell], b0,
                 g.alpha, g.beta, g.thr, bound_at(ell));
             MAPA_CUDA_TRY(cudaGetLastError());
@@ -286,7 +288,7 @@ struct Runner {
     int run_host() {
         int rc = allow_smem();
         if (rc != MAPA_OK) return rc;
-        rc = plan_layout(e, g.size, pat.k, T, W, false, t.n, &lay, err);
+        rc = plan_layout(e, gr.slot, g.size, pat.k, T, W, false, t.n, &lay, err);
         if (rc != MAPA_OK) return rc;
         rc = setup(nullptr);
         if (rc != MAPA_OK) return rc;
