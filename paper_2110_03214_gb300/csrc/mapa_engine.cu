@@ -97,6 +97,37 @@ __global__ void k_commit(mapa_result *res, uint32_t *occ, int64_t *owner, unsign
     res->job_id = job;
 }
 
+// One step of a commit chain, last kernel of the step: commits the decision
+// at batch position *cursor as k_commit does, logs the step's overflow flag
+// for that position and clears it, and moves the cursor to the next request.
+// Every kernel of a step reads its request through the cursor, so the launch
+// sequence of a step is the same for every request of a pattern and can be
+// replayed from one captured graph.
+__global__ void k_commit_step(mapa_result *out, int32_t *chain, uint32_t *occ, int64_t *owner,
+                              unsigned long long *next_job, int32_t *blocked, int32_t *ovf_log) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    const int32_t pos = chain[0];
+    mapa_result *res = out + pos;
+    ovf_log[pos] = chain[1];
+    chain[1] = 0;
+    chain[0] = pos + 1;
+    if (blocked) {
+        if (*blocked || res->status == MAPA_NO_FIT) {
+            *blocked = 1;
+            res->reserved = kDeferred;
+            return;
+        }
+    }
+    if (res->status != MAPA_OK) return;
+    const long long job = static_cast<long long>(atomicAdd(next_job, 1ull)) + 1;
+    for (int i = 0; i < res->k; ++i) {
+        const int v = res->verts[i];
+        occ[v >> 5] |= 1u << (v & 31);
+        owner[v] = job;
+    }
+    res->job_id = job;
+}
+
 // State management (Sec. 3.6): return a job's vertices to the free pool.
 __global__ void k_release(int n, long long job, uint32_t *occ, int64_t *owner, int32_t *freed) {
     for (int v = threadIdx.x; v < n; v += blockDim.x) {
@@ -237,12 +268,13 @@ Engine *engine_create(int device, uint64_t frontier_cap, std::string *err) {
     if (cudaStreamCreateWithFlags(&en->own_stream, cudaStreamNonBlocking) != cudaSuccess ||
         cudaMalloc(&en->d_error, sizeof(int32_t)) != cudaSuccess ||
         cudaMalloc(&en->d_stats, kStatWords * sizeof(unsigned long long)) != cudaSuccess ||
-        cudaMalloc(&en->d_blocked, sizeof(int32_t)) != cudaSuccess ||
+        cudaMalloc(&en->d_chain, 3 * sizeof(int32_t)) != cudaSuccess ||
         cudaMallocHost(&en->h_pinned, 64 * sizeof(unsigned long long)) != cudaSuccess) {
         if (err) *err = "context allocation failed";
         engine_destroy(en);
         return nullptr;
     }
+    en->d_blocked = en->d_chain + 2;
     en->stream = en->own_stream;
     cudaMemset(en->d_error, 0, sizeof(int32_t));
     cudaMemset(en->d_stats, 0, kStatWords * sizeof(unsigned long long));
@@ -269,7 +301,7 @@ void engine_destroy(Engine *e) {
     cudaFree(e->overflow);
     cudaFree(e->d_error);
     cudaFree(e->d_stats);
-    cudaFree(e->d_blocked);
+    cudaFree(e->d_chain);
     cudaFree(e->effbw_rank);
     cudaFree(e->effbw_milli);
     for (cudaEvent_t ev : e->events) cudaEventDestroy(ev);
@@ -796,9 +828,15 @@ int engine_run_batch(Engine *e, const TopoDevice &t, const std::vector<PatternAr
 // MAPA_E_NOMEM (its commit would not be trustworthy).
 int engine_run_chain(Engine *e, const TopoDevice &t, const std::vector<PatternArgs> &patterns, int32_t n,
                      const int32_t *pattern_ids, const uint8_t *kinds, const mapa_request *reqs_dev,
-                     mapa_result *out_dev, bool fifo_wait, std::string *err) {
+                     mapa_result *out_dev, bool fifo_wait, mapa_result *out_host, std::string *err) {
     MAPA_CUDA_TRY(cudaSetDevice(e->device));
     if (n <= 0) return MAPA_OK;
+    const int32_t npat = static_cast<int32_t>(patterns.size());
+    for (int32_t i = 0; i < n; ++i)
+        if (pattern_ids[i] < 0 || pattern_ids[i] >= npat) {
+            if (err) *err = "unknown pattern id in a served request";
+            return MAPA_E_INVALID;
+        }
     GroupArgs g;
     memset(&g, 0, sizeof(g));
     g.reqs = reqs_dev;
@@ -807,36 +845,89 @@ int engine_run_chain(Engine *e, const TopoDevice &t, const std::vector<PatternAr
     g.error = e->d_error;
     g.occupancy = t.occupancy;
     g.size = 1;
+    g.req_index = e->d_chain;  // the cursor: batch position of the step's request
     int rc = begin_batch(e, err);
     if (rc == MAPA_OK) rc = group_arrays(e, 0, 1, &g, err);
-    if (rc == MAPA_OK) rc = ensure_i32(e, &e->order, &e->order_cap, n, err);
     if (rc == MAPA_OK) rc = ensure_i32(e, &e->overflow, &e->overflow_cap, n, err);
     if (rc != MAPA_OK) return rc;
-    std::vector<int32_t> idx(n);
-    for (int32_t i = 0; i < n; ++i) idx[i] = i;
-    MAPA_CUDA_TRY(cudaMemcpyAsync(e->order, idx.data(), sizeof(int32_t) * n, cudaMemcpyHostToDevice, e->stream));
-    MAPA_CUDA_TRY(cudaMemsetAsync(e->overflow, 0, sizeof(int32_t) * n, e->stream));
-    MAPA_CUDA_TRY(cudaMemsetAsync(e->d_blocked, 0, sizeof(int32_t), e->stream));
-    const int32_t npat = static_cast<int32_t>(patterns.size());
-    for (int32_t i = 0; i < n; ++i) {
-        const int32_t pid = pattern_ids[i];
-        if (pid < 0 || pid >= npat) {
-            if (err) *err = "unknown pattern id in a served request";
-            return MAPA_E_INVALID;
-        }
-        g.req_index = e->order + i;
-        GroupRun gr{&patterns[pid], g, tail_depth(e, t, patterns[pid]), e->overflow + i,
-                    kinds != nullptr && (kinds[i] & kKindBounded) != 0,
-                    kinds != nullptr && (kinds[i] & kKindSensitive) != 0};
-        rc = run_group(e, t, gr, true, err);
-        if (rc != MAPA_OK) return rc;
-        k_commit<<<1, 32, 0, e->stream>>>(out_dev + i, t.occupancy, t.owner, t.next_job,
-                                          fifo_wait ? e->d_blocked : nullptr);
+    // cursor, step overflow flag and FIFO-wait flag; every step writes its
+    // own entry of the overflow log
+    MAPA_CUDA_TRY(cudaMemsetAsync(e->d_chain, 0, 3 * sizeof(int32_t), e->stream));
+    int32_t *blocked = fifo_wait ? e->d_blocked : nullptr;
+    auto step = [&](const GroupRun &gr) -> int {
+        const int r = run_group(e, t, gr, true, err);
+        if (r != MAPA_OK) return r;
+        k_commit_step<<<1, 32, 0, e->stream>>>(out_dev, e->d_chain, t.occupancy, t.owner, t.next_job, blocked,
+                                                e->overflow);
         MAPA_CUDA_TRY(cudaGetLastError());
         e->st.kernel_launches += 1;
+        return MAPA_OK;
+    };
+    for (int32_t i = 0; i < n; ++i) {
+        const PatternArgs &pat = patterns[pattern_ids[i]];
+        const bool bounded = kinds != nullptr && (kinds[i] & kKindBounded) != 0;
+        const bool sens = kinds != nullptr && (kinds[i] & kKindSensitive) != 0;
+        const GroupRun gr{&pat, g, tail_depth(e, t, pat), e->d_chain + 1, bounded, sens};
+        if (!e->use_graphs || e->timing) {
+            rc = step(gr);
+            if (rc != MAPA_OK) return rc;
+            continue;
+        }
+        // the launches of a step depend only on these: replay them from a
+        // graph once a step of the same kind has run directly
+        const Slot &sl = e->slots[0];
+        const std::vector<int64_t> key = {-1, t.id, pat.id, gr.tail, bounded, sens, fifo_wait,
+                                          reinterpret_cast<int64_t>(reqs_dev), reinterpret_cast<int64_t>(out_dev),
+                                          reinterpret_cast<int64_t>(sl.arena), static_cast<int64_t>(sl.arena_bytes),
+                                          reinterpret_cast<int64_t>(sl.group_mem), reinterpret_cast<int64_t>(e->overflow),
+                                          reinterpret_cast<int64_t>(e->stream)};
+        auto it = e->graphs.find(key);
+        if (it == e->graphs.end() && e->shapes_seen.count(key)) {
+            if (e->graphs.size() >= 64) e->clear_graphs();
+            const mapa_stats before = e->st;
+            cudaGraph_t graph = nullptr;
+            MAPA_CUDA_TRY(cudaStreamBeginCapture(e->stream, cudaStreamCaptureModeRelaxed));
+            rc = step(gr);
+            const cudaError_t ce = cudaStreamEndCapture(e->stream, &graph);
+            if (rc != MAPA_OK) {
+                if (graph) cudaGraphDestroy(graph);
+                return rc;
+            }
+            Engine::GraphEntry entry;
+            cudaError_t ie = ce;
+            if (ce == cudaSuccess) ie = cudaGraphInstantiate(&entry.exec, graph, 0);
+            if (graph) cudaGraphDestroy(graph);
+            const mapa_stats delta_src = e->st;
+            e->st = before;
+            if (ie != cudaSuccess) {
+                cudaGetLastError();
+                e->use_graphs = false;  // capture not possible here: direct launches from now on
+                rc = step(gr);
+                if (rc != MAPA_OK) return rc;
+                continue;
+            }
+            entry.delta.kernel_launches = delta_src.kernel_launches - before.kernel_launches;
+            entry.delta.tail_launches = delta_src.tail_launches - before.tail_launches;
+            entry.delta.requests = delta_src.requests - before.requests;
+            it = e->graphs.emplace(key, entry).first;
+        }
+        if (it != e->graphs.end()) {
+            MAPA_CUDA_TRY(cudaGraphLaunch(it->second.exec, e->stream));
+            e->st.kernel_launches += it->second.delta.kernel_launches;
+            e->st.tail_launches += it->second.delta.tail_launches;
+            e->st.requests += it->second.delta.requests;
+        } else {
+            if (e->shapes_seen.size() >= 256) e->shapes_seen.clear();
+            e->shapes_seen[key] = 1;
+            rc = step(gr);
+            if (rc != MAPA_OK) return rc;
+        }
     }
     std::vector<int32_t> ovf(n);
     MAPA_CUDA_TRY(cudaMemcpyAsync(ovf.data(), e->overflow, sizeof(int32_t) * n, cudaMemcpyDeviceToHost, e->stream));
+    if (out_host)
+        MAPA_CUDA_TRY(
+            cudaMemcpyAsync(out_host, out_dev, sizeof(mapa_result) * n, cudaMemcpyDeviceToHost, e->stream));
     rc = end_batch(e, err);
     if (rc != MAPA_OK) return rc;
     for (int32_t i = 0; i < n; ++i)

@@ -57,7 +57,8 @@ struct Engine {
     int32_t overflow_cap = 0;
     int32_t *d_error = nullptr;
     unsigned long long *d_stats = nullptr;  // kStatWords counters of the current batch
-    int32_t *d_blocked = nullptr;           // FIFO-wait flag of a commit chain
+    int32_t *d_blocked = nullptr;           // FIFO-wait flag of a commit chain (= d_chain + 2)
+    int32_t *d_chain = nullptr;             // [3] commit chain: cursor, step overflow flag, FIFO-wait flag
     int32_t *effbw_rank = nullptr;          // [kEffbwRadix^3] (built on first use)
     int32_t *effbw_milli = nullptr;
     unsigned long long *h_pinned = nullptr;  // small pinned scratch

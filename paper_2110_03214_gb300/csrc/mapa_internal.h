@@ -175,9 +175,11 @@ int engine_commit_round(Engine *e, const TopoDevice &t, mapa_result *out_dev, in
 // kinds[i]: bit 0 = request i is in bounded mode, bit 1 = bandwidth-sensitive
 // (nullptr = neither, for every request).
 constexpr uint8_t kKindBounded = 1, kKindSensitive = 2;
+// out_host (may be null): pinned host copy of the n results, filled before
+// the call returns.
 int engine_run_chain(Engine *e, const TopoDevice &t, const std::vector<PatternArgs> &patterns, int32_t n,
                      const int32_t *pattern_ids, const uint8_t *kinds, const mapa_request *reqs_dev,
-                     mapa_result *out_dev, bool fifo_wait, std::string *err);
+                     mapa_result *out_dev, bool fifo_wait, mapa_result *out_host, std::string *err);
 int engine_release_many(Engine *e, const TopoDevice &t, const int64_t *jobs_dev, int32_t njobs, std::string *err);
 
 // Scratch for staging host batches.

@@ -264,14 +264,9 @@ int decide_round(mapa_server srv, std::vector<Pending> &round, std::vector<mapa_
             return MAPA_E_CUDA;
         }
         rc = mapa::engine_run_chain(ctx->engine, t, ctx->pattern_args, m, chain_pids.data() + c0,
-                                    chain_bounded.data() + c0, srv->d_reqs, srv->d_out, srv->fifo_wait, err);
+                                    chain_bounded.data() + c0, srv->d_reqs, srv->d_out, srv->fifo_wait, srv->h_out,
+                                    err);
         if (rc != MAPA_OK) return rc;
-        if (cudaMemcpyAsync(srv->h_out, srv->d_out, sizeof(mapa_result) * m, cudaMemcpyDeviceToHost, st) !=
-                cudaSuccess ||
-            cudaStreamSynchronize(st) != cudaSuccess) {
-            if (err) *err = "chain result copy failed";
-            return MAPA_E_CUDA;
-        }
         for (int32_t j = 0; j < m; ++j) {
             const int32_t i = chain[c0 + j];
             memcpy(&snaps[static_cast<size_t>(i) * MAPA_MASK_WORDS], cur, sizeof(cur));
