@@ -190,7 +190,7 @@ class NvmlSampler:
 def _kernel_source_hash() -> str:
     """Hash of the sources that define the fused-tail kernel and its launch."""
     h = hashlib.sha256()
-    for name in ("mapa_kernels.cuh", "mapa_runner.cuh", "mapa_engine.cu"):
+    for name in ("mapa_kernels.cuh", "mapa_runner.cuh"):
         with open(os.path.join(ROOT, "paper_2110_03214_gb300", "csrc", name), "rb") as f:
             h.update(f.read())
     return h.hexdigest()[:16]
