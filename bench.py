@@ -295,6 +295,8 @@ def simulator_measure(M, W, jobs_count: int, seed: int = 6):
     of bandwidth-sensitive and -insensitive jobs, the makespan in cycles, and
     the decisions per second of the run (every non-Baseline decision on the
     GPU)."""
+    import numpy as np
+
     names = {M.MAPA_SIM_BASELINE: "baseline", M.MAPA_SIM_GREEDY: "greedy", M.MAPA_SIM_PRESERVE: "preserve",
              M.MAPA_SIM_EFFBW: "effbw"}
     jobs = W.sim_jobs(jobs_count, seed=seed)
