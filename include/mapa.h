@@ -148,8 +148,11 @@ typedef struct {
 /* ---- context ----------------------------------------------------------- */
 
 /* Creates a context on CUDA device `device`.  frontier_mem_cap bounds the
- * device memory used for partial-match frontiers, in bytes (0 = 4 GiB); the
- * enumeration proceeds in chunks so any request fits, only slower.
+ * device memory used for the partial-match frontier of one pattern group,
+ * in bytes (0 = 4 GiB); the enumeration proceeds in chunks so any request
+ * fits, only slower.  The pattern groups of an independent batch run
+ * concurrently, up to four at a time, each with its own frontier, so a
+ * context may hold up to four times this amount.
  * Returns MAPA_E_CUDA if the device cannot be used. */
 int mapa_ctx_create(int device, uint64_t frontier_mem_cap, mapa_ctx *out);
 

@@ -659,7 +659,6 @@ int engine_run_batch(Engine *e, const TopoDevice &t, const std::vector<PatternAr
     e->st.kernel_launches += 2;
 
     std::vector<GroupRun> runs;
-    int32_t largest = 0;
     for (int32_t key = 0; key < nkey; ++key) {
         const int32_t p = key % npat;
         const bool sens = key >= npat;
@@ -667,7 +666,6 @@ int engine_run_batch(Engine *e, const TopoDevice &t, const std::vector<PatternAr
             GroupArgs gs = g;
             gs.size = std::min(kMaxGroup, hist[key] - s0);
             gs.req_index = e->order + start[key] + s0;
-            largest = std::max(largest, gs.size);
             runs.push_back(GroupRun{&patterns[p], gs, tail_depth(e, t, patterns[p]), nullptr,
                                     hist[nkey + key] > 0, sens});
         }
@@ -678,7 +676,6 @@ int engine_run_batch(Engine *e, const TopoDevice &t, const std::vector<PatternAr
     // group's small early levels overlap another's large ones.
     // With per-kernel timing on, groups run one after another so each timed
     // kernel has the GPU to itself.
-    (void)largest;
     const int nslots = e->timing ? 1 : static_cast<int>(std::min<size_t>(kSlots, runs.size()));
     int32_t largest_in[kSlots] = {0, 0, 0, 0};
     for (size_t i = 0; i < runs.size(); ++i)
