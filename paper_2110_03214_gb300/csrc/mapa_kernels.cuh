@@ -1168,18 +1168,19 @@ __device__ __forceinline__ void walk_short_tail(const SmemTopo &s, const LevelVi
         int v1;
         while ((v1 = pop_lowest<W>(c1)) >= 0) {
             ++nodes;
-            const int32_t s1 = S + delta_rolled<W>(s, v1, B, R, al, be);
-            uint32_t R1[W], c2[W], B2n[W];
+            uint32_t R1[W], c2[W];
 #pragma unroll
-            for (int w = 0; w < W; ++w) {
-                R1[w] = R[w];
-                B2n[w] = B2[w];
-            }
+            for (int w = 0; w < W; ++w) R1[w] = R[w];
             clear_bit<W>(R1, v1);
-            if (nb) set_bit<W>(B2n, v1);
 #pragma unroll
             for (int w = 0; w < W; ++w) c2[w] = R1[w] & A2[w] & (nb ? s.adj[v1 * W + w] : ~0u);
             and_above<W>(c2, nl ? max(lb2, v1) : lb2);
+            if (!popc_mask<W>(c2)) continue;  // no leaf below: its score is not needed
+            const int32_t s1 = S + delta_rolled<W>(s, v1, B, R, al, be);
+            uint32_t B2n[W];
+#pragma unroll
+            for (int w = 0; w < W; ++w) B2n[w] = B2[w];
+            if (nb) set_bit<W>(B2n, v1);
             int v2;
             while ((v2 = pop_lowest<W>(c2)) >= 0) leaf(s1 + delta_rolled<W>(s, v2, B2n, R1, al, be));
         }
@@ -1482,16 +1483,10 @@ __global__ void __launch_bounds__(kTpb) k_last_coop3(TopoArgs topo, LevelView in
             int v2;
             while ((v2 = pop_lowest<W>(c2)) >= 0) {
                 ++nodes;
-                const int32_t s2 = s1 + delta_rolled<W>(s, v2, B2n, R1, als, bes);
                 uint32_t R2[W], c3[W], B3n[W];
 #pragma unroll
-                for (int w = 0; w < W; ++w) {
-                    R2[w] = R1[w];
-                    B3n[w] = B3s[w];
-                }
+                for (int w = 0; w < W; ++w) R2[w] = R1[w];
                 clear_bit<W>(R2, v2);
-                if (nb31) set_bit<W>(B3n, v1);
-                if (nb32) set_bit<W>(B3n, v2);
 #pragma unroll
                 for (int w = 0; w < W; ++w)
                     c3[w] = R2[w] & A3s[w] & (nb31 ? s.adj[v1 * W + w] : ~0u) & (nb32 ? s.adj[v2 * W + w] : ~0u);
@@ -1499,6 +1494,12 @@ __global__ void __launch_bounds__(kTpb) k_last_coop3(TopoArgs topo, LevelView in
                 if (nl31) lb = max(lb, v1);
                 if (nl32) lb = max(lb, v2);
                 and_above<W>(c3, lb);
+                if (!popc_mask<W>(c3)) continue;  // no leaf below: its score is not needed
+                const int32_t s2 = s1 + delta_rolled<W>(s, v2, B2n, R1, als, bes);
+#pragma unroll
+                for (int w = 0; w < W; ++w) B3n[w] = B3s[w];
+                if (nb31) set_bit<W>(B3n, v1);
+                if (nb32) set_bit<W>(B3n, v2);
                 int v3;
                 while ((v3 = pop_lowest<W>(c3)) >= 0) {
                     smax = max(smax, s2 + delta_rolled<W>(s, v3, B3n, R2, als, bes));
