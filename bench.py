@@ -547,10 +547,10 @@ def run_ours(a):
             sb = served_measure(M, W, a.served_rate, a.served_requests, 4096, kmax=a.served_kmax)
             sp = served_measure(M, W, a.served_rate, a.served_requests, 1, kmax=a.served_kmax)
             line["served"] = {"batched": sb, "plain": sp}
-        if world == 1 and a.sim_jobs > 0:
-            line["simulator"] = simulator_measure(M, W, a.sim_jobs)
             line["latency_ms"].update({"served_batched_p50": sb["p50_ms"], "served_batched_p99": sb["p99_ms"],
                                        "served_plain_p50": sp["p50_ms"], "served_plain_p99": sp["p99_ms"]})
+        if world == 1 and a.sim_jobs > 0:
+            line["simulator"] = simulator_measure(M, W, a.sim_jobs)
         if world == 1 and not a.no_cpu_baseline:
             threads = os.cpu_count() or 1
             emb, done, dt = _oracle_sample(wl, a.cpu_seconds, threads)
