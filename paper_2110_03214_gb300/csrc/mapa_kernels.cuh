@@ -1141,9 +1141,33 @@ __device__ __forceinline__ int32_t delta_rolled(const SmemTopo &s, int v, const 
     return acc;
 }
 
+// The same with the class count known at compile time (CT > 0).
+template <int W, int CT>
+__device__ __forceinline__ int32_t delta_c(const SmemTopo &s, int v, const uint32_t (&B)[W], const uint32_t (&R)[W],
+                                           int32_t al, int32_t be) {
+    if constexpr (CT == 0) {
+        return delta_rolled<W>(s, v, B, R, al, be);
+    } else {
+        const uint32_t *x = s.cls + v * (CT * W);
+        int32_t acc = 0;
+#pragma unroll
+        for (int c = 0; c < CT; ++c) {
+            int pb = 0, pr = 0;
+#pragma unroll
+            for (int w = 0; w < W; ++w) {
+                const uint32_t xw = x[c * W + w];
+                pb += __popc(B[w] & xw);
+                pr += __popc(R[w] & xw);
+            }
+            acc += s.wc[c] * (al * pb - be * pr);
+        }
+        return acc;
+    }
+}
+
 // Walks the last T (1 or 2) levels below parent p; leaf(score) for every
 // complete match.
-template <int W, int T, typename Leaf>
+template <int W, int CT, int T, typename Leaf>
 __device__ __forceinline__ void walk_short_tail(const SmemTopo &s, const LevelView &in, uint32_t p, const TailArgs &ta,
                                                 int32_t al, int32_t be, Leaf &&leaf, uint32_t &nodes) {
     const int32_t S = in.S[p];
@@ -1158,7 +1182,7 @@ __device__ __forceinline__ void walk_short_tail(const SmemTopo &s, const LevelVi
     and_above<W>(c1, lb);
     if constexpr (T == 1) {
         int v;
-        while ((v = pop_lowest<W>(c1)) >= 0) leaf(S + delta_rolled<W>(s, v, B, R, al, be));
+        while ((v = pop_lowest<W>(c1)) >= 0) leaf(S + delta_c<W, CT>(s, v, B, R, al, be));
     } else {
         uint32_t A2[W], B2[W];
         int lb2;
@@ -1176,20 +1200,20 @@ __device__ __forceinline__ void walk_short_tail(const SmemTopo &s, const LevelVi
             for (int w = 0; w < W; ++w) c2[w] = R1[w] & A2[w] & (nb ? s.adj[v1 * W + w] : ~0u);
             and_above<W>(c2, nl ? max(lb2, v1) : lb2);
             if (!popc_mask<W>(c2)) continue;  // no leaf below: its score is not needed
-            const int32_t s1 = S + delta_rolled<W>(s, v1, B, R, al, be);
+            const int32_t s1 = S + delta_c<W, CT>(s, v1, B, R, al, be);
             uint32_t B2n[W];
 #pragma unroll
             for (int w = 0; w < W; ++w) B2n[w] = B2[w];
             if (nb) set_bit<W>(B2n, v1);
             int v2;
-            while ((v2 = pop_lowest<W>(c2)) >= 0) leaf(s1 + delta_rolled<W>(s, v2, B2n, R1, al, be));
+            while ((v2 = pop_lowest<W>(c2)) >= 0) leaf(s1 + delta_c<W, CT>(s, v2, B2n, R1, al, be));
         }
     }
 }
 
 // Sens: the scores are link-count indices of bandwidth-sensitive requests
 // and the argmax is taken over their Eq. 2 ranks lut[score].
-template <int W, int T, bool Sens>
+template <int W, int CT, int T, bool Sens>
 __global__ void __launch_bounds__(kTpb) k_last_short(TopoArgs topo, LevelView in, const unsigned long long *count_in,
                                                      unsigned long long count_host, TailArgs ta, const int32_t *alpha,
                                                      const int32_t *beta, uint64_t *key, unsigned long long *count,
@@ -1225,7 +1249,7 @@ __global__ void __launch_bounds__(kTpb) k_last_short(TopoArgs topo, LevelView in
         }
         int32_t smax = INT_MIN;
         uint32_t leaves = 0;
-        walk_short_tail<W, T>(
+        walk_short_tail<W, CT, T>(
             s, in, p, ta, alpha[r], beta[r],
             [&](int32_t sc) {
                 if constexpr (Sens) sc = lut[sc];

@@ -106,12 +106,12 @@ struct Runner {
         MAPA_CUDA_TRY(cudaFuncSetAttribute(k_last<W, CT, T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, b));
         if constexpr (T <= 2 && W <= 2)
             MAPA_CUDA_TRY(
-                cudaFuncSetAttribute(k_last_short<W, T, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, b));
+                cudaFuncSetAttribute(k_last_short<W, CT, T, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, b));
         if constexpr (T == 3 && W <= 2)
             MAPA_CUDA_TRY(cudaFuncSetAttribute(k_last_coop3<W>, cudaFuncAttributeMaxDynamicSharedMemorySize, b));
         if constexpr (T == 1)
             MAPA_CUDA_TRY(
-                cudaFuncSetAttribute(k_last_short<W, 1, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, b));
+                cudaFuncSetAttribute(k_last_short<W, CT, 1, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, b));
         MAPA_CUDA_TRY(cudaFuncSetAttribute(k_resolve<W, CT, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, b));
         MAPA_CUDA_TRY(cudaFuncSetAttribute(k_finalize<W>, cudaFuncAttributeMaxDynamicSharedMemorySize, b));
         return MAPA_OK;
@@ -162,7 +162,7 @@ struct Runner {
         if constexpr (T == 1) {
             if (g.sens) {
                 // bandwidth-sensitive group: argmax over Eq. 2 ranks
-                k_last_short<W, 1, true><<<sgrid, kTpb, smem_all, st>>>(
+                k_last_short<W, CT, 1, true><<<sgrid, kTpb, smem_all, st>>>(
                     targs, in, count_dev, count_host, ta, g.alpha, g.beta, g.key, g.count, e->d_stats, g.effbw_rank);
                 launched = true;
             }
@@ -182,7 +182,7 @@ struct Runner {
         if constexpr (T <= 2 && W <= 2) {
             if (!g.thr && !launched) {
                 // masks of at most 64 vertices: one tile of parents per block
-                k_last_short<W, T, false><<<sgrid, kTpb, smem_all, st>>>(
+                k_last_short<W, CT, T, false><<<sgrid, kTpb, smem_all, st>>>(
                     targs, in, count_dev, count_host, ta, g.alpha, g.beta, g.key, g.count, e->d_stats, nullptr);
                 launched = true;
             }
