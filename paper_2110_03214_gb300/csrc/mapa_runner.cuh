@@ -108,7 +108,7 @@ struct Runner {
             MAPA_CUDA_TRY(
                 cudaFuncSetAttribute(k_last_short<W, CT, T, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, b));
         if constexpr (T == 3 && W <= 2)
-            MAPA_CUDA_TRY(cudaFuncSetAttribute(k_last_coop3<W>, cudaFuncAttributeMaxDynamicSharedMemorySize, b));
+            MAPA_CUDA_TRY(cudaFuncSetAttribute(k_last_coop3<W, CT>, cudaFuncAttributeMaxDynamicSharedMemorySize, b));
         if constexpr (T == 1)
             MAPA_CUDA_TRY(
                 cudaFuncSetAttribute(k_last_short<W, CT, 1, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, b));
@@ -171,10 +171,10 @@ struct Runner {
             if (!g.thr && !launched) {
                 // depth 3: the first tail level handed out across lanes
                 static int nb3 = 0;
-                if (!nb3) nb3 = blocks_per_sm(k_last_coop3<W>, smem_all);
+                if (!nb3) nb3 = blocks_per_sm(k_last_coop3<W, CT>, smem_all);
                 const unsigned cgrid = static_cast<unsigned>(std::max<uint64_t>(
                     1, std::min<uint64_t>(ceil_div(max_parents, kTpb), uint64_t(e->sm_count) * nb3)));
-                k_last_coop3<W><<<cgrid, kTpb, smem_all, st>>>(targs, in, count_dev, count_host, ta, g.alpha,
+                k_last_coop3<W, CT><<<cgrid, kTpb, smem_all, st>>>(targs, in, count_dev, count_host, ta, g.alpha,
                                                                      g.beta, g.key, g.count, tile_ctr, e->d_stats);
                 launched = true;
             }
