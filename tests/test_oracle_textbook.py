@@ -1,0 +1,262 @@
+"""Pins of the CPU oracle on named graphs and against an independent matcher.
+
+* match counts on the hypercube Q_d, the complete bipartite graph K_{a,b},
+  the Petersen graph and the cycle C_n, from closed forms and from the
+  graphs' known cycle counts (tests/golden/textbook_counts.json);
+* the chosen match and its score where every candidate ties (K_{a,b}, Q_d,
+  Petersen), so Eq. 1, Eq. 3 and the lexicographic tie-break are fixed by
+  hand;
+* on random weighted graphs of 9-13 vertices, well past the reach of the
+  pure-Python permutation brute force, the number of injective maps, |Aut(P)|
+  and the decision are re-derived from networkx's VF2 matcher: every
+  monomorphism of the pattern into the free subgraph, each scored with
+  Eq. 1 (pattern-edge weights) and Eq. 3 (the weighted size of the free
+  subgraph left after removing the match).
+
+Counting convention: one match per distinct subgraph (Sec. 3.3), i.e.
+injective adjacency-preserving maps modulo Aut(P); non-induced (E(P) must
+map into E(G), Sec. 3.4.1).
+"""
+
+import itertools
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_2110_03214_gb300 import workloads as W
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _golden():
+    with open(os.path.join(GOLDEN, "textbook_counts.json")) as f:
+        return json.load(f)
+
+
+def _instance(n, pairs, w=1):
+    u = np.asarray([p[0] for p in pairs], np.int32)
+    v = np.asarray([p[1] for p in pairs], np.int32)
+    ws = np.full(len(pairs), w, np.int32) if np.isscalar(w) else np.asarray(w, np.int32)
+    return O.Instance(n, u, v, ws)
+
+
+def _hypercube(d):
+    return [(x, x ^ (1 << i)) for x in range(1 << d) for i in range(d) if x < x ^ (1 << i)]
+
+
+def _bipartite(a, b):
+    return [(i, a + j) for i in range(a) for j in range(b)]
+
+
+def _petersen():
+    outer = [(i, (i + 1) % 5) for i in range(5)]
+    spokes = [(i, i + 5) for i in range(5)]
+    inner = [(5 + i, 5 + (i + 2) % 5) for i in range(5)]
+    return outer + spokes + inner
+
+
+def _cycle(n):
+    return [(i, (i + 1) % n) for i in range(n)]
+
+
+def _claw():
+    return W.Pattern("custom", 4, np.asarray([0, 0, 0], np.int32), np.asarray([1, 2, 3], np.int32))
+
+
+def _classes(inst, n, p, busy=None):
+    d = inst.decide(np.zeros(n, bool) if busy is None else busy, p.k, p.a, p.b)
+    assert d.status in (O.STATUS_OK, O.STATUS_NO_MATCH)
+    return d.classes
+
+
+# ----------------------------------------------------------------- counts
+
+
+@pytest.mark.parametrize("d", [3, 4, 5])
+def test_hypercube_counts(d):
+    n = 1 << d
+    inst = _instance(n, _hypercube(d))
+    want = {
+        ("path", 2): d * 2 ** (d - 1),
+        ("path", 3): n * math.comb(d, 2),
+        ("ring", 4): math.comb(d, 2) * 2 ** (d - 2),
+        ("path", 4): n * d * (d - 1) ** 2 // 2,
+        ("clique", 3): 0,
+        ("ring", 5): 0,
+    }
+    for (kind, k), c in want.items():
+        assert _classes(inst, n, W.pattern(kind, k)) == c, (d, kind, k)
+    assert _classes(inst, n, _claw()) == n * math.comb(d, 3)
+    if d == 3:
+        g = _golden()["hypercube"]
+        assert _classes(inst, n, W.pattern("ring", 6)) == g["cube_ring6"]
+        assert _classes(inst, n, W.pattern("ring", 8)) == g["cube_ring8"]
+
+
+@pytest.mark.parametrize("a,b", [(2, 3), (3, 3), (4, 4), (3, 5)])
+def test_complete_bipartite_counts(a, b):
+    n = a + b
+    inst = _instance(n, _bipartite(a, b))
+    want = {
+        ("path", 2): a * b,
+        ("path", 3): a * math.comb(b, 2) + b * math.comb(a, 2),
+        ("ring", 4): math.comb(a, 2) * math.comb(b, 2),
+        ("ring", 6): 6 * math.comb(a, 3) * math.comb(b, 3),
+        ("ring", 8): 72 * math.comb(a, 4) * math.comb(b, 4),
+        ("clique", 3): 0,
+        ("ring", 5): 0,
+    }
+    for (kind, k), c in want.items():
+        if k <= n:
+            assert _classes(inst, n, W.pattern(kind, k)) == c, (a, b, kind, k)
+
+
+def test_petersen_counts():
+    g = _golden()["petersen"]
+    inst = _instance(10, _petersen())
+    for name, want in g.items():
+        if name == "note":
+            continue
+        kind, k = name.split("-")
+        assert _classes(inst, 10, W.pattern(kind, int(k))) == want, name
+    assert _classes(inst, 10, _claw()) == 10
+
+
+@pytest.mark.parametrize("n", [5, 8, 13])
+def test_cycle_graph_counts(n):
+    inst = _instance(n, _cycle(n))
+    assert _classes(inst, n, W.pattern("ring", n)) == 1
+    for k in range(2, n):
+        assert _classes(inst, n, W.pattern("path", k)) == n, k
+    # one busy vertex turns the cycle into a path on n-1 vertices
+    busy = np.zeros(n, bool)
+    busy[n // 2] = True
+    assert _classes(inst, n, W.pattern("ring", n), busy) == 0
+    for k in range(2, n):
+        assert _classes(inst, n, W.pattern("path", k), busy) == n - k, k
+
+
+# ----------------------------------------------------------------- decisions that tie
+
+
+@pytest.mark.parametrize("a,b,w", [(3, 4, 25), (4, 4, 50), (5, 3, 12)])
+def test_bipartite_ring4_decision(a, b, w):
+    # Every 4-cycle uses two vertices per side, so every match scores
+    # Eq. 1: 4w and Eq. 3: (a-2)(b-2)w; the lexicographically smallest map
+    # of the cycle 0-1-2-3-0 is (0, a, 1, a+1).
+    inst = _instance(a + b, _bipartite(a, b), w)
+    p = W.pattern("ring", 4)
+    d = inst.decide(np.zeros(a + b, bool), 4, p.a, p.b, 1, 1)
+    assert d.status == O.STATUS_OK
+    assert (d.agg, d.pres) == (4 * w, (a - 2) * (b - 2) * w)
+    assert d.score == d.agg + d.pres
+    assert d.tuple == (0, a, 1, a + 1)
+
+
+@pytest.mark.parametrize("d", [3, 4, 5])
+def test_hypercube_ring4_preserve_decision(d):
+    # Removing a face (4 vertices of degree d spanning 4 edges) leaves
+    # d*2^(d-1) - 4d + 4 edges whichever face it is; the smallest map of the
+    # cycle 0-1-2-3-0 runs around the face {0, 1, 3, 2}.
+    n = 1 << d
+    inst = _instance(n, _hypercube(d))
+    p = W.pattern("ring", 4)
+    r = inst.decide(np.zeros(n, bool), 4, p.a, p.b, 0, 1)
+    assert r.status == O.STATUS_OK
+    assert r.pres == r.score == d * 2 ** (d - 1) - 4 * d + 4
+    assert r.agg == 4
+    assert r.tuple == (0, 1, 3, 2)
+
+
+def test_petersen_ring5_decision():
+    # Any pentagon leaves its complementary pentagon: agg 5w, pres 5w for
+    # every match; the smallest map is the outer cycle in order.
+    inst = _instance(10, _petersen(), 7)
+    p = W.pattern("ring", 5)
+    d = inst.decide(np.zeros(10, bool), 5, p.a, p.b, 1, 1)
+    assert (d.status, d.agg, d.pres, d.score) == (O.STATUS_OK, 35, 35, 70)
+    assert d.tuple == (0, 1, 2, 3, 4)
+
+
+# ----------------------------------------------------------------- independent matcher
+
+
+def _vf2_decision(nx, n, pairs, ws, busy, p, alpha, beta):
+    from networkx.algorithms import isomorphism as iso
+
+    G = nx.Graph()
+    G.add_nodes_from(range(n))
+    for (x, y), w in zip(pairs, ws):
+        G.add_edge(x, y, weight=int(w))
+    free = [x for x in range(n) if not busy[x]]
+    Gf = G.subgraph(free)
+    P = nx.Graph()
+    P.add_nodes_from(range(p.k))
+    P.add_edges_from(zip(p.a.tolist(), p.b.tolist()))
+    aut = sum(1 for _ in iso.GraphMatcher(P, P).isomorphisms_iter())
+    maps = 0
+    best = None
+    for m in iso.GraphMatcher(Gf, P).subgraph_monomorphisms_iter():
+        phi = [0] * p.k
+        for gv, pv in m.items():
+            phi[pv] = gv
+        maps += 1
+        agg = sum(G[phi[x]][phi[y]]["weight"] for x, y in zip(p.a.tolist(), p.b.tolist()))
+        rest = set(free) - set(phi)
+        pres = G.subgraph(rest).size(weight="weight")
+        key = (alpha * agg + beta * int(pres), tuple(-x for x in phi))
+        if best is None or key > best[0]:
+            best = (key, agg, int(pres), tuple(phi))
+    return maps, aut, best
+
+
+def test_vf2_matcher_agrees_on_random_graphs():
+    nx = pytest.importorskip("networkx")
+    rng = W.Rng(4711, 3)
+    checked = 0
+    for trial in range(36):
+        n = int(rng.integers(9, 13, 1)[0])
+        all_pairs = [(x, y) for x in range(n) for y in range(x + 1, n)]
+        keep = rng.uniform(len(all_pairs)) < 0.38
+        pairs = [q for q, kk in zip(all_pairs, keep) if kk]
+        ws = rng.integers(1, 50, len(pairs))
+        busy = rng.uniform(n) < 0.15
+        k = int(rng.integers(1, 6, 1)[0])
+        p = W.random_pattern(rng, k, 0.3, connected=bool(trial % 4))
+        alpha, beta = (int(x) for x in rng.integers(-2, 3, 2))
+        inst = _instance(n, pairs, ws)
+        d = inst.decide(busy, p.k, p.a, p.b, alpha, beta)
+        maps, aut, best = _vf2_decision(nx, n, pairs, ws, busy, p, alpha, beta)
+        assert O.aut_count(p.k, p.a, p.b) == aut, trial
+        if maps == 0:
+            assert d.status == O.STATUS_NO_MATCH and d.classes == 0, trial
+            continue
+        assert d.status == O.STATUS_OK and d.aut == aut, trial
+        assert (d.maps, d.classes) == (maps, maps // aut), trial
+        assert (d.score, d.agg, d.pres, d.tuple) == (best[0][0], best[1], best[2], best[3]), trial
+        checked += 1
+    assert checked >= 20
+
+
+def test_vf2_matcher_counts_on_named_graphs():
+    # The same matcher on the named graphs above, for shapes without a
+    # closed form here (trees, the heap tree of 7 vertices, 5-cliques).
+    nx = pytest.importorskip("networkx")
+    from networkx.algorithms import isomorphism as iso
+
+    graphs = {"Q4": (16, _hypercube(4)), "petersen": (10, _petersen()), "K44": (8, _bipartite(4, 4))}
+    for name, (n, pairs) in graphs.items():
+        G = nx.Graph(pairs)
+        inst = _instance(n, pairs)
+        for kind, k in itertools.product(("tree", "ring", "clique"), (5, 6, 7)):
+            p = W.pattern(kind, k)
+            P = nx.Graph()
+            P.add_nodes_from(range(k))
+            P.add_edges_from(zip(p.a.tolist(), p.b.tolist()))
+            maps = sum(1 for _ in iso.GraphMatcher(G, P).subgraph_monomorphisms_iter())
+            d = inst.decide(np.zeros(n, bool), k, p.a, p.b)
+            assert d.maps == maps, (name, kind, k)
