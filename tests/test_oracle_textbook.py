@@ -11,7 +11,8 @@
   and the decision are re-derived from networkx's VF2 matcher: every
   monomorphism of the pattern into the free subgraph, each scored with
   Eq. 1 (pattern-edge weights) and Eq. 3 (the weighted size of the free
-  subgraph left after removing the match).
+  subgraph left after removing the match); the branch-and-bound oracle
+  must reach the same decision.
 
 Counting convention: one match per distinct subgraph (Sec. 3.3), i.e.
 injective adjacency-preserving maps modulo Aut(P); non-induced (E(P) must
@@ -238,6 +239,8 @@ def test_vf2_matcher_agrees_on_random_graphs():
         assert d.status == O.STATUS_OK and d.aut == aut, trial
         assert (d.maps, d.classes) == (maps, maps // aut), trial
         assert (d.score, d.agg, d.pres, d.tuple) == (best[0][0], best[1], best[2], best[3]), trial
+        b = inst.decide_bounded(busy, p.k, p.a, p.b, alpha, beta)
+        assert (b.status, b.score, b.agg, b.pres, b.tuple) == (d.status, d.score, d.agg, d.pres, d.tuple), trial
         checked += 1
     assert checked >= 20
 
