@@ -12,7 +12,9 @@
   monomorphism of the pattern into the free subgraph, each scored with
   Eq. 1 (pattern-edge weights) and Eq. 3 (the weighted size of the free
   subgraph left after removing the match); the branch-and-bound oracle
-  must reach the same decision.
+  must reach the same decision;
+* the same matcher re-derives the bandwidth-sensitive decision (Algorithm 1,
+  Eq. 2 over the link types of the pattern-edge images).
 
 Counting convention: one match per distinct subgraph (Sec. 3.3), i.e.
 injective adjacency-preserving maps modulo Aut(P); non-induced (E(P) must
@@ -263,3 +265,57 @@ def test_vf2_matcher_counts_on_named_graphs():
             maps = sum(1 for _ in iso.GraphMatcher(G, P).subgraph_monomorphisms_iter())
             d = inst.decide(np.zeros(n, bool), k, p.a, p.b)
             assert d.maps == maps, (name, kind, k)
+
+
+def test_vf2_matcher_agrees_on_bandwidth_sensitive_decisions():
+    # Algorithm 1's first branch on graphs with the link weights of Table 1
+    # (50 double NVLink, 25 single, 12 PCIe, 10 none of these): every
+    # monomorphism's pattern-edge images are typed by weight, Eq. 2 is taken
+    # from the oracle's own evaluation (pinned to the paper's printed values
+    # elsewhere), and the largest prediction wins, ties to the smallest tuple.
+    nx = pytest.importorskip("networkx")
+    from networkx.algorithms import isomorphism as iso
+
+    typ = {50: 0, 25: 1, 20: 1, 12: 2}
+    rng = W.Rng(5150, 9)
+    checked = 0
+    for trial in range(24):
+        n = int(rng.integers(8, 12, 1)[0])
+        all_pairs = [(x, y) for x in range(n) for y in range(x + 1, n)]
+        keep = rng.uniform(len(all_pairs)) < 0.45
+        pairs = [q for q, kk in zip(all_pairs, keep) if kk]
+        ws = np.asarray([50, 25, 20, 12, 10])[rng.integers(0, 4, len(pairs))]
+        busy = rng.uniform(n) < 0.15
+        k = int(rng.integers(2, 5, 1)[0])
+        p = W.random_pattern(rng, k, 0.3, connected=True)
+        inst = _instance(n, pairs, ws)
+        d, xyz = inst.decide_effbw(busy, p.k, p.a, p.b)
+        G = nx.Graph()
+        G.add_nodes_from(range(n))
+        for (x, y), w in zip(pairs, ws):
+            G.add_edge(x, y, weight=int(w))
+        Gf = G.subgraph([x for x in range(n) if not busy[x]])
+        P = nx.Graph()
+        P.add_nodes_from(range(k))
+        P.add_edges_from(zip(p.a.tolist(), p.b.tolist()))
+        best = None
+        for m in iso.GraphMatcher(Gf, P).subgraph_monomorphisms_iter():
+            phi = [0] * k
+            for gv, pv in m.items():
+                phi[pv] = gv
+            cnt = [0, 0, 0]
+            for x, y in zip(p.a.tolist(), p.b.tolist()):
+                t = typ.get(G[phi[x]][phi[y]]["weight"])
+                if t is not None:
+                    cnt[t] += 1
+            key = (O.effbw(*cnt), tuple(-v for v in phi))
+            if best is None or key > best[0]:
+                best = (key, tuple(cnt), tuple(phi))
+        if best is None:
+            assert d.status == O.STATUS_NO_MATCH, trial
+            continue
+        assert d.status == O.STATUS_OK, trial
+        assert (d.tuple, xyz) == (best[2], best[1]), trial
+        assert abs(d.score - 1000 * best[0][0]) <= 0.5 + 1e-9, trial
+        checked += 1
+    assert checked >= 15
