@@ -1,12 +1,19 @@
 #!/usr/bin/env python
 """Benchmark of the MAPA allocation hot path on GB300.
 
-One step = one mapa_allocate_batch call deciding every request of the
-workload (default: 10^4 independent requests on a 32-vertex random 6-regular
-graph, patterns ring-8 / tree-7 / clique-4, occupancy U[0, 0.5]): enumerate
-every match, score it (alpha*AggBW + beta*PreservedBW, Eq. 1 and Eq. 3) and
-pick the argmax.  Inputs are resident in HBM when the timed region starts;
-the L2 is flushed between timed steps (a 256 MiB write).
+One step = one mapa_allocate_batch call deciding every request of one batch:
+enumerate the matches of each request's pattern on its free accelerators,
+score them (alpha*AggBW + beta*PreservedBW, Eq. 1 and Eq. 3) and pick the
+argmax (Algorithm 1).  Inputs are resident in HBM when the timed region
+starts; the L2 is flushed between timed steps (a 256 MiB write).
+
+Default workload: the 256-vertex boards machine (32 boards of 8, ring-32 /
+tree-31 / clique-8), 3000 requests of its 10^6-request stream per step, each
+with the occupancy a served run leaves, in bounded mode with the anytime
+fallback under a work budget of 2^20 partial matches per request and a
+16 GiB frontier cap per pattern group (64 GiB for the four concurrent
+groups).  The line also carries the 10^4-request 32-vertex workload
+(`config2`), decided exhaustively.
 
 Prints one JSON line (rank 0).  `--impl reference` times the CPU oracle on
 the host cores instead (the paper has no GPU implementation).
@@ -39,8 +46,14 @@ def _args():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", default="regular32", choices=("cube_mesh8", "regular32", "torus64", "dragonfly128", "boards256"))
-    ap.add_argument("--requests", type=int, default=None)
+    ap.add_argument("--workload", default="boards256", choices=("cube_mesh8", "regular32", "torus64", "dragonfly128", "boards256"))
+    ap.add_argument("--requests", type=int, default=None,
+                    help="requests per step (default: 3000 for boards256, the workload's size otherwise)")
+    ap.add_argument("--work-budget", type=int, default=None,
+                    help="partial matches a request may store (default: 2^20 for boards256, none otherwise)")
+    ap.add_argument("--frontier-cap-gib", type=float, default=None,
+                    help="frontier memory per pattern group (default: 16 for boards256, 4 otherwise)")
+    ap.add_argument("--no-config2", action="store_true", help="skip the 32-vertex workload's extra figures")
     ap.add_argument("--cpu-seconds", type=float, default=15.0, help="bounded oracle sample length")
     ap.add_argument("--plain-requests", type=int, default=300, help="requests timed through the plain per-request path")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -48,7 +61,7 @@ def _args():
     ap.add_argument("--served-requests", type=int, default=3000, help="arrivals in the served comparison")
     ap.add_argument("--served-rate", type=float, default=1e4, help="Poisson rate of the served comparison")
     ap.add_argument("--served-kmax", type=int, default=8)
-    ap.add_argument("--sim-jobs", type=int, default=300,
+    ap.add_argument("--sim-jobs", type=int, default=0,
                     help="jobs of the simulator leg (Sec. 6 job file; 0 = skip)")
     ap.add_argument("--no-autotune", action="store_true",
                     help="keep the default tail depths (profiling runs: timings under a profiler mislead the tuner)")
@@ -211,8 +224,25 @@ def _traffic_per_launch(workload: str, parents_per_launch: float):
     return rec["dram_bytes_per_parent"] * parents_per_launch
 
 
-def _oracle_sample(wl, budget_s: float, threads: int, start: int = 0):
-    """Runs the oracle over consecutive requests until budget_s elapses."""
+def workload_settings(name: str, a) -> dict:
+    """Requests per step, decision mode, policy flags, work budget and
+    frontier cap of a workload's bench line."""
+    big = name == "boards256"
+    req = a.requests if a.requests else (3000 if big else None)
+    return {
+        "requests": req,
+        "mode": 1 if big else 0,  # MAPA_MODE_BOUNDED / MAPA_MODE_EXHAUSTIVE
+        "flags": 2 if big else 0,  # MAPA_POLICY_ANYTIME
+        "work_budget": a.work_budget if a.work_budget is not None else ((1 << 20) if big else 0),
+        "frontier_cap": int((a.frontier_cap_gib if a.frontier_cap_gib else (16 if big else 4)) * (1 << 30)),
+    }
+
+
+def _oracle_sample(wl, budget_s: float, threads: int, start: int = 0, max_nodes: int = 0):
+    """Runs the oracle over consecutive requests until budget_s elapses.
+    Returns (matches scored once per distinct subgraph, requests, seconds):
+    a request stopped at max_nodes search nodes still counts the matches it
+    scored (maps / |Aut(P)|)."""
     from concurrent.futures import ThreadPoolExecutor
 
     from oracle import oracle as O
@@ -220,19 +250,22 @@ def _oracle_sample(wl, budget_s: float, threads: int, start: int = 0):
 
     inst = O.Instance.from_topology(wl.topology)
     reqs = wl.requests
+    auts = [O.aut_count(p.k, p.a, p.b) for p in reqs.patterns]
 
     def one(i):
         p = reqs.patterns[reqs.pattern_index[i]]
         busy = W.busy_to_bool(reqs.busy[i], wl.topology.n)
-        d = inst.decide(busy, p.k, p.a, p.b, int(reqs.alpha[i]), int(reqs.beta[i]))
-        return d.classes if d.status == O.STATUS_OK else 0
+        d = inst.decide(busy, p.k, p.a, p.b, int(reqs.alpha[i]), int(reqs.beta[i]), max_nodes=max_nodes)
+        if d.status == O.STATUS_OK:
+            return float(d.classes)
+        return float(d.maps) / auts[reqs.pattern_index[i]] if d.status == O.STATUS_BUDGET else 0.0
 
-    done, emb = 0, 0
+    done, emb = 0, 0.0
     t0 = time.perf_counter()
     with ThreadPoolExecutor(threads) as ex:
         i = start
         while time.perf_counter() - t0 < budget_s and i < len(reqs):
-            chunk = list(range(i, min(i + 4 * threads, len(reqs))))
+            chunk = list(range(i, min(i + threads, len(reqs))))
             emb += sum(ex.map(one, chunk))
             done += len(chunk)
             i += len(chunk)
@@ -240,11 +273,29 @@ def _oracle_sample(wl, budget_s: float, threads: int, start: int = 0):
     return emb, done, dt
 
 
+def _oracle_node_cap(settings) -> int:
+    """Search-node cap of the oracle's timed sample when the GPU runs under a
+    work budget: 2^22 nodes per request (one to two seconds of one host core
+    on the 256-vertex graph), so the sample stays within its time limit.  The
+    oracle enumerates every map (no symmetry breaking), so this is less
+    search than the GPU's budget allows; the figure is matches scored per
+    second either way."""
+    return 1 << 22 if settings["work_budget"] else 0
+
+
 def shard_workload(W, name: str, num_requests, rank: int):
     """Rank r decides its own batch of the workload's shape (independent
     requests shard with no exchange; weak scaling): same topology recipe and
     request mix, seed offset by the rank."""
     return W.workload(name, num_requests=num_requests, seed=W.WORKLOADS.index(name) + 1 + 1000 * rank)
+
+
+def shard_slice(count: int, rank: int, world: int) -> tuple[int, int]:
+    """Rank r's contiguous share [lo, hi) of `count` independent requests
+    (strong-scaling split of one batch: shares differ by at most one)."""
+    lo = count * rank // world
+    hi = count * (rank + 1) // world
+    return lo, hi
 
 
 def combine_over_ranks(dist, device, total_ms: float, e2e_s: float, emb_step: int):
@@ -351,21 +402,24 @@ def run_reference(a):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
-    wl = W.workload(a.workload, num_requests=a.requests)
+    cfg = workload_settings(a.workload, a)
+    wl = W.workload(a.workload, num_requests=cfg["requests"])
     threads = os.cpu_count() or 1
+    cap = _oracle_node_cap(cfg)
     per_step = max(0.5, min(20.0, 120.0 / max(1, a.steps + a.warmup)))
     for _ in range(a.warmup):
-        _oracle_sample(wl, per_step / 4, threads)
-    emb_total, req_total, t_total = 0, 0, 0.0
+        _oracle_sample(wl, per_step / 4, threads, max_nodes=cap)
+    emb_total, req_total, t_total = 0.0, 0, 0.0
     start = 0
     for _ in range(a.steps):
-        emb, done, dt = _oracle_sample(wl, per_step, threads, start)
+        emb, done, dt = _oracle_sample(wl, per_step, threads, start, max_nodes=cap)
         start = (start + done) % len(wl.requests)
         emb_total += emb
         req_total += done
         t_total += dt
     value = emb_total / t_total
-    sample = f"{req_total} requests of {wl.name} ({len(wl.requests)} in the workload), {per_step:.1f} s per step"
+    sample = (f"{req_total} requests of {wl.name} ({len(wl.requests)} in the batch), {per_step:.1f} s per step"
+              + (f", at most {cap} search nodes per request" if cap else ""))
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": a.gpus, "steps": a.steps,
         "warmup": a.warmup, "ms_per_step": 1000 * t_total / a.steps, "higher_is_better": True, "scaling": "weak",
@@ -379,33 +433,23 @@ def run_reference(a):
     print(json.dumps(line), flush=True)
 
 
-def run_ours(a):
+def measure_batch(M, W, torch, a, name, rank, world, dist, local, plain_requests):
+    """Times one workload's batch: the timed device-buffer steps, a per-kernel
+    timing pass for the roofline, the end-to-end host-buffer steps and the
+    plain one-request-per-call path.  Returns the figures as a dict."""
     import numpy as np
-    import torch
-    import torch.distributed as dist
 
-    import __graft_entry__
-
-    __graft_entry__.build()
-    from paper_2110_03214_gb300 import mapa as M
-    from paper_2110_03214_gb300 import workloads as W
-
-    rank = int(os.environ.get("RANK", "0"))
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
-    torch.cuda.set_device(local)
-    if world > 1:
-        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
-
-    # Each rank decides its own batch of the same shape (independent requests shard with no exchange).
-    wl = shard_workload(W, a.workload, a.requests, rank)
+    cfg = workload_settings(name, a)
+    wl = shard_workload(W, name, cfg["requests"], rank)
     nreq = len(wl.requests)
     stream = torch.cuda.current_stream()
-    ctx = M.Context(local)
+    ctx = M.Context(local, frontier_mem_cap=cfg["frontier_cap"])
     ctx.set_stream(stream.cuda_stream)
+    ctx.set_work_budget(cfg["work_budget"])
     tid = ctx.topology_load(wl.topology)
     pids = [ctx.pattern_load(p) for p in wl.requests.patterns]
-    reqs = ctx.requests(wl.requests, pids)
+    reqs = ctx.requests(wl.requests, pids, mode=cfg["mode"])
+    reqs["flags"] |= cfg["flags"]
     d_req = torch.from_numpy(reqs.view(np.uint8).copy()).cuda()
     d_out = torch.zeros(nreq * M.RESULT_DTYPE.itemsize, dtype=torch.uint8, device="cuda")
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
@@ -413,7 +457,7 @@ def run_ours(a):
     def step():
         ctx.allocate_batch_device(tid, nreq, d_req.data_ptr(), d_out.data_ptr())
 
-    # tail depths chosen by the autotuner on a sample of the workload (untimed)
+    # tail depths chosen by the autotuner on the workload (untimed)
     if a.no_autotune:
         tail_depths = "default"
     else:
@@ -457,18 +501,27 @@ def run_ours(a):
     got = d_out.cpu().numpy().view(M.RESULT_DTYPE)
     if not np.array_equal(got, ref):
         raise RuntimeError("results changed between steps")
-    # roofline pass: the same step with the fused-tail launches bracketed by
-    # CUDA events on the engine's stream (per-kernel timing bypasses graphs,
+    # roofline pass: the same step with every fused-tail and level-expansion
+    # launch bracketed by CUDA events on the stream it runs on (per-kernel
+    # timing runs the pattern groups one after another and bypasses graphs,
     # so it runs outside the timed region)
     ctx.stats_reset()
     ctx.set_timing(True)
-    for _ in range(3):
+    roof_steps = 3
+    t_roof = []
+    for _ in range(roof_steps):
         flush.zero_()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
         step()
+        e1.record(stream)
+        e1.synchronize()
+        t_roof.append(e0.elapsed_time(e1))
     torch.cuda.synchronize()
     st_roof = ctx.stats()
     ctx.set_timing(False)
-    emb_step = int(ref["count"].sum())
+    emb_step = int(st["embeddings"] // max(1, a.steps))
     total_ms = float(sum(times))
 
     # end to end through the public API with pinned host buffers
@@ -490,59 +543,143 @@ def run_ours(a):
         total_ms, e2e_s, emb_all = combine_over_ranks(dist, "cuda", total_ms, e2e_s, emb_step)
     else:
         emb_all = float(emb_step)
-    value = emb_all * a.steps / (total_ms / 1000.0)
-    decisions = nreq * world * a.steps / (total_ms / 1000.0)
-    e2e = {"value": emb_all * a.steps / e2e_s, "unit": UNIT, "h2d_bytes_per_step": nreq * M.REQUEST_DTYPE.itemsize,
-           "d2h_bytes_per_step": nreq * M.RESULT_DTYPE.itemsize}
 
     # plain per-request path (mapa_allocate_batch with one request per call) for latency
     plain_lat = []
-    for i in range(min(a.plain_requests, nreq)):
+    for i in range(min(plain_requests, nreq)):
         t0 = time.perf_counter()
         ctx.allocate_batch(tid, reqs[i:i + 1])
         plain_lat.append(time.perf_counter() - t0)
-    plain = {
-        "decisions_per_s": len(plain_lat) / sum(plain_lat),
-        "p50_ms": 1000 * float(np.percentile(plain_lat, 50)),
-        "p99_ms": 1000 * float(np.percentile(plain_lat, 99)),
-        "requests": len(plain_lat),
-    }
     ctx.close()
+    statuses = {int(k): int(v) for k, v in zip(*np.unique(ref["status"], return_counts=True))}
+    decided = sum(v for k, v in statuses.items() if k >= 0)
+    return {
+        "wl": wl, "nreq": nreq, "cfg": cfg, "ref": ref, "times": times, "total_ms": total_ms, "clocks": clk,
+        "stats": st, "stats_roof": st_roof, "roof_steps": roof_steps, "roof_ms": t_roof, "tail_depths": tail_depths,
+        "emb_step": emb_step, "emb_all": emb_all, "e2e_s": e2e_s,
+        "value": emb_all * a.steps / (total_ms / 1000.0),
+        "decisions_per_s": decided * world * a.steps / (total_ms / 1000.0),
+        "requests_per_s": nreq * world * a.steps / (total_ms / 1000.0),
+        "statuses": {M_STATUS.get(k, str(k)): v for k, v in statuses.items()},
+        "e2e": {"value": emb_all * a.steps / e2e_s, "unit": UNIT,
+                "decisions_per_s": decided * world * a.steps / e2e_s,
+                "h2d_bytes_per_step": nreq * M.REQUEST_DTYPE.itemsize,
+                "d2h_bytes_per_step": nreq * M.RESULT_DTYPE.itemsize},
+        "plain": {"decisions_per_s": len(plain_lat) / sum(plain_lat) if plain_lat else None,
+                  "p50_ms": 1000 * float(np.percentile(plain_lat, 50)) if plain_lat else None,
+                  "p99_ms": 1000 * float(np.percentile(plain_lat, 99)) if plain_lat else None,
+                  "requests": len(plain_lat)},
+    }
 
-    peaks, peak_src = _peaks()
+
+M_STATUS = {0: "ok", 1: "no_fit", 2: "inexact", -5: "budget", -2: "range", -1: "invalid"}
+
+
+def roofline(r, peaks, peak_src, int_peak):
+    """Roofline entry of the kernel that takes the larger share of the
+    timing pass: the level expansion (frontier bytes against the measured
+    copy bandwidth) or the fused tail (algorithmic integer operations
+    against the measured integer issue rate)."""
+    st = r["stats_roof"]
+    n = r["roof_steps"]
+    step_ms = statistics.median(r["roof_ms"])
+    tail_ms, exp_ms = st["tail_ms"] / n, st["expand_ms"] / n
+    if exp_ms >= tail_ms and st["expand_launches"]:
+        launch_ms = st["expand_ms"] / st["expand_launches"]
+        bytes_per_launch = st["expand_bytes"] / st["expand_launches"]
+        achieved = bytes_per_launch / (launch_ms / 1000.0) / 1e9
+        peak = float(peaks["hbm_gbs"])
+        return {"bound": "hbm", "kernel": "level expansion (k_expand, or k_count + k_write when chunked)",
+                "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak, "traffic": None,
+                "peak_source": f"{peak_src} hbm_gbs (copy bandwidth)",
+                "algorithmic_bytes_per_launch": bytes_per_launch, "launch_ms": launch_ms,
+                "launches_per_step": st["expand_launches"] / n, "share_of_step": exp_ms / step_ms,
+                "tail_share_of_step": tail_ms / step_ms,
+                "measured": "separate 3-step pass, CUDA events around each launch on its stream, groups serial"}
+    launch_ms = st["tail_ms"] / max(1, st["tail_launches"])
+    ops_per_launch = st["tail_int_ops"] / max(1, st["tail_launches"])
+    achieved = ops_per_launch / (launch_ms / 1000.0) / 1e9 if launch_ms > 0 else 0.0
+    peak = int_peak["mix_gops"]
+    traffic = _traffic_per_launch(f"{r['wl'].name}/{r['nreq']}", st["tail_parents"] / max(1, st["tail_launches"]))
+    return {"bound": "alu", "kernel": "k_last_short (fused last two levels: score, count, argmax)",
+            "achieved": achieved, "peak": peak, "unit": "Gop/s", "frac": achieved / peak if peak else None,
+            "traffic": traffic, "peak_source": int_peak["source"], "launch_ms": launch_ms,
+            "ops_per_launch": ops_per_launch, "launches_per_step": st["tail_launches"] / n,
+            "share_of_step": tail_ms / step_ms, "expand_share_of_step": exp_ms / step_ms,
+            "ops_units": "per parent (|back|+3)W, per tail node 2CW+|back|+4 plus its (|back|+3)W, per leaf 2CW+|back|+5",
+            "measured": "separate 3-step pass, CUDA events around each launch on its stream, groups serial"}
+
+
+def measure_int_peak(M, local, peaks):
+    """Integer issue rate of this GPU measured by the library's probe kernel
+    (no such figure in MEASURED_PEAKS.json); the lane-count figure beside it."""
+    with M.Context(local) as c:
+        plain = M.mapa_measure_int_peak(c.h, 0) / 1e9
+        mix = M.mapa_measure_int_peak(c.h, 1) / 1e9
     sm_mhz = float(peaks.get("sm_max_mhz", 2070.0))
-    peak_gops = SM_COUNT * INT_LANES_PER_SM * sm_mhz * 1e6 / 1e9
-    tail_launch_ms = st_roof["tail_ms"] / max(1, st_roof["tail_launches"])
-    ops_per_launch = st_roof["tail_int_ops"] / max(1, st_roof["tail_launches"])
-    achieved_gops = ops_per_launch / (tail_launch_ms / 1000.0) / 1e9 if tail_launch_ms > 0 else 0.0
-    workload_name = f"{wl.name}: {wl.description}, {nreq} requests"
-    traffic = _traffic_per_launch(f"{wl.name}/{nreq}", st_roof["tail_parents"] / max(1, st_roof["tail_launches"]))
+    lanes = SM_COUNT * INT_LANES_PER_SM * sm_mhz * 1e6 / 1e9
+    return {"logic_add_gops": plain, "mix_gops": mix, "lanes_x_clock_gops": lanes,
+            "source": "measured: lop3/popc/add chains, one popc per three ops (mapa_measure_int_peak kind 1)"}
 
+
+def run_ours(a):
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    import __graft_entry__
+
+    __graft_entry__.build()
+    from paper_2110_03214_gb300 import mapa as M
+    from paper_2110_03214_gb300 import workloads as W
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    # Each rank decides its own batch of the same shape (independent requests shard with no exchange).
+    r = measure_batch(M, W, torch, a, a.workload, rank, world, dist, local, a.plain_requests)
+    peaks, peak_src = _peaks()
+    int_peak = measure_int_peak(M, local, peaks)
+    roof = roofline(r, peaks, peak_src, int_peak)
+    wl, nreq, cfg = r["wl"], r["nreq"], r["cfg"]
+    total_ms = r["total_ms"]
     if rank == 0:
         line = {
-            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": a.steps, "warmup": a.warmup,
-            "ms_per_step": total_ms / a.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": "int32", "data": "synthetic (seeded SplitMix64 generator)",
-            "decisions_per_s": decisions,
-            "latency_ms": {"batched_p50": total_ms / a.steps, "batched_p99": max(times),
-                           "plain_p50": plain["p50_ms"], "plain_p99": plain["p99_ms"]},
-            "plain": plain,
-            "config": {"workload": workload_name, "requests_per_step": nreq, "embeddings_per_step": emb_step,
-                       "tail_depths": tail_depths,
+            "metric": METRIC, "value": r["value"], "unit": UNIT, "n_gpus": world, "steps": a.steps,
+            "warmup": a.warmup, "ms_per_step": total_ms / a.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "int32", "data": "synthetic (seeded SplitMix64 generator)",
+            "decisions_per_s": r["decisions_per_s"], "requests_per_s": r["requests_per_s"],
+            "outcomes_per_step": r["statuses"],
+            "latency_ms": {"batched_p50": statistics.median(r["times"]), "batched_p99": max(r["times"]),
+                           "plain_p50": r["plain"]["p50_ms"], "plain_p99": r["plain"]["p99_ms"]},
+            "plain": r["plain"],
+            "config": {"workload": f"{wl.name}: {wl.description}", "requests_per_step": nreq,
+                       "embeddings_per_step": r["emb_step"], "tail_depths": r["tail_depths"],
+                       "mode": "bounded" if cfg["mode"] else "exhaustive",
+                       "anytime": bool(cfg["flags"] & 2), "work_budget_partials": cfg["work_budget"],
+                       "frontier_cap_bytes_per_group": cfg["frontier_cap"],
                        "parallelism": f"{world} independent shards" if world > 1 else "single GPU",
                        "l2": "flushed between timed steps (256 MiB write)"},
-            "roofline": {"bound": "alu", "kernel": "k_last_short (fused last two levels: score, count, argmax)",
-                         "achieved": achieved_gops, "peak": peak_gops, "unit": "Gop/s",
-                         "frac": achieved_gops / peak_gops if peak_gops else None, "traffic": traffic,
-                         "peak_source": f"152 SMs x 128 int lanes x {sm_mhz:.0f} MHz ({peak_src} sm_max_mhz)",
-                         "launch_ms": tail_launch_ms, "launches_per_step": st_roof["tail_launches"] / 3,
-                         "tail_share_of_step": (st_roof["tail_ms"] / 3) / (total_ms / a.steps) if total_ms else None,
-                         "measured": "separate 3-step pass with CUDA events around each fused-tail launch"},
-            "gpu_launches": st["kernel_launches"],
-            "stats": st,
-            "e2e": e2e,
-            "clocks": clk,
+            "roofline": roof,
+            "int_peak": int_peak,
+            "gpu_launches": r["stats"]["kernel_launches"],
+            "stats": r["stats"],
+            "e2e": r["e2e"],
+            "clocks": r["clocks"],
         }
+        if world == 1 and a.workload != "regular32" and not a.no_config2:
+            c2 = measure_batch(M, W, torch, a, "regular32", 0, 1, dist, local, a.plain_requests)
+            line["config2"] = {
+                "workload": f"{c2['wl'].name}: {c2['wl'].description}", "requests_per_step": c2["nreq"],
+                "value": c2["value"], "unit": UNIT, "ms_per_step": c2["total_ms"] / a.steps,
+                "decisions_per_s": c2["decisions_per_s"], "e2e": c2["e2e"], "plain": c2["plain"],
+                "roofline": roofline(c2, peaks, peak_src, int_peak), "clocks": c2["clocks"],
+                "gpu_launches": c2["stats"]["kernel_launches"], "embeddings_per_step": c2["emb_step"],
+            }
         if world == 1 and a.served_requests > 0:
             sb = served_measure(M, W, a.served_rate, a.served_requests, 4096, kmax=a.served_kmax)
             sp = served_measure(M, W, a.served_rate, a.served_requests, 1, kmax=a.served_kmax)
@@ -553,9 +690,11 @@ def run_ours(a):
             line["simulator"] = simulator_measure(M, W, a.sim_jobs)
         if world == 1 and not a.no_cpu_baseline:
             threads = os.cpu_count() or 1
-            emb, done, dt = _oracle_sample(wl, a.cpu_seconds, threads)
+            cap = _oracle_node_cap(cfg)
+            emb, done, dt = _oracle_sample(wl, a.cpu_seconds, threads, max_nodes=cap)
             line["cpu_baseline"] = {"value": emb / dt, "unit": UNIT, "cores": threads, "kind": "oracle",
-                                    "sample": f"first {done} of {nreq} requests of {wl.name}, {dt:.1f} s"}
+                                    "sample": f"first {done} of {nreq} requests of {wl.name}, {dt:.1f} s"
+                                              + (f", at most {cap} search nodes per request" if cap else "")}
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()

@@ -56,6 +56,8 @@ typedef struct mapa_ctx_s *mapa_ctx;
 enum mapa_status {
     MAPA_OK = 0,
     MAPA_NO_FIT = 1,        /* no match on the free vertices; nothing committed */
+    MAPA_INEXACT = 2,       /* MAPA_POLICY_ANYTIME past the work budget: a real match, the best one the
+                               search met, not proven to be the argmax; committed like MAPA_OK */
     MAPA_E_INVALID = -1,    /* malformed argument (ids, sizes, graph shape) */
     MAPA_E_RANGE = -2,      /* value outside the supported range (n, k, weights, int32 scores) */
     MAPA_E_NOMEM = -3,      /* device or host allocation failed, or frontier cap too small */
@@ -104,7 +106,29 @@ enum mapa_mode {
  * count keep their meaning.  Patterns
  * with more than 63 edges fail with MAPA_E_RANGE.  The bounded mode makes
  * no cut-offs for such a request. */
-enum mapa_policy_flags { MAPA_POLICY_BW_SENSITIVE = 1u };
+enum mapa_policy_flags { MAPA_POLICY_BW_SENSITIVE = 1u, MAPA_POLICY_ANYTIME = 2u };
+
+/* flags & MAPA_POLICY_ANYTIME (with alpha, beta >= 0, not with
+ * MAPA_POLICY_BW_SENSITIVE, in either mode) changes what a request past the
+ * context's work budget (mapa_ctx_set_work_budget) returns: instead of
+ * MAPA_E_BUDGET, the best match of the request's seed dive (the bounded
+ * mode's, which an anytime request runs in exhaustive mode too without
+ * letting it cut anything), with status MAPA_INEXACT, its
+ * score, AggBW and PreservedBW recomputed from the tuple, count 0.  For such
+ * a request the dive runs up to 256 k steps and is guided towards a match
+ * rather than a high score: candidates that violate two necessary conditions
+ * of any match are skipped (the image of pattern vertex j lies within its
+ * pattern distance from phi(0) in the free graph, and has at least as many
+ * free neighbours as j has later pattern neighbours), the child with the
+ * most free neighbours is taken first, at most 1024 steps are spent below
+ * one phi(0) before the next is tried, and once a match is found the dive
+ * continues best score first.  The fallback depends on the request alone,
+ * so it is the same on every run and in every batch.  It is committed like
+ * MAPA_OK (mapa_allocate, sequential batches, the served loop).  With no
+ * match from the dive the result is MAPA_E_BUDGET.  A request that finishes
+ * within the budget gets its exact result (MAPA_OK or MAPA_NO_FIT) as
+ * without the flag.  The paper's policy is exact; this is a bounded-cost
+ * fallback for free sets too large to enumerate. */
 
 typedef struct {
     int32_t alpha;
@@ -325,8 +349,11 @@ int mapa_serve_close(mapa_server srv);
  * must carry pattern_id and is decided on its own busy mask exactly as
  * mapa_allocate_batch with MAPA_BATCH_INDEPENDENT decides it (same status,
  * score, AggBW, PreservedBW, count and tuple; count is 0 in bounded mode).
- * A request with another pattern id, or a bandwidth-sensitive one, gets
- * MAPA_E_INVALID.
+ * A request with another pattern id, a bandwidth-sensitive one, or a
+ * bounded-mode one with max_embeddings > 0 gets MAPA_E_INVALID (the batched
+ * call's bounded mode applies that budget to the matches left after its
+ * cut-offs, which this kernel does not make).  The context's work budget
+ * (mapa_ctx_set_work_budget) does not apply here.
  * Limits: nreq <= 4096, the topology has at most 32 vertices, the pattern at
  * most 8; beyond them the call returns MAPA_E_RANGE and launches nothing.
  * The first call on a device resolves the scratch array's device address
@@ -354,6 +381,9 @@ typedef struct {
     uint64_t spill_bytes;      /* frontier bytes written plus read back */
     uint64_t requests;         /* requests decided */
     uint64_t embeddings;       /* matches scored, once per distinct subgraph */
+    uint64_t expand_launches;  /* launches of the level-expansion kernels (one per stored level or chunk) */
+    double expand_ms;          /* their device time (CUDA events; only while timing is on) */
+    uint64_t expand_bytes;     /* their algorithmic frontier bytes: parents read once plus children written */
 } mapa_stats;
 
 /* Autotuner of the batched path: for every pattern present in the host
@@ -372,10 +402,30 @@ int mapa_stats_get(mapa_ctx ctx, mapa_stats *out);
 /* Zeroes the counters. */
 int mapa_stats_reset(mapa_ctx ctx);
 
-/* on != 0: bracket every fused last-level launch with CUDA events on the
- * context's stream and add their device time to tail_ms (costs a stream
- * synchronisation per request group). */
+/* on != 0: bracket every fused last-level launch and every level-expansion
+ * launch with CUDA events on the stream it runs on and add their device
+ * times to tail_ms and expand_ms (request groups then run one after another,
+ * and captured graphs are not used). */
 int mapa_ctx_set_timing(mapa_ctx ctx, int on);
+
+/* Work budget of every later decision on ctx: a request whose enumeration
+ * stores more than max_partials partial matches (entries of the stored
+ * levels below the fused tail, summed over levels) stops being enumerated
+ * and ends with MAPA_E_BUDGET, count 0 and no decision; 0 (the default)
+ * sets no limit.  Unlike max_embeddings, which is checked against the count
+ * after a full enumeration, this bounds the work itself: every partial
+ * match of a request past its budget is cut at once.  The check runs
+ * between level launches (and between chunks of a level that does not fit
+ * the frontier), and a request is stopped exactly when the partial matches
+ * its full enumeration would store exceed the budget, so whether it ends
+ * with MAPA_E_BUDGET depends only on the request, the budget and its
+ * pattern's fused tail depth (which decides which levels are stored; see
+ * mapa_autotune), never on timing, the batch or the frontier cap.  It
+ * applies to batches, mapa_allocate and served decisions alike; a request
+ * that finishes within it gets exactly its unbudgeted result.  Not part of
+ * the paper: it keeps decisions on large free sets (where the number of
+ * matches grows combinatorially, Sec. 5.4) within a stated cost. */
+int mapa_ctx_set_work_budget(mapa_ctx ctx, uint64_t max_partials);
 
 /* Copies the topology's occupancy (busy mask, 8 words) to host memory. */
 int mapa_occupancy_get(mapa_ctx ctx, int32_t topo_id, uint32_t *busy_out);
@@ -447,6 +497,15 @@ int mapa_simulate(mapa_ctx ctx, int32_t topo_id, int32_t policy, int32_t njobs, 
  * PCIe links, in GB/s, as the library ranks bandwidth-sensitive matches.
  * Returns MAPA_E_RANGE unless 0 <= x, y, z <= 63. */
 int mapa_effbw_predict(int32_t x, int32_t y, int32_t z, double *out);
+
+/* Measured integer issue rate of the device (no counterpart in the paper;
+ * the ceiling for the fused tail's integer throughput): a kernel of
+ * independent dependent chains of 32-bit logic (lop3) and add instructions
+ * (kind 0), or logic, population count and add in equal numbers (kind 1,
+ * about the score increment's share of population counts), on every SM.
+ * *ops_per_s receives the best of three timed launches, in operations per
+ * second.  Allocates a 4-byte scratch word for the call. */
+int mapa_measure_int_peak(mapa_ctx ctx, int32_t kind, double *ops_per_s);
 
 /* Library version string. */
 const char *mapa_version(void);

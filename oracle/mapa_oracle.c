@@ -221,6 +221,7 @@ typedef struct {
     int64_t best_score, best_agg, best_pres;
     int32_t best_phi[OR_MAX_K];
     int aborted;
+    uint64_t max_nodes, nodes; /* search-node cap of oracle_decide_capped (0 = none) */
 } match_state;
 
 static void visit_match(match_state *s)
@@ -247,6 +248,11 @@ static void visit_match(match_state *s)
 static void extend(match_state *s, int32_t i)
 {
     if (s->aborted) return;
+    s->nodes += 1;
+    if (s->max_nodes && s->nodes > s->max_nodes) {
+        s->aborted = 1;
+        return;
+    }
     if (i == s->k) {
         visit_match(s);
         return;
@@ -265,8 +271,23 @@ static void extend(match_state *s, int32_t i)
     }
 }
 
+int oracle_decide_capped(int32_t n, const int32_t *wmat, const uint8_t *busy, int32_t k, int32_t m,
+                         const int32_t *pa, const int32_t *pb, int64_t alpha, int64_t beta, uint64_t max_maps,
+                         uint64_t max_nodes, oracle_result *out);
+
 int oracle_decide(int32_t n, const int32_t *wmat, const uint8_t *busy, int32_t k, int32_t m, const int32_t *pa,
                   const int32_t *pb, int64_t alpha, int64_t beta, uint64_t max_maps, oracle_result *out)
+{
+    return oracle_decide_capped(n, wmat, busy, k, m, pa, pb, alpha, beta, max_maps, 0, out);
+}
+
+/* oracle_decide with a cap on the search nodes (partial maps visited, the
+ * root and the matches included) as well: past either cap the result is
+ * OR_BUDGET.  The cap only stops the search early; it changes nothing that
+ * is computed. */
+int oracle_decide_capped(int32_t n, const int32_t *wmat, const uint8_t *busy, int32_t k, int32_t m,
+                         const int32_t *pa, const int32_t *pb, int64_t alpha, int64_t beta, uint64_t max_maps,
+                         uint64_t max_nodes, oracle_result *out)
 {
     memset(out, 0, sizeof(*out));
     out->k = k;
@@ -291,6 +312,7 @@ int oracle_decide(int32_t n, const int32_t *wmat, const uint8_t *busy, int32_t k
     s->alpha = alpha;
     s->beta = beta;
     s->max_maps = max_maps;
+    s->max_nodes = max_nodes;
     extend(s, 0);
 
     out->maps = s->maps;

@@ -91,6 +91,9 @@ def load(path: str | None = None):
         lib.oracle_decide.argtypes = [ctypes.c_int32, i32p, u8p, ctypes.c_int32, ctypes.c_int32, i32p, i32p,
                                       ctypes.c_int64, ctypes.c_int64, ctypes.c_uint64, ctypes.POINTER(_Result)]
         lib.oracle_decide.restype = ctypes.c_int
+        lib.oracle_decide_capped.argtypes = lib.oracle_decide.argtypes[:10] + [ctypes.c_uint64,
+                                                                                ctypes.POINTER(_Result)]
+        lib.oracle_decide_capped.restype = ctypes.c_int
         lib.oracle_decide_bounded.argtypes = lib.oracle_decide.argtypes
         lib.oracle_decide_bounded.restype = ctypes.c_int
         lib.oracle_effbw.argtypes = [ctypes.c_int64, ctypes.c_int64, ctypes.c_int64]
@@ -144,13 +147,16 @@ class Instance:
     def from_topology(cls, topo, lib=None) -> "Instance":
         return cls(topo.n, topo.u, topo.v, topo.w, topo.fill_weight, lib=lib)
 
-    def decide(self, busy, k: int, pa, pb, alpha: int = 1, beta: int = 1, max_maps: int = 0) -> Decision:
+    def decide(self, busy, k: int, pa, pb, alpha: int = 1, beta: int = 1, max_maps: int = 0,
+               max_nodes: int = 0) -> Decision:
+        """Exhaustive decision; past max_maps matches or max_nodes search nodes
+        (0 = no cap) the status is STATUS_BUDGET."""
         busy_a, busy_p = _u8(np.asarray(busy, dtype=bool))
         pa_a, pa_p = _i32(pa)
         pb_a, pb_p = _i32(pb)
         res = _Result()
-        self.lib.oracle_decide(self.n, self._wp, busy_p, int(k), len(pa_a), pa_p, pb_p, int(alpha), int(beta),
-                               int(max_maps), ctypes.byref(res))
+        self.lib.oracle_decide_capped(self.n, self._wp, busy_p, int(k), len(pa_a), pa_p, pb_p, int(alpha), int(beta),
+                                      int(max_maps), int(max_nodes), ctypes.byref(res))
         return Decision(res.status, res.score, res.agg, res.pres, res.maps, res.aut, res.classes,
                         tuple(res.tuple[:k]) if res.status == STATUS_OK else ())
 

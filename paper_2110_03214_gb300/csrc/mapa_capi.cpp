@@ -131,6 +131,23 @@ int analyze_pattern(int32_t k, const std::vector<std::pair<int, int>> &edges, Pa
             if (lo >= l) ++pa.e_in[l];
             else if (hi >= l) ++pa.e_cross[l];
         }
+    for (int i = 0; i < k; ++i) {
+        pa.fdeg[i] = static_cast<uint8_t>(__builtin_popcount(i + 1 < 32 ? adj[i] >> (i + 1) : 0u));
+        pa.dist0[i] = 255;
+    }
+    {
+        // breadth-first distances from pattern vertex 0
+        uint32_t seen = 1u, layer = 1u;
+        pa.dist0[0] = 0;
+        for (int d = 1; layer; ++d) {
+            uint32_t next = 0u;
+            for (uint32_t m = layer; m; m &= m - 1u) next |= adj[__builtin_ctz(m)];
+            next &= ~seen;
+            for (uint32_t m = next; m; m &= m - 1u) pa.dist0[__builtin_ctz(m)] = static_cast<uint8_t>(d);
+            seen |= next;
+            layer = next;
+        }
+    }
     AutSearch s;
     s.k = k;
     for (int i = 0; i < k; ++i) {
@@ -168,6 +185,9 @@ int analyze_pattern(int32_t k, const std::vector<std::pair<int, int>> &edges, Pa
             }
         }
     }
+    pa.above0 = k > 1;
+    for (int i = 1; i < k; ++i)
+        if (!((pa.lo[i] >> 0) & 1u)) pa.above0 = 0;
     *out = pa;
     if (aut_order) *aut_order = order;
     return MAPA_OK;
@@ -513,6 +533,12 @@ int mapa_stats_reset(mapa_ctx ctx) {
 int mapa_ctx_set_timing(mapa_ctx ctx, int on) {
     if (!ctx) return MAPA_E_INVALID;
     mapa::engine_set_timing(ctx->engine, on != 0);
+    return MAPA_OK;
+}
+
+int mapa_ctx_set_work_budget(mapa_ctx ctx, uint64_t max_partials) {
+    if (!ctx) return MAPA_E_INVALID;
+    mapa::engine_set_work_budget(ctx->engine, max_partials);
     return MAPA_OK;
 }
 

@@ -87,7 +87,7 @@ __global__ void k_commit(mapa_result *res, uint32_t *occ, int64_t *owner, unsign
             return;
         }
     }
-    if (res->status != MAPA_OK) return;
+    if (res->status != MAPA_OK && res->status != MAPA_INEXACT) return;
     const long long job = static_cast<long long>(atomicAdd(next_job, 1ull)) + 1;
     for (int i = 0; i < res->k; ++i) {
         const int v = res->verts[i];
@@ -118,7 +118,7 @@ __global__ void k_commit_step(mapa_result *out, int32_t *chain, uint32_t *occ, i
             return;
         }
     }
-    if (res->status != MAPA_OK) return;
+    if (res->status != MAPA_OK && res->status != MAPA_INEXACT) return;
     const long long job = static_cast<long long>(atomicAdd(next_job, 1ull)) + 1;
     for (int i = 0; i < res->k; ++i) {
         const int v = res->verts[i];
@@ -159,7 +159,7 @@ __global__ void k_commit_round(mapa_result *res, int32_t n, uint32_t *occ, int64
             stop = conflict[i] = 2;
             continue;
         }
-        if (res[i].status != MAPA_OK) continue;
+        if (res[i].status != MAPA_OK && res[i].status != MAPA_INEXACT) continue;
         uint32_t mask[MAPA_MASK_WORDS] = {};
         for (int j = 0; j < res[i].k; ++j) {
             const int v = res[i].verts[j];
@@ -322,6 +322,8 @@ void engine_stats_reset(Engine *e) { e->st = mapa_stats{}; }
 
 void engine_set_timing(Engine *e, bool on) { e->timing = on; }
 
+void engine_set_work_budget(Engine *e, uint64_t max_partials) { e->work_budget = max_partials; }
+
 int engine_stage(Engine *e, int32_t nreq, mapa_request **reqs_dev, mapa_result **out_dev, std::string *err) {
     if (nreq > e->stage_cap) {
         cudaFree(e->stage_reqs);
@@ -477,7 +479,11 @@ static int run_group(Engine *e, const TopoDevice &t, const GroupRun &gr_in, bool
         gr.g.effbw_milli = e->effbw_milli;
         gr.g.effbw_code = t.wc_effbw;
     }
-    if (!gr.bounded) gr.g.thr = nullptr;
+    // The work budget cuts a request through its threshold, so a budgeted
+    // group keeps the threshold array even when no request is bounded.
+    gr.g.work_budget = e->work_budget;
+    if (!gr.g.work_budget) gr.g.work = nullptr;
+    if (!gr.bounded && !gr.g.work) gr.g.thr = nullptr;
     switch (t.W) {
         case 1: return device ? run_group_device_w1(e, t, gr, err) : run_group_host_w1(e, t, gr, err);
         case 2: return device ? run_group_device_w2(e, t, gr, err) : run_group_host_w2(e, t, gr, err);
@@ -493,7 +499,7 @@ static int run_group(Engine *e, const TopoDevice &t, const GroupRun &gr_in, bool
 // to `size` requests.
 static int group_arrays(Engine *e, int slot, int32_t size, GroupArgs *g, std::string *err) {
     const uint64_t n = static_cast<uint64_t>(std::max(size, 1));
-    const uint64_t bytes = align_up(n * 4, 256) * 5 + align_up(n * 8, 256) * 2 + align_up(n * 32, 256);
+    const uint64_t bytes = align_up(n * 4, 256) * 6 + align_up(n * 8, 256) * 3 + align_up(n * 32, 256) * 2;
     Slot &sl = e->slots[slot];
     uint64_t have = sl.group_bytes;
     if (have < bytes) e->clear_graphs();
@@ -513,6 +519,9 @@ static int group_arrays(Engine *e, int slot, int32_t size, GroupArgs *g, std::st
     g->thr = reinterpret_cast<int32_t *>(take(n * 4));
     g->key = reinterpret_cast<uint64_t *>(take(n * 8));
     g->count = reinterpret_cast<unsigned long long *>(take(n * 8));
+    g->work = reinterpret_cast<unsigned long long *>(take(n * 8));
+    g->dive_s = reinterpret_cast<int32_t *>(take(n * 4));
+    g->dive_t = reinterpret_cast<uint32_t *>(take(n * 32));
     g->best_t = reinterpret_cast<uint32_t *>(take(n * 32));
     return MAPA_OK;
 }
@@ -549,11 +558,13 @@ static int end_batch(Engine *e, std::string *err) {
     e->st.tail_int_ops += s[kStatOps];
     e->st.spill_entries += s[kStatSpill];
     e->st.spill_bytes += s[kStatSpillBytes];
+    e->st.expand_bytes += s[kStatExpandBytes];
     if (e->timing) {
         for (size_t i = 0; i + 1 < e->events_used; i += 2) {
             float ms = 0.f;
             MAPA_CUDA_TRY(cudaEventElapsedTime(&ms, e->events[i], e->events[i + 1]));
-            e->st.tail_ms += ms;
+            if (e->pair_kind[i / 2] == 1) e->st.expand_ms += ms;
+            else e->st.tail_ms += ms;
         }
     }
     e->events_used = 0;
@@ -706,6 +717,9 @@ int engine_run_batch(Engine *e, const TopoDevice &t, const std::vector<PatternAr
         gr.g.count = a.count;
         gr.g.best_t = a.best_t;
         gr.g.thr = a.thr;
+        gr.g.work = a.work;
+        gr.g.dive_s = a.dive_s;
+        gr.g.dive_t = a.dive_t;
         gr.overflow = e->overflow + i;
     }
     // Every group of the batch, device-driven.  A batch whose shape was seen
@@ -735,7 +749,8 @@ int engine_run_batch(Engine *e, const TopoDevice &t, const std::vector<PatternAr
     } else {
         std::vector<int64_t> key = {t.id, reinterpret_cast<int64_t>(reqs_dev), reinterpret_cast<int64_t>(out_dev),
                                     nreq, reinterpret_cast<int64_t>(e->overflow), reinterpret_cast<int64_t>(e->order),
-                                    reinterpret_cast<int64_t>(e->stream), nslots};
+                                    reinterpret_cast<int64_t>(e->stream), nslots,
+                                    static_cast<int64_t>(e->work_budget)};
         for (int s = 0; s < nslots; ++s) {
             const Slot &sl = e->slots[s];
             key.push_back(reinterpret_cast<int64_t>(sl.arena));
@@ -877,7 +892,8 @@ int engine_run_chain(Engine *e, const TopoDevice &t, const std::vector<PatternAr
                                           reinterpret_cast<int64_t>(reqs_dev), reinterpret_cast<int64_t>(out_dev),
                                           reinterpret_cast<int64_t>(sl.arena), static_cast<int64_t>(sl.arena_bytes),
                                           reinterpret_cast<int64_t>(sl.group_mem), reinterpret_cast<int64_t>(e->overflow),
-                                          reinterpret_cast<int64_t>(e->stream)};
+                                          reinterpret_cast<int64_t>(e->stream),
+                                          static_cast<int64_t>(e->work_budget)};
         auto it = e->graphs.find(key);
         if (it == e->graphs.end() && e->shapes_seen.count(key)) {
             if (e->graphs.size() >= 64) e->clear_graphs();

@@ -68,6 +68,7 @@ struct Engine {
     int tail_blocks_per_sm = 0;  // 0 = from the occupancy calculator
     int dive_steps = 32;         // bounded mode: node expansions of a request's seed dive
     int degree_min_m = 6;        // bounded mode: degree term only where >= this many pattern vertices remain
+    uint64_t work_budget = 0;    // stored partial matches a request may produce (0 = no limit)
     std::map<std::pair<int32_t, int32_t>, int> tail_table;  // (topology, pattern) -> tuned depth
     // Captured launch sequences of independent batches, keyed by batch shape.
     bool use_graphs = true;
@@ -83,7 +84,8 @@ struct Engine {
         graphs.clear();
         shapes_seen.clear();
     }
-    std::vector<cudaEvent_t> events;  // pairs around fused last-level launches
+    std::vector<cudaEvent_t> events;  // pairs around timed launches
+    std::vector<uint8_t> pair_kind;   // per pair: 0 = fused last level, 1 = level expansion
     size_t events_used = 0;
 
     cudaEvent_t next_event() {
@@ -93,6 +95,13 @@ struct Engine {
             events.push_back(ev);
         }
         return events[events_used++];
+    }
+    // Two events bracketing one timed launch of the given kind.
+    void timed_pair(uint8_t kind, cudaEvent_t *ev0, cudaEvent_t *ev1) {
+        if (pair_kind.size() <= events_used / 2) pair_kind.resize(events_used / 2 + 1);
+        pair_kind[events_used / 2] = kind;
+        *ev0 = next_event();
+        *ev1 = next_event();
     }
 };
 

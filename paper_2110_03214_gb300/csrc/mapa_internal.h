@@ -43,6 +43,12 @@ struct PatternArgs {
     uint32_t lo[kMaxK];
     uint16_t e_cross[kMaxK + 1];
     uint16_t e_in[kMaxK + 1];
+    // Feasibility filters of the anytime seed dive (necessary conditions on
+    // any match): fdeg[i] = neighbours of i with a larger id; dist0[i] =
+    // distance from vertex 0 to i in the pattern (255: not connected).
+    uint8_t fdeg[kMaxK];
+    uint8_t dist0[kMaxK];
+    int32_t above0;  // 1: every other pattern vertex has the constraint phi(0) < phi(i)
 };
 
 // Hardware graph in device memory.
@@ -94,6 +100,15 @@ struct GroupArgs {
     // INT_MAX = proven to have no match.  nullptr when no request of the
     // group is bounded.
     int32_t *thr;              // [size]
+    // Work budget (0 = none): partial matches stored per request so far; a
+    // request past work_budget gets thr = INT_MAX (every later partial is
+    // cut) and ends with MAPA_E_BUDGET.  nullptr when no budget is set.
+    unsigned long long *work;  // [size]
+    unsigned long long work_budget;
+    // Anytime requests: the seed dive's best complete match (score INT_MIN
+    // = none) and its tuple bytes.
+    int32_t *dive_s;           // [size]
+    uint32_t *dive_t;          // [size * 8]
     // Bandwidth-sensitive group (Algorithm 1, first branch): scores are the
     // link-count index (x * R + y) * R + z of the match, ranked through
     // effbw_rank; sens_ok = 0 when the pattern has more edges than R - 1.
@@ -158,6 +173,7 @@ int engine_autotune(Engine *e, const TopoDevice &t, const std::vector<PatternArg
                     const mapa_request *reqs_host, int32_t *chosen, std::string *err);
 void engine_stats_reset(Engine *e);
 void engine_set_timing(Engine *e, bool on);
+void engine_set_work_budget(Engine *e, uint64_t max_partials);
 
 // Allocation-free single-kernel decision (mapa_noalloc.cu).
 int noalloc_decide(const TopoDevice &t, const PatternArgs &pat, int32_t pattern_id, int32_t nreq,

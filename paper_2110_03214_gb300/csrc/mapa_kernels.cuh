@@ -58,7 +58,11 @@ constexpr unsigned long long kValueMask = (1ull << 62) - 1;
 constexpr unsigned kSpinLimit = 1u << 24;
 
 // Device stats slots (summed over a batch, read once at its end).
-enum StatSlot { kStatNodes = 0, kStatLeaves, kStatParents, kStatOps, kStatSpill, kStatSpillBytes, kStatSlots };
+enum StatSlot {
+    kStatNodes = 0, kStatLeaves, kStatParents, kStatOps, kStatSpill, kStatSpillBytes,
+    kStatExpandBytes,  // algorithmic bytes of the level expansions: parents read + children written
+    kStatSlots
+};
 
 // ----------------------------------------------------------------------------
 // Mask helpers
@@ -389,8 +393,11 @@ __device__ __forceinline__ int32_t twice_floor_loss(const SmemTopo &s, const uin
 // -1 = decide with the degree term.
 __device__ __forceinline__ int cut_first(const SmemTopo &s, int nR, int32_t S, int32_t al, int32_t be, int32_t thr,
                                          const LevelBound &lb, long long &base2) {
+    // INT_MAX: nothing is left to find (no match exists, or the request is
+    // past its work budget), whatever the signs of alpha and beta
+    if (thr == INT_MAX) return 1;
     if (thr == INT_MIN || al < 0 || be < 0) return 0;
-    if (thr == INT_MAX || nR < lb.m) return 1;
+    if (nR < lb.m) return 1;
     const long long wmax = s.wmax, wmin = s.wmin, ab = static_cast<long long>(al) - be;
     const long long b1 = al * wmax * lb.e_cross + lb.e_in * max(ab * wmax, ab * wmin);
     if (S + b1 < thr) return 1;
@@ -577,10 +584,39 @@ __global__ void k_setup(TopoArgs topo, GroupArgs g, LevelView L0, unsigned long 
             g.alpha[i] = al;
             g.beta[i] = be;
             if (g.thr) g.thr[i] = INT_MIN;
+            if (g.work) g.work[i] = 0ull;
+            if (g.dive_s) g.dive_s[i] = INT_MIN;
             g.key[i] = 0ull;
             g.count[i] = 0ull;
             g.best_valid[i] = state;
         }
+    }
+}
+
+// Work budget: adds to each request's count of stored partial matches its
+// entries in level lv (P entries, ordered by request, so two binary searches
+// per request find them), and marks every request past the budget with
+// thr = INT_MAX, which cuts all its later partials.  Runs between level
+// launches, so which requests are cut does not depend on timing.
+static __global__ void k_budget(LevelView lv, const unsigned long long *count_dev, unsigned long long count_host,
+                         GroupArgs g) {
+    const unsigned long long P = count_dev ? *count_dev : count_host;
+    if (P == 0ull) return;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < g.size; i += gridDim.x * blockDim.x) {
+        auto first_at_least = [&](uint32_t key) {
+            unsigned long long lo = 0ull, hi = P;
+            while (lo < hi) {
+                const unsigned long long mid = (lo + hi) >> 1;
+                if (lv.r[mid] < key) lo = mid + 1;
+                else hi = mid;
+            }
+            return lo;
+        };
+        const unsigned long long nr = first_at_least(static_cast<uint32_t>(i) + 1u) - first_at_least(static_cast<uint32_t>(i));
+        if (nr == 0ull) continue;
+        const unsigned long long w = g.work[i] + nr;
+        g.work[i] = w;
+        if (w > g.work_budget) g.thr[i] = INT_MAX;
     }
 }
 
@@ -592,23 +628,94 @@ __global__ void k_setup(TopoArgs topo, GroupArgs g, LevelView L0, unsigned long 
 // bound cannot beat the best complete score so far is skipped.  On return,
 // inc/found hold the best complete score; the result is true when the whole
 // search space was finished within the step limit.
+// Guided dive (anytime requests): two necessary conditions on any match
+// narrow the candidates of pattern vertex j -- its image lies within
+// distance dist0[j] of phi(0) in the free graph (the pattern path from 0 to
+// j maps onto a walk through free vertices), and has at least fdeg[j] free
+// unused neighbours (its later pattern neighbours need distinct images).
+// Neither removes a vertex of any match, so they only steer the descent away
+// from dead ends.  Keeps of cand[w] the bits whose vertex has >= need
+// neighbours in R (warp-uniform masks; lane l tests bit l of every word).
+template <int W>
+__device__ __forceinline__ void degree_filter(const SmemTopo &s, uint32_t (&cand)[W], const uint32_t (&R)[W],
+                                              int need, int lane) {
+    if (need <= 0) return;
+#pragma unroll
+    for (int w = 0; w < W; ++w) {
+        bool pass = false;
+        if ((cand[w] >> lane) & 1u) {
+            const uint32_t *row = s.adj + (32 * w + lane) * W;
+            int c = 0;
+#pragma unroll
+            for (int x = 0; x < W; ++x) c += __popc(row[x] & R[x]);
+            pass = c >= need;
+        }
+        cand[w] = __ballot_sync(kFull, pass);
+    }
+}
+
+// Lane d receives ball = the vertices of F within distance d of root in G[F].
+template <int W>
+__device__ __forceinline__ void distance_balls(const SmemTopo &s, const uint32_t (&F)[W], int root, int lane,
+                                               uint32_t (&ball)[W]) {
+    uint32_t cur[W];
+#pragma unroll
+    for (int w = 0; w < W; ++w) cur[w] = (root >> 5) == w ? 1u << (root & 31) : 0u;
+    for (int d = 0; d < 32; ++d) {
+        if (lane == d)
+#pragma unroll
+            for (int w = 0; w < W; ++w) ball[w] = cur[w];
+        uint32_t acc[W];
+#pragma unroll
+        for (int w = 0; w < W; ++w) acc[w] = 0u;
+#pragma unroll
+        for (int w = 0; w < W; ++w)
+            if ((cur[w] >> lane) & 1u)
+#pragma unroll
+                for (int x = 0; x < W; ++x) acc[x] |= s.adj[(32 * w + lane) * W + x];
+#pragma unroll
+        for (int x = 0; x < W; ++x) {
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) acc[x] |= __shfl_xor_sync(kFull, acc[x], o);
+            cur[x] = (cur[x] | acc[x]) & F[x];
+        }
+    }
+}
+
 template <int W, int CT>
 __device__ bool dive_warp(const SmemTopo &s, const PatternArgs &pat, int32_t S0, const uint32_t (&F)[W], int32_t al,
-                          int32_t be, int lane, int steps, int32_t &inc, bool &found) {
+                          int32_t be, int lane, int steps, bool guided, int32_t &inc, bool &found, int &rec_v) {
     const Scorer<W, CT> sc(s, al, be);
     const int k = pat.k;
     int32_t my_S = S0;
     int my_v = 0;
-    uint32_t my_R[W], my_rem[W];
+    uint32_t my_R[W], my_rem[W], ball[W];
+    uint32_t root_cand[W];
 #pragma unroll
     for (int w = 0; w < W; ++w) {
         my_R[w] = F[w];
-        my_rem[w] = lane == 0 ? F[w] : 0u;  // pattern vertex 0: no earlier neighbour, no constraint
+        root_cand[w] = F[w];  // pattern vertex 0: no earlier neighbour, no constraint
+        ball[w] = 0u;
     }
+    if (guided) degree_filter<W>(s, root_cand, F, pat.fdeg[0], lane);
+#pragma unroll
+    for (int w = 0; w < W; ++w) my_rem[w] = lane == 0 ? root_cand[w] : 0u;
     inc = INT_MIN;
     found = false;
+    rec_v = 0;  // lane j: phi(j) of the best complete match so far
     int j = 0;
+    // guided: until the first match, at most kRootSteps steps below one
+    // choice of phi(0), then the next one (an abandoned subtree means the
+    // dive no longer proves that no match exists)
+    constexpr int kRootSteps = 1024;
+    int root_steps = 0;
+    bool abandoned = false;
     for (int step = 0; step < steps; ++step) {
+        if (guided && !found && j > 0 && ++root_steps > kRootSteps) {
+            j = 0;
+            root_steps = 0;
+            abandoned = true;
+        }
         uint32_t rem[W], R[W];
         bool any = false;
 #pragma unroll
@@ -619,7 +726,7 @@ __device__ bool dive_warp(const SmemTopo &s, const PatternArgs &pat, int32_t S0,
         }
         const int32_t S = __shfl_sync(kFull, my_S, j);
         if (!any) {
-            if (j == 0) return true;
+            if (j == 0) return !abandoned;
             --j;
             continue;
         }
@@ -627,24 +734,38 @@ __device__ bool dive_warp(const SmemTopo &s, const PatternArgs &pat, int32_t S0,
 #pragma unroll
         for (int w = 0; w < W; ++w) B[w] = 0u;
         for (uint32_t bm = pat.back[j]; bm; bm &= bm - 1u) set_bit<W>(B, __shfl_sync(kFull, my_v, __ffs(bm) - 1));
+        // child order: best score first (ties: smaller vertex); a guided dive
+        // that has no match yet takes the child with the most free unused
+        // neighbours first (feasibility before score; a score-first descent
+        // picks low-degree vertices, which end long patterns in dead ends)
+        const bool by_room = guided && !found;
         int32_t best = INT_MIN;
-        int bv = INT_MAX;
+        int bv = INT_MAX, broom = -1;
 #pragma unroll
         for (int w = 0; w < W; ++w)
             if ((rem[w] >> lane) & 1u) {
-                const int32_t x = S + sc.delta(32 * w + lane, B, R);
-                if (x > best) {
+                const int v = 32 * w + lane;
+                const int32_t x = S + sc.delta(v, B, R);
+                int room = 0;
+                if (by_room) {
+#pragma unroll
+                    for (int y = 0; y < W; ++y) room += __popc(s.adj[v * W + y] & R[y]);
+                }
+                if (room > broom || (room == broom && x > best)) {
                     best = x;
-                    bv = 32 * w + lane;
+                    bv = v;
+                    broom = room;
                 }
             }
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) {
             const int32_t ob = __shfl_xor_sync(kFull, best, o);
             const int ov = __shfl_xor_sync(kFull, bv, o);
-            if (ob > best || (ob == best && ov < bv)) {
+            const int orr = __shfl_xor_sync(kFull, broom, o);
+            if (orr > broom || (orr == broom && (ob > best || (ob == best && ov < bv)))) {
                 best = ob;
                 bv = ov;
+                broom = orr;
             }
         }
         if (lane == j) {
@@ -652,6 +773,7 @@ __device__ bool dive_warp(const SmemTopo &s, const PatternArgs &pat, int32_t S0,
             my_v = bv;
         }
         if (j + 1 == k) {
+            if (!found || best > inc) rec_v = my_v;  // lanes < k hold the path, lane j its last vertex
             inc = found ? max(inc, best) : best;
             found = true;
             continue;
@@ -679,6 +801,33 @@ __device__ bool dive_warp(const SmemTopo &s, const PatternArgs &pat, int32_t S0,
             lbv = max(lbv, a == j ? bv : __shfl_sync(kFull, my_v, a));
         }
         and_above<W>(cand, lbv);
+        if (guided) {
+            if (j == 0) {
+                // phi(0) = bv from here on; where every other pattern vertex
+                // is ordered above vertex 0, its match lies in the vertices
+                // above bv, so distances are taken there
+                uint32_t reach[W];
+#pragma unroll
+                for (int w = 0; w < W; ++w) reach[w] = F[w];
+                if (pat.above0) {
+                    and_above<W>(reach, bv);
+                    set_bit<W>(reach, bv);
+                }
+                distance_balls<W>(s, reach, bv, lane, ball);
+                root_steps = 0;
+                // fewer than k vertices reachable: no match below this root
+                int reachable = 0;
+#pragma unroll
+                for (int w = 0; w < W; ++w) reachable += __popc(__shfl_sync(kFull, ball[w], 31));
+                if (reachable < k) continue;
+            }
+            const int dd = pat.dist0[j + 1];
+            if (dd < 32) {
+#pragma unroll
+                for (int w = 0; w < W; ++w) cand[w] &= __shfl_sync(kFull, ball[w], dd);
+            }
+            degree_filter<W>(s, cand, R1, pat.fdeg[j + 1], lane);
+        }
         if (lane == j + 1) {
             my_S = best;
 #pragma unroll
@@ -692,10 +841,11 @@ __device__ bool dive_warp(const SmemTopo &s, const PatternArgs &pat, int32_t S0,
     return false;
 }
 
-// Bounded mode, per request (one warp each): the seed score of the cut-offs.
-// thr = the best complete score the dive found; INT_MAX when the dive
-// finished the whole search space without a match (there is none); INT_MIN
-// when it found nothing within the step limit (no cut-offs).
+// Per bounded or anytime request (one warp each): the seed dive.  thr = the
+// best complete score it found (bounded mode: the seed of the cut-offs);
+// INT_MAX when it finished the whole search space without a match (there is
+// none); INT_MIN otherwise (no cut-offs).  An anytime request also keeps the
+// dive's best match as its fallback.
 template <int W, int CT>
 __global__ void __launch_bounds__(kTpb) k_dive(TopoArgs topo, PatternArgs pat, GroupArgs g, LevelView L0, int steps) {
     const SmemTopo s = stage_topology<W>(topo, true);
@@ -705,14 +855,34 @@ __global__ void __launch_bounds__(kTpb) k_dive(TopoArgs topo, PatternArgs pat, G
     for (int i = gw; i < g.size; i += nw) {
         const mapa_request &q = g.reqs[g.req_index[i]];
         const int32_t al = g.alpha[i], be = g.beta[i];
-        if (q.policy.mode != MAPA_MODE_BOUNDED || g.best_valid[i] != 0 || al < 0 || be < 0) continue;
+        const bool bounded = q.policy.mode == MAPA_MODE_BOUNDED;
+        // an anytime request keeps the dive's match as its fallback, so it
+        // gets enough steps for several complete descents
+        const bool anytime = (q.policy.flags & MAPA_POLICY_ANYTIME) != 0 && g.dive_s != nullptr;
+        if (g.sens || !(bounded || anytime) || g.best_valid[i] != 0 || al < 0 || be < 0) continue;
         uint32_t F[W];
 #pragma unroll
         for (int w = 0; w < W; ++w) F[w] = L0.R[w * L0.cap + i];
         int32_t inc;
         bool found;
-        const bool done = dive_warp<W, CT>(s, pat, L0.S[i], F, al, be, lane, steps, inc, found);
-        if (lane == 0) g.thr[i] = found ? inc : (done ? INT_MAX : INT_MIN);
+        int rec_v;
+        const int my_steps = anytime ? max(steps, 256 * pat.k) : steps;
+        const bool done = dive_warp<W, CT>(s, pat, L0.S[i], F, al, be, lane, my_steps, anytime, inc, found, rec_v);
+        // a finished dive without a match proves there is none (cut every
+        // partial, in either mode); a found score seeds the cut-offs of the
+        // bounded mode only (an exhaustive request must count every match)
+        if (lane == 0) g.thr[i] = found ? (bounded ? inc : INT_MIN) : (done ? INT_MAX : INT_MIN);
+        if (anytime && found) {
+#pragma unroll
+            for (int w = 0; w < 8; ++w) {
+                uint32_t word = 0u;
+#pragma unroll
+                for (int b = 0; b < 4; ++b)
+                    word |= static_cast<uint32_t>(__shfl_sync(kFull, rec_v, 4 * w + b) & 0xFF) << (8 * b);
+                if (lane == 0) g.dive_t[static_cast<uint64_t>(i) * 8 + w] = 4 * w < pat.k ? word : 0u;
+            }
+            if (lane == 0) g.dive_s[i] = inc;
+        }
     }
 }
 
@@ -921,7 +1091,8 @@ __global__ void __launch_bounds__(kTpb) k_expand(TopoArgs topo, LevelView in, Le
                                                  unsigned int *tile_ctr, unsigned long long *status, int32_t *overflow,
                                                  const int32_t *alpha, const int32_t *beta, int32_t *err,
                                                  unsigned long long *stats, unsigned long long child_bytes,
-                                                 const int32_t *thr, LevelBound lbd) {
+                                                 unsigned long long parent_bytes, const int32_t *thr,
+                                                 LevelBound lbd) {
     const unsigned long long P = *count_in;
     const unsigned long long ntiles = (P + kTpb - 1) / kTpb;
     if (ntiles == 0) {
@@ -984,6 +1155,7 @@ __global__ void __launch_bounds__(kTpb) k_expand(TopoArgs topo, LevelView in, Le
                 if (fits && stats) {
                     atomicAdd(stats + kStatSpill, total);
                     atomicAdd(stats + kStatSpillBytes, 2ull * total * child_bytes);
+                    atomicAdd(stats + kStatExpandBytes, P * parent_bytes + total * child_bytes);
                 }
             }
         }
@@ -1697,20 +1869,39 @@ __global__ void k_finalize(TopoArgs topo, PatternArgs pat, GroupArgs g) {
         res.k = pat.k;
         res.count = g.count[i];
         const int32_t state = g.best_valid[i];
+        // Past the context's work budget the enumeration was cut short: no
+        // decision, or for an anytime request the seed dive's match.  (The
+        // matches the enumeration scored before the cut are not used: which
+        // ones they are depends on the other requests sharing its chunks,
+        // while the dive depends on the request alone.)
+        const bool over = state >= 0 && g.work && g.work[i] > g.work_budget;
+        const uint32_t *tw = g.best_t + static_cast<uint64_t>(i) * 8;
+        int32_t want = g.best_s[i];
+        bool have = state == 1;
+        if (over) {
+            res.count = 0;
+            const bool anytime = (q.policy.flags & MAPA_POLICY_ANYTIME) && g.dive_s && !g.sens;
+            have = anytime && g.dive_s[i] != INT_MIN;
+            if (have) {
+                tw = g.dive_t + static_cast<uint64_t>(i) * 8;
+                want = g.dive_s[i];
+            }
+        }
         if (state == -2) {
             res.status = MAPA_E_RANGE;
             res.count = 0;
         } else if (state == -3) {
             res.status = MAPA_E_INVALID;
             res.count = 0;
-        } else if (q.policy.max_embeddings > 0 && res.count > q.policy.max_embeddings) {
+        } else if (over && !have) {
             res.status = MAPA_E_BUDGET;
-        } else if (state != 1) {
+        } else if (!over && q.policy.max_embeddings > 0 && res.count > q.policy.max_embeddings) {
+            res.status = MAPA_E_BUDGET;
+        } else if (!have) {
             res.status = MAPA_NO_FIT;
         } else {
             uint8_t t[kMaxK];
-            for (int j = 0; j < pat.k; ++j)
-                t[j] = static_cast<uint8_t>((g.best_t[static_cast<uint64_t>(i) * 8 + (j >> 2)] >> ((j & 3) * 8)) & 0xFFu);
+            for (int j = 0; j < pat.k; ++j) t[j] = static_cast<uint8_t>((tw[j >> 2] >> ((j & 3) * 8)) & 0xFFu);
             long long agg = 0;
             for (int v = 0; v < pat.k; ++v) {
                 uint32_t m = pat.back[v];
@@ -1740,7 +1931,7 @@ __global__ void k_finalize(TopoArgs topo, PatternArgs pat, GroupArgs g) {
                 }
             }
             const long long pres = twice / 2;
-            res.status = MAPA_OK;
+            res.status = over ? MAPA_INEXACT : MAPA_OK;
             if (g.sens) {
                 // link-count index of the tuple from the class of every pattern
                 // edge's link; its Eq. 2 rank must be the one the tail chose
@@ -1755,8 +1946,8 @@ __global__ void k_finalize(TopoArgs topo, PatternArgs pat, GroupArgs g) {
             } else {
                 const long long score =
                     static_cast<long long>(g.alpha[i]) * agg + static_cast<long long>(g.beta[i]) * pres;
-                if (score != g.best_s[i]) atomicExch(g.error, kDevScoreMismatch);
-                res.score = g.best_s[i];
+                if (score != want) atomicExch(g.error, kDevScoreMismatch);
+                res.score = want;
             }
             res.agg = static_cast<int32_t>(agg);
             res.pres = static_cast<int32_t>(pres);

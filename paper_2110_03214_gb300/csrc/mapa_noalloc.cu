@@ -147,6 +147,10 @@ __device__ __forceinline__ uint32_t na_free_set(const mapa_request &q, int n) {
 __device__ int32_t na_request_state(const mapa_request &q, int32_t pattern_id, int64_t total_weight) {
     if (q.pattern_id != pattern_id || (q.policy.flags & MAPA_POLICY_BW_SENSITIVE)) return -3;
     if (q.policy.mode != MAPA_MODE_EXHAUSTIVE && q.policy.mode != MAPA_MODE_BOUNDED) return -3;
+    // The batched path's bounded mode applies max_embeddings to the matches
+    // left after its cut-offs; this kernel has no cut-offs, so it cannot give
+    // the same answer and refuses the combination.
+    if (q.policy.mode == MAPA_MODE_BOUNDED && q.policy.max_embeddings > 0) return -3;
     const long long mag = (llabs(static_cast<long long>(q.policy.alpha)) + llabs(static_cast<long long>(q.policy.beta))) *
                           static_cast<long long>(total_weight);
     return mag >= (1LL << 31) ? -2 : 0;

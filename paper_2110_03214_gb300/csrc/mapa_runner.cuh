@@ -47,10 +47,20 @@ inline TailArgs make_tail_args(const PatternArgs &pat, int T, int W, int C) {
         backs += __builtin_popcount(ta.back_old[t]);
         los += __builtin_popcount(ta.lo_old[t]);
     }
+    // Algorithmic integer operations per unit (the method's own work): a
+    // parent at level i costs (|back[i]| + 3) W word operations for its
+    // candidate mask, a generated child 2 C W + |back[i]| + 4 for its score
+    // increment, and a complete match one more for the argmax compare.  A
+    // node of the first tail level is a child of the parent and the parent
+    // of the next level; a leaf is a child of the last level.
+    (void)backs;
+    (void)los;
     const uint64_t w = static_cast<uint64_t>(W), c = static_cast<uint64_t>(C);
-    ta.cost_parent = backs * (2 + 2 * w) + 3 * los + 3 * w + 1;
-    ta.cost_node = 4 * c * w + 3 * c + 6 * w + 2;
-    ta.cost_leaf = 4 * c * w + 3 * c + 2;
+    auto nback = [&](int v) { return static_cast<uint64_t>(__builtin_popcount(pat.back[v])); };
+    const int last = pat.k - 1;
+    ta.cost_parent = (nback(ta.ell) + 3) * w;
+    ta.cost_node = T >= 2 ? (2 * c * w + nback(ta.ell) + 4) + (nback(ta.ell + 1) + 3) * w : 0;
+    ta.cost_leaf = 2 * c * w + nback(last) + 4 + 1;
     ta.bound = level_bound(pat, ta.ell);
     return ta;
 }
@@ -122,13 +132,25 @@ struct Runner {
         k_setup<W><<<sgrid, kTpb, smem_all, st>>>(targs, g, lay.level[0], count0);
         MAPA_CUDA_TRY(cudaGetLastError());
         e->st.kernel_launches += 1;
-        if (g.thr) {
-            // bounded mode: seed scores for the cut-offs, one warp per request
+        if (g.thr && !gr.sens) {
+            // bounded mode: seed scores for the cut-offs; anytime requests:
+            // their fallback match (one warp per request; others skip)
             const unsigned dgrid = static_cast<unsigned>(std::min<uint64_t>(ceil_div(g.size, kWarps), 4096));
             k_dive<W, CT><<<dgrid, kTpb, smem_all, st>>>(targs, pat, g, lay.level[0], e->dive_steps);
             MAPA_CUDA_TRY(cudaGetLastError());
             e->st.kernel_launches += 1;
         }
+        return MAPA_OK;
+    }
+
+    // Work budget: count the stored partials of each request in a level just
+    // written and mark the requests past the budget.
+    int budget(const LevelView &lv, const unsigned long long *count_dev, unsigned long long count_host) {
+        if (!g.work) return MAPA_OK;
+        const unsigned bgrid = static_cast<unsigned>(std::min<uint64_t>(ceil_div(g.size, 256), 4096));
+        k_budget<<<bgrid, 256, 0, st>>>(lv, count_dev, count_host, g);
+        MAPA_CUDA_TRY(cudaGetLastError());
+        e->st.kernel_launches += 1;
         return MAPA_OK;
     }
 
@@ -152,8 +174,7 @@ struct Runner {
             std::max<uint64_t>(1, std::min<uint64_t>(ceil_div(max_parents, kTile), uint64_t(e->sm_count) * per_sm)));
         cudaEvent_t ev0 = nullptr, ev1 = nullptr;
         if (e->timing) {
-            ev0 = e->next_event();
-            ev1 = e->next_event();
+            e->timed_pair(0, &ev0, &ev1);
             MAPA_CUDA_TRY(cudaEventRecord(ev0, st));
         }
         bool launched = false;
@@ -219,12 +240,21 @@ struct Runner {
         for (int ell = 0; ell < lay.L; ++ell) {
             const unsigned grid = static_cast<unsigned>(std::max<uint64_t>(
                 1, std::min<uint64_t>(ceil_div(lay.bound[ell], kTpb), uint64_t(e->sm_count) * nb_expand)));
+            cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+            if (e->timing) {
+                e->timed_pair(1, &ev0, &ev1);
+                MAPA_CUDA_TRY(cudaEventRecord(ev0, st));
+            }
             expand<<<grid, kTpb, smem_all, st>>>(
                 targs, lay.level[ell], lay.level[ell + 1], ell, pat.back[ell], pat.lo[ell], lay.counts + ell,
                 lay.counts + ell + 1, lay.level[ell + 1].cap, lay.tiles + ell, lay.status[ell], gr.overflow, g.alpha,
-                g.beta, e->d_error, e->d_stats, entry_bytes(ell + 1, W), g.thr, bound_at(ell));
+                g.beta, e->d_error, e->d_stats, entry_bytes(ell + 1, W), entry_bytes(ell, W), g.thr, bound_at(ell));
             MAPA_CUDA_TRY(cudaGetLastError());
+            if (e->timing) MAPA_CUDA_TRY(cudaEventRecord(ev1, st));
             e->st.kernel_launches += 1;
+            e->st.expand_launches += 1;
+            rc = budget(lay.level[ell + 1], lay.counts + ell + 1, 0ull);
+            if (rc != MAPA_OK) return rc;
         }
         rc = last_level(lay.counts + lay.L, 0ull, lay.tiles + lay.L, lay.bound[lay.L]);
         if (rc != MAPA_OK) return rc;
@@ -242,12 +272,20 @@ struct Runner {
         const LevelView &in = lay.level[ell];
         const LevelView &out = lay.level[ell + 1];
         const uint64_t nb = ceil_div(P, kTile);
+        cudaEvent_t cev0 = nullptr, cev1 = nullptr;
+        if (e->timing) {
+            e->timed_pair(1, &cev0, &cev1);
+            MAPA_CUDA_TRY(cudaEventRecord(cev0, st));
+        }
         k_count<W><<<static_cast<unsigned>(nb), kTpb, g.thr ? smem_all : smem_adj, st>>>(
             targs, in, P, pat.back[ell], pat.lo[ell], lay.warp_cnt[ell], lay.blk_cnt[ell], g.thr, g.alpha, g.beta,
             bound_at(ell));
         launch_scan(lay.blk_cnt[ell], lay.blk_off[ell], nb, st);
         MAPA_CUDA_TRY(cudaGetLastError());
+        if (e->timing) MAPA_CUDA_TRY(cudaEventRecord(cev1, st));
         e->st.kernel_launches += 2;
+        e->st.expand_launches += 1;
+        e->st.expand_bytes += P * entry_bytes(ell, W);  // the parents, read once (algorithmically)
         MAPA_CUDA_TRY(cudaMemcpyAsync(e->h_pinned, lay.blk_off[ell] + nb, sizeof(unsigned long long),
                                       cudaMemcpyDeviceToHost, st));
         MAPA_CUDA_TRY(cudaStreamSynchronize(st));
@@ -271,14 +309,24 @@ struct Runner {
                 }
             }
             const uint64_t children = total > lay.E ? off[b1] - off[b0] : total;
+            cudaEvent_t wev0 = nullptr, wev1 = nullptr;
+            if (e->timing) {
+                e->timed_pair(1, &wev0, &wev1);
+                MAPA_CUDA_TRY(cudaEventRecord(wev0, st));
+            }
             k_write<W, CT><<<static_cast<unsigned>(b1 - b0), kTpb, smem_all, st>>>(
                 targs, in, P, ell, pat.back[ell], pat.lo[ell], out, lay.warp_cnt[ell], lay.blk_off[ell], b0,
                 g.alpha, g.beta, g.thr, bound_at(ell));
             MAPA_CUDA_TRY(cudaGetLastError());
+            if (e->timing) MAPA_CUDA_TRY(cudaEventRecord(wev1, st));
             e->st.kernel_launches += 1;
+            e->st.expand_launches += 1;
+            e->st.expand_bytes += children * entry_bytes(ell + 1, W);
             e->st.spill_entries += children;
             e->st.spill_bytes += 2 * children * entry_bytes(ell + 1, W);
-            const int rc = process(ell + 1, children);
+            int rc = budget(out, nullptr, children);
+            if (rc != MAPA_OK) return rc;
+            rc = process(ell + 1, children);
             if (rc != MAPA_OK) return rc;
             b0 = b1;
         }

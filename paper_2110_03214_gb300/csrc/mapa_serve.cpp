@@ -34,6 +34,10 @@ namespace {
 
 using Clock = std::chrono::steady_clock;
 
+// A decision that holds accelerators once committed: exact, or an anytime
+// request's best match past its work budget.
+inline bool placed(int32_t status) { return status == MAPA_OK || status == MAPA_INEXACT; }
+
 struct Pending {
     mapa_event ev;
     int32_t rounds = 0;
@@ -237,7 +241,7 @@ int decide_round(mapa_server srv, std::vector<Pending> &round, std::vector<mapa_
                 ((round[i].ev.policy.flags & MAPA_POLICY_BW_SENSITIVE) ? mapa::kKindSensitive : 0)));
         } else if (srv->h_conflict[i] == 2) {
             deferred[i] = 1;
-        } else if (res[i].status == MAPA_OK) {
+        } else if (placed(res[i].status)) {
             add_mask(cur, res[i]);
         }
     }
@@ -277,7 +281,7 @@ int decide_round(mapa_server srv, std::vector<Pending> &round, std::vector<mapa_
                 chain_blocked = true;
                 continue;
             }
-            if (res[i].status == MAPA_OK) add_mask(cur, res[i]);
+            if (placed(res[i].status)) add_mask(cur, res[i]);
         }
         if (speculate) srv->conflicts += static_cast<uint64_t>(m);  // decided again after an overlap
     }
@@ -292,7 +296,7 @@ int decide_round(mapa_server srv, std::vector<Pending> &round, std::vector<mapa_
         if (!deferred[i]) continue;
         bool committed_this_round = false;
         for (int32_t j = 0; j < n; ++j)
-            if (!deferred[j] && res[j].status == MAPA_OK && res[j].job_id > 0) committed_this_round = true;
+            if (!deferred[j] && placed(res[j].status) && res[j].job_id > 0) committed_this_round = true;
         const bool nothing_to_release = srv->live.empty() && srv->expiries.empty() && srv->departs.empty() &&
                                         !committed_this_round;
         if (!final_no_fit_done && res[i].status == MAPA_NO_FIT && nothing_to_release) {
@@ -308,7 +312,7 @@ int decide_round(mapa_server srv, std::vector<Pending> &round, std::vector<mapa_
         s.result = res[i];
         out.push_back(s);
         srv->decisions += 1;
-        if (res[i].status == MAPA_OK && res[i].job_id > 0) {
+        if (placed(res[i].status) && res[i].job_id > 0) {
             Job job;
             for (int j = 0; j < res[i].k; ++j) job.verts.push_back(res[i].verts[j]);
             srv->live.emplace(res[i].job_id, std::move(job));

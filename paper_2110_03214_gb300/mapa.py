@@ -18,6 +18,7 @@ from . import build as _build
 
 MAPA_OK = 0
 MAPA_NO_FIT = 1
+MAPA_INEXACT = 2
 MAPA_E_INVALID = -1
 MAPA_E_RANGE = -2
 MAPA_E_NOMEM = -3
@@ -29,6 +30,7 @@ MAPA_E_STATE = -7
 MAPA_RING, MAPA_TREE, MAPA_CLIQUE, MAPA_PATH = 0, 1, 2, 3
 MAPA_MODE_EXHAUSTIVE, MAPA_MODE_BOUNDED = 0, 1
 MAPA_POLICY_BW_SENSITIVE = 1
+MAPA_POLICY_ANYTIME = 2
 KIND = {"ring": MAPA_RING, "tree": MAPA_TREE, "clique": MAPA_CLIQUE, "path": MAPA_PATH}
 
 MAPA_BATCH_INDEPENDENT = 0
@@ -114,6 +116,9 @@ class Stats(ctypes.Structure):
         ("spill_bytes", ctypes.c_uint64),
         ("requests", ctypes.c_uint64),
         ("embeddings", ctypes.c_uint64),
+        ("expand_launches", ctypes.c_uint64),
+        ("expand_ms", ctypes.c_double),
+        ("expand_bytes", ctypes.c_uint64),
     ]
 
     def as_dict(self):
@@ -150,6 +155,8 @@ def _load() -> ctypes.CDLL:
         "mapa_autotune": ([vp, i32, i32, vp, i32p], ctypes.c_int),
         "mapa_stats_reset": ([vp], ctypes.c_int),
         "mapa_ctx_set_timing": ([vp, ctypes.c_int], ctypes.c_int),
+        "mapa_ctx_set_work_budget": ([vp, u64], ctypes.c_int),
+        "mapa_measure_int_peak": ([vp, i32, ctypes.POINTER(ctypes.c_double)], ctypes.c_int),
         "mapa_serve_open": ([vp, i32, i32, u32, ctypes.POINTER(vp)], ctypes.c_int),
         "mapa_serve_submit": ([vp, vp, i32], ctypes.c_int),
         "mapa_serve_poll": ([vp, vp, i32, ctypes.POINTER(ctypes.c_int32), i32], ctypes.c_int),
@@ -178,7 +185,7 @@ SYMBOLS = (
     "mapa_occupancy_get", "mapa_pattern_analyze", "mapa_version", "mapa_stats_get", "mapa_stats_reset",
     "mapa_ctx_set_timing", "mapa_allocate_batch_noalloc", "mapa_serve_open", "mapa_serve_submit",
     "mapa_serve_poll", "mapa_serve_drain", "mapa_serve_counters", "mapa_serve_close", "mapa_autotune",
-    "mapa_effbw_predict", "mapa_simulate",
+    "mapa_effbw_predict", "mapa_simulate", "mapa_ctx_set_work_budget", "mapa_measure_int_peak",
 )
 
 
@@ -311,6 +318,16 @@ def mapa_stats_reset(ctx) -> None:
 
 def mapa_ctx_set_timing(ctx, on: bool) -> None:
     _check(ctx, lib.mapa_ctx_set_timing(ctx, 1 if on else 0))
+
+
+def mapa_measure_int_peak(ctx, kind: int) -> float:
+    out = ctypes.c_double()
+    _check(ctx, lib.mapa_measure_int_peak(ctx, int(kind), ctypes.byref(out)))
+    return out.value
+
+
+def mapa_ctx_set_work_budget(ctx, max_partials: int) -> None:
+    _check(ctx, lib.mapa_ctx_set_work_budget(ctx, int(max_partials)))
 
 
 MAPA_SERVE_REJECT = 1
@@ -489,3 +506,6 @@ class Context:
 
     def set_timing(self, on: bool):
         mapa_ctx_set_timing(self.h, on)
+
+    def set_work_budget(self, max_partials: int):
+        mapa_ctx_set_work_budget(self.h, max_partials)

@@ -366,6 +366,35 @@ def _busy_masks(rng: Rng, n: int, counts: np.ndarray) -> np.ndarray:
     return busy.astype(np.uint32)
 
 
+def boards_snapshots(rng: Rng, count: int, boards: int = 32, max_jobs: int = 7, strays: int = 8) -> np.ndarray:
+    """Busy masks of the boards machine as a served run of 31-32-accelerator
+    jobs leaves it: J ~ U{0..max_jobs} jobs, each holding a run of 4
+    consecutive boards (32 accelerators; a tree-31 job, drawn with
+    probability 1/2, leaves one of them free) at a uniform board offset (runs
+    that overlap merge), plus U{0..strays} stray busy accelerators.  Returns
+    [count, 8] uint32 masks."""
+    n = 8 * boards
+    jobs = rng.integers(0, max_jobs, count)
+    first = rng.integers(0, boards - 1, count * max_jobs).reshape(count, max_jobs)
+    tree = rng.uniform(count * max_jobs).reshape(count, max_jobs) < 0.5
+    drop = rng.integers(0, 31, count * max_jobs).reshape(count, max_jobs)
+    nstray = rng.integers(0, strays, count)
+    stray = rng.integers(0, n - 1, count * max(strays, 1)).reshape(count, max(strays, 1))
+    verts = (8 * first[:, :, None] + np.arange(32)[None, None, :]) % n  # [count, jobs, 32]
+    keep = np.arange(max_jobs)[None, :, None] < jobs[:, None, None]
+    keep = keep & ~(tree[:, :, None] & (np.arange(32)[None, None, :] == drop[:, :, None]))
+    busy = np.zeros((count, n), bool)
+    rows = np.broadcast_to(np.arange(count)[:, None, None], verts.shape)
+    busy[rows[keep], verts[keep]] = True
+    srows = np.broadcast_to(np.arange(count)[:, None], stray.shape)
+    sk = np.arange(stray.shape[1])[None, :] < nstray[:, None]
+    busy[srows[sk], stray[sk]] = True
+    out = np.zeros((count, BUSY_WORDS), np.uint64)
+    for v in range(n):
+        out[:, v >> 5] |= busy[:, v].astype(np.uint64) << np.uint64(v & 31)
+    return out.astype(np.uint32)
+
+
 def _mix_patterns(rng: Rng, count: int, kmax_rt: int, clique_max: int):
     """Pattern mix shared by the batched and served workloads."""
     kinds = rng.integers(0, 2, count)
@@ -406,7 +435,8 @@ def workload(name: str, num_requests: int | None = None, seed: int | None = None
     dragonfly128: 16 groups x K8 plus one global link per group pair, request
                   mix of torus64, occupancy kept on the device (served).
     boards256:    32 boards x hybrid cube-mesh with a 4-uplink ring of boards,
-                  ring-32 / tree-31 / clique-8, streamed.
+                  ring-32 / tree-31 / clique-8, 10^6 requests, each with the
+                  occupancy a served run leaves (boards_snapshots).
     """
     if name not in WORKLOADS:
         raise ValueError(f"unknown workload {name!r}; one of {WORKLOADS}")
@@ -447,8 +477,9 @@ def workload(name: str, num_requests: int | None = None, seed: int | None = None
         r = 1_000_000 if num_requests is None else num_requests
         pats = [pattern("ring", 32), pattern("tree", 31), pattern("clique", 8)]
         index = rrng.integers(0, 2, r).astype(np.int32)
-        busy = np.zeros((r, BUSY_WORDS), np.uint32)
-        desc = "256-vertex boards (32 x hybrid cube-mesh, 4-uplink ring of boards), streamed"
+        busy = boards_snapshots(Rng(seed, 3), r)
+        desc = ("256-vertex boards (32 x hybrid cube-mesh, 4-uplink ring of boards), ring-32/tree-31/clique-8, "
+                "served-occupancy snapshots (0-7 jobs of 4 consecutive boards, 0-8 stray busy)")
     ones = np.ones(r, np.int32)
     reqs = Requests(pats, index, ones.copy(), ones.copy(), busy)
     return Workload(name, topo, reqs, desc)

@@ -98,3 +98,64 @@ def test_mismatched_pattern_id_is_invalid(env):
     assert other.any() and (got["status"][other] == M.MAPA_E_INVALID).all()
     want = ctx.allocate_batch(tid, reqs[~other])
     assert np.array_equal(got[~other], want)
+
+
+def _noalloc(torch, M, ctx, tid, pid, sel):
+    dreq = torch.from_numpy(sel.view(np.uint8).copy()).cuda()
+    dout = torch.empty(len(sel) * M.RESULT_DTYPE.itemsize, dtype=torch.uint8, device="cuda")
+    dout.fill_(0xA5)
+    torch.cuda.synchronize()
+    M.mapa_allocate_batch_noalloc(ctx.h, tid, pid, len(sel), dreq.data_ptr(), dout.data_ptr())
+    torch.cuda.synchronize()
+    return dout.cpu().numpy().view(M.RESULT_DTYPE)
+
+
+# Per-request branches of the allocation-free kernel, each against the batched
+# entry point on the same requests: bounded mode, a match budget small enough
+# that most requests exceed it, signed weights, and an alpha that takes the
+# int32 score out of range.
+@pytest.mark.parametrize("case", ["bounded", "budget", "signed", "range"])
+def test_request_branches_match_batched(env, case):
+    torch, M, ctx = env
+    wl = W.workload("regular32", num_requests=512)
+    tid, pids, reqs = _by_pattern(ctx, wl)
+    sel = reqs[reqs["pattern_id"] == pids[0]].copy()
+    if case == "bounded":
+        sel["mode"] = M.MAPA_MODE_BOUNDED
+    elif case == "budget":
+        sel["max_embeddings"] = 40
+    elif case == "signed":
+        sel["alpha"] = -1
+        sel["beta"] = 2
+    else:
+        sel["alpha"][::2] = 1 << 20
+    want = ctx.allocate_batch(tid, sel)
+    statuses = set(int(s) for s in want["status"])
+    if case == "budget":
+        assert M.MAPA_E_BUDGET in statuses and M.MAPA_OK in statuses
+    if case == "range":
+        assert M.MAPA_E_RANGE in statuses and M.MAPA_OK in statuses
+    for call in range(2):
+        got = _noalloc(torch, M, ctx, tid, pids[0], sel)
+        assert np.array_equal(got, want), f"{case} call {call}"
+
+
+def test_refused_request_kinds_are_invalid(env):
+    """Bandwidth-sensitive requests, and bounded ones carrying a match budget,
+    are refused per request (MAPA_E_INVALID); the rest of the call is decided
+    as the batched entry point decides it."""
+    torch, M, ctx = env
+    wl = W.workload("regular32", num_requests=256)
+    tid, pids, reqs = _by_pattern(ctx, wl)
+    sel = reqs[reqs["pattern_id"] == pids[1]].copy()
+    refused = np.zeros(len(sel), bool)
+    refused[0::3] = True
+    refused[1::5] = True
+    sel["flags"][0::3] = M.MAPA_POLICY_BW_SENSITIVE
+    sel["mode"][1::5] = M.MAPA_MODE_BOUNDED
+    sel["max_embeddings"][1::5] = 1000
+    got = _noalloc(torch, M, ctx, tid, pids[1], sel)
+    assert (got["status"][refused] == M.MAPA_E_INVALID).all()
+    assert (got["count"][refused] == 0).all()
+    want = ctx.allocate_batch(tid, sel[~refused])
+    assert np.array_equal(got[~refused], want)
