@@ -9,10 +9,9 @@ starts; the L2 is flushed between timed steps (a 256 MiB write).
 
 Default workload: the 256-vertex boards machine (32 boards of 8, ring-32 /
 tree-31 / clique-8), 3000 requests of its 10^6-request stream per step, each
-with the occupancy a served run leaves, in bounded mode with the anytime
-fallback under a work budget of 2^20 partial matches per request and a
-16 GiB frontier cap per pattern group (64 GiB for the four concurrent
-groups).  The line also carries the 10^4-request 32-vertex workload
+with the occupancy a served run leaves, with the anytime fallback under a
+work budget of 2^20 partial matches per request and a 16 GiB frontier cap
+per pattern group (64 GiB for the four concurrent groups).  The line also carries the 10^4-request 32-vertex workload
 (`config2`), decided exhaustively.
 
 Prints one JSON line (rank 0).  `--impl reference` times the CPU oracle on
@@ -61,6 +60,7 @@ def _args():
     ap.add_argument("--served-requests", type=int, default=3000, help="arrivals in the served comparison")
     ap.add_argument("--served-rate", type=float, default=1e4, help="Poisson rate of the served comparison")
     ap.add_argument("--served-kmax", type=int, default=8)
+    ap.add_argument("--no-served-sweep", action="store_true", help="skip the rate sweep of the served loop (kmax 16)")
     ap.add_argument("--sim-jobs", type=int, default=0,
                     help="jobs of the simulator leg (Sec. 6 job file; 0 = skip)")
     ap.add_argument("--no-autotune", action="store_true",
@@ -231,7 +231,10 @@ def workload_settings(name: str, a) -> dict:
     req = a.requests if a.requests else (3000 if big else None)
     return {
         "requests": req,
-        "mode": 1 if big else 0,  # MAPA_MODE_BOUNDED / MAPA_MODE_EXHAUSTIVE
+        # exhaustive: on this stream the bounded mode's degree term (a scan of
+        # the free set per partial) costs 7x more than it prunes (2.85 s
+        # against 0.40 s per 3000-request step, the same outcomes)
+        "mode": 0,
         "flags": 2 if big else 0,  # MAPA_POLICY_ANYTIME
         "work_budget": a.work_budget if a.work_budget is not None else ((1 << 20) if big else 0),
         "frontier_cap": int((a.frontier_cap_gib if a.frontier_cap_gib else (16 if big else 4)) * (1 << 30)),
@@ -240,9 +243,9 @@ def workload_settings(name: str, a) -> dict:
 
 def _oracle_sample(wl, budget_s: float, threads: int, start: int = 0, max_nodes: int = 0):
     """Runs the oracle over consecutive requests until budget_s elapses.
-    Returns (matches scored once per distinct subgraph, requests, seconds):
-    a request stopped at max_nodes search nodes still counts the matches it
-    scored (maps / |Aut(P)|)."""
+    Returns (matches scored once per distinct subgraph, requests, decisions,
+    seconds): a request stopped at max_nodes search nodes still counts the
+    matches it scored (maps / |Aut(P)|) but is not a decision."""
     from concurrent.futures import ThreadPoolExecutor
 
     from oracle import oracle as O
@@ -257,20 +260,24 @@ def _oracle_sample(wl, budget_s: float, threads: int, start: int = 0, max_nodes:
         busy = W.busy_to_bool(reqs.busy[i], wl.topology.n)
         d = inst.decide(busy, p.k, p.a, p.b, int(reqs.alpha[i]), int(reqs.beta[i]), max_nodes=max_nodes)
         if d.status == O.STATUS_OK:
-            return float(d.classes)
-        return float(d.maps) / auts[reqs.pattern_index[i]] if d.status == O.STATUS_BUDGET else 0.0
+            return float(d.classes), 1
+        if d.status == O.STATUS_NO_MATCH:
+            return 0.0, 1
+        return (float(d.maps) / auts[reqs.pattern_index[i]] if d.status == O.STATUS_BUDGET else 0.0), 0
 
-    done, emb = 0, 0.0
+    done, emb, decided = 0, 0.0, 0
     t0 = time.perf_counter()
     with ThreadPoolExecutor(threads) as ex:
         i = start
         while time.perf_counter() - t0 < budget_s and i < len(reqs):
             chunk = list(range(i, min(i + threads, len(reqs))))
-            emb += sum(ex.map(one, chunk))
+            for e, dcd in ex.map(one, chunk):
+                emb += e
+                decided += dcd
             done += len(chunk)
             i += len(chunk)
     dt = time.perf_counter() - t0
-    return emb, done, dt
+    return emb, done, decided, dt
 
 
 def _oracle_node_cap(settings) -> int:
@@ -310,34 +317,54 @@ def combine_over_ranks(dist, device, total_ms: float, e2e_s: float, emb_step: in
     return float(t[0].item()), float(t[1].item()), float(e[0].item())
 
 
-def served_measure(M, W, rate: float, count: int, max_batch: int, kmax: int = 8, seed: int = 4):
+def served_measure(M, W, rate: float, count: int, max_batch: int, kmax: int = 8, seed: int = 4, mode: int = 0,
+                   flags: int = 0, budget: int = 0):
     """Drives the served loop with a Poisson trace on the 128-vertex dragonfly;
     returns decisions/s over the run and p50/p99 arrival-to-decision latency."""
     import numpy as np
 
     tr = W.served_trace(count, rate=rate, kmax_rt=kmax, seed=seed)
     with M.Context(0) as ctx:
+        ctx.set_work_budget(budget)
         tid = ctx.topology_load(tr.topology)
         pids = np.asarray([ctx.pattern_load(p) for p in tr.patterns], np.int32)
-        ev = M.make_events(pids[tr.pattern_index], tr.at_ns, tr.lifetime_ns)
+        ev = M.make_events(pids[tr.pattern_index], tr.at_ns, tr.lifetime_ns, mode=mode, flags=flags)
         srv = M.mapa_serve_open(ctx.h, tid, max_batch)
         try:
             M.mapa_serve_submit(srv, ev)
-            M.mapa_serve_drain(srv, timeout_ms=120_000)
+            M.mapa_serve_drain(srv, timeout_ms=300_000)
             out = M.mapa_serve_poll(srv, max_events=count + 16)
             counters = M.mapa_serve_counters(srv)
         finally:
             M.mapa_serve_close(srv)
     lat = (out["done_ns"] - out["arrive_ns"]) / 1e6
     span = (out["done_ns"].max() - out["arrive_ns"].min()) / 1e9
-    ok = out["result"]["status"] == 0
+    st = out["result"]["status"]
     return {
-        "rate_per_s": rate, "requests": int(count), "max_batch": int(max_batch),
+        "rate_per_s": rate, "requests": int(count), "max_batch": int(max_batch), "kmax": kmax,
         "decisions_per_s": float(len(out) / span), "p50_ms": float(np.percentile(lat, 50)),
         "p99_ms": float(np.percentile(lat, 99)), "rounds": counters["rounds"], "conflicts_redone": counters["conflicts"],
-        "placed": int(ok.sum()), "matches_scored": int(out["result"]["count"].sum()),
+        "placed": int(((st == 0) | (st == 2)).sum()), "inexact": int((st == 2).sum()), "budget": int((st == -5).sum()),
+        "matches_scored": int(out["result"]["count"].sum()),
         "trace_s": float((tr.at_ns[-1] - tr.at_ns[0]) / 1e9), "workload": tr.description,
+        "mode": "bounded" if mode else "exhaustive", "anytime": bool(flags & 2), "work_budget_partials": budget,
     }
+
+
+def served_sweep(M, W, kmax: int = 16, rates=(1e3, 1e4, 1e5, 1e6), budget: int = 1 << 16):
+    """Config 4's sweep: Poisson arrivals at each rate on the dragonfly, pattern
+    sizes 2..kmax, decided by the served loop in batched rounds (max_batch
+    4096) and one request per round (max_batch 1, the plain per-request
+    form), with the anytime fallback under a work budget of 2^16 partial
+    matches (so an oversized request cannot stall the queue)."""
+    out = []
+    for rate in rates:
+        count = int(min(3000, max(1000, rate * 1.0)))
+        row = {"rate_per_s": rate}
+        for mb, key in ((4096, "batched"), (1, "plain")):
+            row[key] = served_measure(M, W, rate, count, mb, kmax=kmax, mode=0, flags=2, budget=budget)
+        out.append(row)
+    return out
 
 
 def simulator_measure(M, W, jobs_count: int, seed: int = 6):
@@ -375,22 +402,16 @@ def simulator_measure(M, W, jobs_count: int, seed: int = 6):
 
 
 def run_served_sweep(a):
-    """Served loop: batched rounds vs one request per round over a rate sweep."""
+    """Served loop only: the rate sweep (batched rounds vs one request per
+    round), one JSON line per rate."""
     import __graft_entry__
 
     __graft_entry__.build()
     from paper_2110_03214_gb300 import mapa as M
     from paper_2110_03214_gb300 import workloads as W
 
-    for rate in (1e3, 1e4, 1e5, 1e6):
-        count = int(min(20000, max(2000, rate * 0.5)))
-        for mb in (4096, 1):
-            if mb == 1 and rate > 1e4:
-                count_plain = 4000
-            else:
-                count_plain = count
-            r = served_measure(M, W, rate, count if mb > 1 else count_plain, mb, kmax=a.served_kmax)
-            print(json.dumps(r), flush=True)
+    for row in served_sweep(M, W, kmax=16):
+        print(json.dumps(row), flush=True)
 
 
 def run_reference(a):
@@ -409,26 +430,28 @@ def run_reference(a):
     per_step = max(0.5, min(20.0, 120.0 / max(1, a.steps + a.warmup)))
     for _ in range(a.warmup):
         _oracle_sample(wl, per_step / 4, threads, max_nodes=cap)
-    emb_total, req_total, t_total = 0.0, 0, 0.0
+    emb_total, req_total, dec_total, t_total = 0.0, 0, 0, 0.0
     start = 0
     for _ in range(a.steps):
-        emb, done, dt = _oracle_sample(wl, per_step, threads, start, max_nodes=cap)
+        emb, done, decided, dt = _oracle_sample(wl, per_step, threads, start, max_nodes=cap)
         start = (start + done) % len(wl.requests)
         emb_total += emb
         req_total += done
+        dec_total += decided
         t_total += dt
-    value = emb_total / t_total
+    unit = line_unit(a.workload)
+    value = (dec_total if unit == "decisions/s" else emb_total) / t_total
     sample = (f"{req_total} requests of {wl.name} ({len(wl.requests)} in the batch), {per_step:.1f} s per step"
               + (f", at most {cap} search nodes per request" if cap else ""))
     line = {
-        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": a.gpus, "steps": a.steps,
+        "impl": "reference", "metric": METRIC, "value": value, "unit": unit, "n_gpus": a.gpus, "steps": a.steps,
         "warmup": a.warmup, "ms_per_step": 1000 * t_total / a.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "int32", "data": "synthetic",
-        "decisions_per_s": req_total / t_total,
+        "decisions_per_s": dec_total / t_total, "embeddings_per_s": emb_total / t_total,
         "config": {"workload": f"{wl.name}: {wl.description}", "requests_per_step": req_total // a.steps,
                    "l2": "host run"},
-        "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle", "sample": sample},
-        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+        "cpu_baseline": {"value": value, "unit": unit, "cores": threads, "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": unit, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
 
@@ -553,15 +576,16 @@ def measure_batch(M, W, torch, a, name, rank, world, dist, local, plain_requests
     ctx.close()
     statuses = {int(k): int(v) for k, v in zip(*np.unique(ref["status"], return_counts=True))}
     decided = sum(v for k, v in statuses.items() if k >= 0)
-    return {
+    unit = line_unit(name)
+    out = {
         "wl": wl, "nreq": nreq, "cfg": cfg, "ref": ref, "times": times, "total_ms": total_ms, "clocks": clk,
         "stats": st, "stats_roof": st_roof, "roof_steps": roof_steps, "roof_ms": t_roof, "tail_depths": tail_depths,
         "emb_step": emb_step, "emb_all": emb_all, "e2e_s": e2e_s,
-        "value": emb_all * a.steps / (total_ms / 1000.0),
+        "embeddings_per_s": emb_all * a.steps / (total_ms / 1000.0),
         "decisions_per_s": decided * world * a.steps / (total_ms / 1000.0),
         "requests_per_s": nreq * world * a.steps / (total_ms / 1000.0),
         "statuses": {M_STATUS.get(k, str(k)): v for k, v in statuses.items()},
-        "e2e": {"value": emb_all * a.steps / e2e_s, "unit": UNIT,
+        "e2e": {"embeddings_per_s": emb_all * a.steps / e2e_s,
                 "decisions_per_s": decided * world * a.steps / e2e_s,
                 "h2d_bytes_per_step": nreq * M.REQUEST_DTYPE.itemsize,
                 "d2h_bytes_per_step": nreq * M.RESULT_DTYPE.itemsize},
@@ -570,6 +594,21 @@ def measure_batch(M, W, torch, a, name, rank, world, dist, local, plain_requests
                   "p99_ms": 1000 * float(np.percentile(plain_lat, 99)) if plain_lat else None,
                   "requests": len(plain_lat)},
     }
+    key = "decisions_per_s" if unit == "decisions/s" else "embeddings_per_s"
+    out["value"] = out[key]
+    out["unit"] = unit
+    out["e2e"]["value"] = out["e2e"][key]
+    out["e2e"]["unit"] = unit
+    return out
+
+
+def line_unit(name: str) -> str:
+    """Unit of a workload's headline value: matches scored per second, or
+    decisions per second on the boards stream, where no request finishes an
+    enumeration within its work budget (its decisions are exact no-fits,
+    budget-capped inexact matches or budget ends) and the scored-match rate
+    says nothing."""
+    return "decisions/s" if name == "boards256" else UNIT
 
 
 M_STATUS = {0: "ok", 1: "no_fit", 2: "inexact", -5: "budget", -2: "range", -1: "invalid"}
@@ -649,10 +688,11 @@ def run_ours(a):
     total_ms = r["total_ms"]
     if rank == 0:
         line = {
-            "metric": METRIC, "value": r["value"], "unit": UNIT, "n_gpus": world, "steps": a.steps,
+            "metric": METRIC, "value": r["value"], "unit": r["unit"], "n_gpus": world, "steps": a.steps,
             "warmup": a.warmup, "ms_per_step": total_ms / a.steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "int32", "data": "synthetic (seeded SplitMix64 generator)",
-            "decisions_per_s": r["decisions_per_s"], "requests_per_s": r["requests_per_s"],
+            "decisions_per_s": r["decisions_per_s"], "embeddings_per_s": r["embeddings_per_s"],
+            "requests_per_s": r["requests_per_s"],
             "outcomes_per_step": r["statuses"],
             "latency_ms": {"batched_p50": statistics.median(r["times"]), "batched_p99": max(r["times"]),
                            "plain_p50": r["plain"]["p50_ms"], "plain_p99": r["plain"]["p99_ms"]},
@@ -675,7 +715,7 @@ def run_ours(a):
             c2 = measure_batch(M, W, torch, a, "regular32", 0, 1, dist, local, a.plain_requests)
             line["config2"] = {
                 "workload": f"{c2['wl'].name}: {c2['wl'].description}", "requests_per_step": c2["nreq"],
-                "value": c2["value"], "unit": UNIT, "ms_per_step": c2["total_ms"] / a.steps,
+                "value": c2["value"], "unit": c2["unit"], "ms_per_step": c2["total_ms"] / a.steps,
                 "decisions_per_s": c2["decisions_per_s"], "e2e": c2["e2e"], "plain": c2["plain"],
                 "roofline": roofline(c2, peaks, peak_src, int_peak), "clocks": c2["clocks"],
                 "gpu_launches": c2["stats"]["kernel_launches"], "embeddings_per_step": c2["emb_step"],
@@ -686,13 +726,17 @@ def run_ours(a):
             line["served"] = {"batched": sb, "plain": sp}
             line["latency_ms"].update({"served_batched_p50": sb["p50_ms"], "served_batched_p99": sb["p99_ms"],
                                        "served_plain_p50": sp["p50_ms"], "served_plain_p99": sp["p99_ms"]})
+        if world == 1 and not a.no_served_sweep:
+            line["served_sweep"] = served_sweep(M, W)
         if world == 1 and a.sim_jobs > 0:
             line["simulator"] = simulator_measure(M, W, a.sim_jobs)
         if world == 1 and not a.no_cpu_baseline:
             threads = os.cpu_count() or 1
             cap = _oracle_node_cap(cfg)
-            emb, done, dt = _oracle_sample(wl, a.cpu_seconds, threads, max_nodes=cap)
-            line["cpu_baseline"] = {"value": emb / dt, "unit": UNIT, "cores": threads, "kind": "oracle",
+            emb, done, decided, dt = _oracle_sample(wl, a.cpu_seconds, threads, max_nodes=cap)
+            line["cpu_baseline"] = {"value": (decided if r["unit"] == "decisions/s" else emb) / dt, "unit": r["unit"],
+                                    "cores": threads, "kind": "oracle", "embeddings_per_s": emb / dt,
+                                    "decisions_per_s": decided / dt,
                                     "sample": f"first {done} of {nreq} requests of {wl.name}, {dt:.1f} s"
                                               + (f", at most {cap} search nodes per request" if cap else "")}
         print(json.dumps(line), flush=True)

@@ -263,6 +263,7 @@ Engine *engine_create(int device, uint64_t frontier_cap, std::string *err) {
     if (const char *ov = std::getenv("MAPA_TAIL_DEPTH")) en->tail_override = std::atoi(ov);
     if (const char *ov = std::getenv("MAPA_TAIL_BLOCKS_PER_SM")) en->tail_blocks_per_sm = std::atoi(ov);
     if (const char *ov = std::getenv("MAPA_GRAPHS")) en->use_graphs = std::atoi(ov) != 0;
+    if (const char *ov = std::getenv("MAPA_TAIL_SORT")) en->tail_sorted = std::atoi(ov) != 0;
     if (const char *ov = std::getenv("MAPA_DIVE_STEPS")) en->dive_steps = std::max(0, std::min(std::atoi(ov), 1 << 20));
     if (const char *ov = std::getenv("MAPA_BOUND_DEGREE_MIN_M")) en->degree_min_m = std::max(0, std::atoi(ov));
     if (cudaStreamCreateWithFlags(&en->own_stream, cudaStreamNonBlocking) != cudaSuccess ||

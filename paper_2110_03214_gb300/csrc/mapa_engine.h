@@ -69,6 +69,7 @@ struct Engine {
     int dive_steps = 32;         // bounded mode: node expansions of a request's seed dive
     int degree_min_m = 6;        // bounded mode: degree term only where >= this many pattern vertices remain
     uint64_t work_budget = 0;    // stored partial matches a request may produce (0 = no limit)
+    bool tail_sorted = false;    // short fused tail: parents of a tile ordered by estimated subtree size (MAPA_TAIL_SORT=1)
     std::map<std::pair<int32_t, int32_t>, int> tail_table;  // (topology, pattern) -> tuned depth
     // Captured launch sequences of independent batches, keyed by batch shape.
     bool use_graphs = true;

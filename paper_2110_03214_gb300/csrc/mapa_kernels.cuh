@@ -1368,42 +1368,50 @@ __device__ __forceinline__ int32_t delta_c(const SmemTopo &s, int v, const uint3
 
 // Walks the last T (1 or 2) levels below parent p; leaf(score) for every
 // complete match.
-template <int W, int CT, int T, typename Leaf>
-__device__ __forceinline__ void walk_short_tail(const SmemTopo &s, const LevelView &in, uint32_t p, const TailArgs &ta,
-                                                int32_t al, int32_t be, Leaf &&leaf, uint32_t &nodes) {
-    const int32_t S = in.S[p];
+// First level of the explicit tail walk of parent p: its score S, free set
+// R, the masks of both tail levels (A, B, lb for pattern vertex ell; A2, B2,
+// lb2 for ell + 1 when T = 2) and the candidates c1 of the first tail level,
+// filtered when T = 2 by necessary conditions for a node to have a leaf.
+template <int W, int T>
+struct ShortTailState {
+    int32_t S;
     uint32_t R[W], A[W], B[W], c1[W];
     int lb;
-    level_masks<W>(in, p, ta.back_old[0], ta.lo_old[0], s.adj, A, B, lb);
+    uint32_t A2[W], B2[W];
+    int lb2;
+    bool nb, nl;
+    int nodes;  // first-level candidates before the filter (telemetry)
+};
+
+template <int W, int T>
+__device__ __forceinline__ void short_tail_first(const SmemTopo &s, const LevelView &in, uint32_t p,
+                                                 const TailArgs &ta, ShortTailState<W, T> &st) {
+    st.S = in.S[p];
+    level_masks<W>(in, p, ta.back_old[0], ta.lo_old[0], s.adj, st.A, st.B, st.lb);
 #pragma unroll
     for (int w = 0; w < W; ++w) {
-        R[w] = in.R[col_at(in, w, p)];
-        c1[w] = R[w] & A[w];
+        st.R[w] = in.R[col_at(in, w, p)];
+        st.c1[w] = st.R[w] & st.A[w];
     }
-    and_above<W>(c1, lb);
-    if constexpr (T == 1) {
-        int v;
-        while ((v = pop_lowest<W>(c1)) >= 0) leaf(S + delta_c<W, CT>(s, v, B, R, al, be));
-    } else {
-        uint32_t A2[W], B2[W];
-        int lb2;
-        level_masks<W>(in, p, ta.back_old[1], ta.lo_old[1], s.adj, A2, B2, lb2);
-        const bool nb = (ta.back_tail[1] & 1u) != 0u;
-        const bool nl = (ta.lo_tail[1] & 1u) != 0u;
-        nodes += popc_mask<W>(c1);
-        if (nb || nl) {
+    and_above<W>(st.c1, st.lb);
+    st.nodes = popc_mask<W>(st.c1);
+    if constexpr (T == 2) {
+        level_masks<W>(in, p, ta.back_old[1], ta.lo_old[1], s.adj, st.A2, st.B2, st.lb2);
+        st.nb = (ta.back_tail[1] & 1u) != 0u;
+        st.nl = (ta.lo_tail[1] & 1u) != 0u;
+        if (st.nb || st.nl) {
             // Necessary conditions for a node to have a leaf, given the free
             // last-level candidates x (the node itself aside): if the last
             // vertex must come after the node's, the node lies below the
             // highest x; if it is adjacent to the node's, the node neighbours
             // some x (on ring patterns this leaves exactly the nodes with
-            // leaves).  The per-node test below stays exact.
+            // leaves).  The per-node test of the walk stays exact.
             uint32_t x[W];
 #pragma unroll
-            for (int w = 0; w < W; ++w) x[w] = R[w] & A2[w];
-            and_above<W>(x, lb2);
-            if (nl) and_below<W>(c1, highest_bit<W>(x));
-            if (nb) {
+            for (int w = 0; w < W; ++w) x[w] = st.R[w] & st.A2[w];
+            and_above<W>(x, st.lb2);
+            if (st.nl) and_below<W>(st.c1, highest_bit<W>(x));
+            if (st.nb) {
                 uint32_t N[W];
 #pragma unroll
                 for (int w = 0; w < W; ++w) N[w] = 0u;
@@ -1413,24 +1421,37 @@ __device__ __forceinline__ void walk_short_tail(const SmemTopo &s, const LevelVi
                     for (int w = 0; w < W; ++w) N[w] |= s.adj[u * W + w];
                 }
 #pragma unroll
-                for (int w = 0; w < W; ++w) c1[w] &= N[w];
+                for (int w = 0; w < W; ++w) st.c1[w] &= N[w];
             }
         }
+    }
+}
+
+template <int W, int CT, int T, typename Leaf>
+__device__ __forceinline__ void walk_short_tail(const SmemTopo &s, const LevelView &in, uint32_t p, const TailArgs &ta,
+                                                int32_t al, int32_t be, Leaf &&leaf, uint32_t &nodes) {
+    ShortTailState<W, T> st;
+    short_tail_first<W, T>(s, in, p, ta, st);
+    if constexpr (T == 2) nodes += st.nodes;  // every first-level candidate, filtered or not
+    if constexpr (T == 1) {
+        int v;
+        while ((v = pop_lowest<W>(st.c1)) >= 0) leaf(st.S + delta_c<W, CT>(s, v, st.B, st.R, al, be));
+    } else {
         int v1;
-        while ((v1 = pop_lowest<W>(c1)) >= 0) {
+        while ((v1 = pop_lowest<W>(st.c1)) >= 0) {
             uint32_t R1[W], c2[W];
 #pragma unroll
-            for (int w = 0; w < W; ++w) R1[w] = R[w];
+            for (int w = 0; w < W; ++w) R1[w] = st.R[w];
             clear_bit<W>(R1, v1);
 #pragma unroll
-            for (int w = 0; w < W; ++w) c2[w] = R1[w] & A2[w] & (nb ? s.adj[v1 * W + w] : ~0u);
-            and_above<W>(c2, nl ? max(lb2, v1) : lb2);
+            for (int w = 0; w < W; ++w) c2[w] = R1[w] & st.A2[w] & (st.nb ? s.adj[v1 * W + w] : ~0u);
+            and_above<W>(c2, st.nl ? max(st.lb2, v1) : st.lb2);
             if (!popc_mask<W>(c2)) continue;  // no leaf below: its score is not needed
-            const int32_t s1 = S + delta_c<W, CT>(s, v1, B, R, al, be);
+            const int32_t s1 = st.S + delta_c<W, CT>(s, v1, st.B, st.R, al, be);
             uint32_t B2n[W];
 #pragma unroll
-            for (int w = 0; w < W; ++w) B2n[w] = B2[w];
-            if (nb) set_bit<W>(B2n, v1);
+            for (int w = 0; w < W; ++w) B2n[w] = st.B2[w];
+            if (st.nb) set_bit<W>(B2n, v1);
             int v2;
             while ((v2 = pop_lowest<W>(c2)) >= 0) leaf(s1 + delta_c<W, CT>(s, v2, B2n, R1, al, be));
         }
@@ -1439,7 +1460,14 @@ __device__ __forceinline__ void walk_short_tail(const SmemTopo &s, const LevelVi
 
 // Sens: the scores are link-count indices of bandwidth-sensitive requests
 // and the argmax is taken over their Eq. 2 ranks lut[score].
-template <int W, int CT, int T, bool Sens>
+// Sorted: the block first estimates each parent's subtree by its filtered
+// first-level candidate count and hands the tile's parents to lanes in
+// decreasing order of it (a counting sort in shared memory), so the 32
+// lanes of a warp walk subtrees of similar size; the argmax keys keep the
+// parents' own indices, so nothing but the order of work changes.
+constexpr int kSortBins = 65;
+
+template <int W, int CT, int T, bool Sens, bool Sorted = false>
 __global__ void __launch_bounds__(kTpb) k_last_short(TopoArgs topo, LevelView in, const unsigned long long *count_in,
                                                      unsigned long long count_host, TailArgs ta, const int32_t *alpha,
                                                      const int32_t *beta, uint64_t *key, unsigned long long *count,
@@ -1447,6 +1475,39 @@ __global__ void __launch_bounds__(kTpb) k_last_short(TopoArgs topo, LevelView in
     const unsigned long long P = count_in ? *count_in : count_host;
     if (static_cast<unsigned long long>(blockIdx.x) * kTile >= P) return;  // tile past the stored parents
     const SmemTopo s = stage_topology<W>(topo, true);
+    __shared__ uint16_t s_order[Sorted ? kTile : 1];
+    __shared__ int s_bin[Sorted ? kSortBins : 1];
+    const uint64_t tile0 = static_cast<uint64_t>(blockIdx.x) * kTile;
+    if constexpr (Sorted) {
+        for (int b = threadIdx.x; b < kSortBins; b += kTpb) s_bin[b] = 0;
+        __syncthreads();
+        int est[kIpt];
+#pragma unroll
+        for (int j = 0; j < kIpt; ++j) {
+            const int idx = threadIdx.x + j * kTpb;
+            est[j] = 0;
+            if (tile0 + idx < P) {
+                ShortTailState<W, T> st;
+                short_tail_first<W, T>(s, in, static_cast<uint32_t>(tile0 + idx), ta, st);
+                est[j] = min(popc_mask<W>(st.c1), kSortBins - 1);
+            }
+            atomicAdd(&s_bin[kSortBins - 1 - est[j]], 1);
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            int acc = 0;
+            for (int b = 0; b < kSortBins; ++b) {
+                const int c = s_bin[b];
+                s_bin[b] = acc;
+                acc += c;
+            }
+        }
+        __syncthreads();
+#pragma unroll
+        for (int j = 0; j < kIpt; ++j)
+            s_order[atomicAdd(&s_bin[kSortBins - 1 - est[j]], 1)] = static_cast<uint16_t>(threadIdx.x + j * kTpb);
+        __syncthreads();
+    }
     __shared__ uint32_t s_r[kWarps];
     __shared__ unsigned long long s_key[kWarps];
     __shared__ unsigned long long s_cnt[kWarps];
@@ -1458,11 +1519,11 @@ __global__ void __launch_bounds__(kTpb) k_last_short(TopoArgs topo, LevelView in
     }
     uint32_t nodes = 0, parents = 0, leaves_total = 0;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const uint64_t wbase = static_cast<uint64_t>(blockIdx.x) * kTile + static_cast<uint64_t>(warp) * 32 * kIpt;
     uint32_t r_cur = kNoReq;
     unsigned long long bkey = 0ull, bcnt = 0ull;
     for (int j = 0; j < kIpt; ++j) {
-        const uint64_t p64 = wbase + j * 32 + lane;
+        const int slot = warp * 32 * kIpt + j * 32 + lane;
+        const uint64_t p64 = tile0 + (Sorted ? s_order[slot] : slot);
         if (p64 >= P) continue;
         const uint32_t p = static_cast<uint32_t>(p64);
         const uint32_t r = in.r[p];

@@ -114,9 +114,12 @@ struct Runner {
         MAPA_CUDA_TRY(cudaFuncSetAttribute(k_expand<W, CT, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, b));
         MAPA_CUDA_TRY(cudaFuncSetAttribute(k_last<W, CT, T, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, b));
         MAPA_CUDA_TRY(cudaFuncSetAttribute(k_last<W, CT, T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, b));
-        if constexpr (T <= 2 && W <= 2)
+        if constexpr (T <= 2 && W <= 2) {
             MAPA_CUDA_TRY(
                 cudaFuncSetAttribute(k_last_short<W, CT, T, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, b));
+            MAPA_CUDA_TRY(cudaFuncSetAttribute(k_last_short<W, CT, T, false, true>,
+                                               cudaFuncAttributeMaxDynamicSharedMemorySize, b));
+        }
         if constexpr (T == 3 && W <= 2)
             MAPA_CUDA_TRY(cudaFuncSetAttribute(k_last_coop3<W, CT>, cudaFuncAttributeMaxDynamicSharedMemorySize, b));
         if constexpr (T == 1)
@@ -203,8 +206,9 @@ struct Runner {
         if constexpr (T <= 2 && W <= 2) {
             if (!g.thr && !launched) {
                 // masks of at most 64 vertices: one tile of parents per block
-                k_last_short<W, CT, T, false><<<sgrid, kTpb, smem_all, st>>>(
-                    targs, in, count_dev, count_host, ta, g.alpha, g.beta, g.key, g.count, e->d_stats, nullptr);
+                auto tail = e->tail_sorted ? k_last_short<W, CT, T, false, true> : k_last_short<W, CT, T, false>;
+                tail<<<sgrid, kTpb, smem_all, st>>>(targs, in, count_dev, count_host, ta, g.alpha, g.beta, g.key,
+                                                    g.count, e->d_stats, nullptr);
                 launched = true;
             }
         }

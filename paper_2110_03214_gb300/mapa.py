@@ -373,7 +373,7 @@ def mapa_serve_close(srv) -> None:
         raise MapaError(rc, "serving loop ended with an error")
 
 
-def make_events(pattern_ids, at_ns, lifetime_ns=0, alpha=1, beta=1, request_ids=None) -> np.ndarray:
+def make_events(pattern_ids, at_ns, lifetime_ns=0, alpha=1, beta=1, request_ids=None, mode=0, flags=0) -> np.ndarray:
     pattern_ids = np.asarray(pattern_ids, np.int32)
     ev = np.zeros(pattern_ids.shape[0], EVENT_DTYPE)
     ev["request_id"] = np.arange(pattern_ids.shape[0]) if request_ids is None else request_ids
@@ -383,6 +383,8 @@ def make_events(pattern_ids, at_ns, lifetime_ns=0, alpha=1, beta=1, request_ids=
     ev["pattern_id"] = pattern_ids
     ev["alpha"] = alpha
     ev["beta"] = beta
+    ev["mode"] = mode
+    ev["flags"] = flags
     return ev
 
 

@@ -73,16 +73,43 @@ def test_config2_every_request(M, ctx):
     assert int(res["count"].sum()) > 10**7
 
 
-def test_config3_torus_subset(M, ctx):
-    wl = W.workload("torus64", num_requests=4000)
-    ks = np.asarray([wl.requests.patterns[i].k for i in wl.requests.pattern_index])
-    busy = np.asarray([sum(bin(int(x)).count("1") for x in row) for row in wl.requests.busy])
-    keep = np.nonzero((ks <= 9) | (busy >= 24))[0][:1500]
-    reqs = wl.requests.subset(keep)
-    rng = W.Rng(3, 5)
-    sample = sorted(set(rng.integers(0, len(reqs) - 1, 200).tolist()))
-    _, compared = _run_and_compare(M, ctx, wl.topology, reqs, idx=sample, max_maps=3_000_000)
-    assert compared >= 150
+def _config3_sample(reqs, n):
+    """Seeded, input-only selection of torus requests for oracle parity: for
+    every pattern of the batch (ring-k, tree-k for k in 2..16, clique-k for k
+    in 2..4), the requests whose busy count is nearest to a few targets,
+    lower for smaller patterns, among those with at least k free vertices
+    (ties: the earlier request)."""
+    busy = np.asarray([sum(bin(int(x)).count("1") for x in row) for row in reqs.busy])
+    free = n - busy
+    sample = []
+    for pi, p in enumerate(reqs.patterns):
+        targets = (38, 30, 20, 10, 4) if p.k <= 8 else ((38, 32, 26, 20) if p.k <= 12 else (38, 34, 31, 29))
+        idx = np.nonzero(reqs.pattern_index == pi)[0]
+        idx = idx[free[idx] >= p.k]
+        chosen = []
+        for tb in targets:
+            for i in idx[np.argsort(np.abs(busy[idx] - tb), kind="stable")]:
+                if int(i) not in chosen:
+                    chosen.append(int(i))
+                    break
+        sample += chosen
+    return sorted(sample)
+
+
+def test_config3_every_pattern_size(M, ctx):
+    """The torus workload's first 10^4 requests (ring/tree k in 2..16,
+    clique k in 2..4, occupancy U[0, 0.6]) decided as one batch; a sample
+    covering every pattern of the batch compared with the oracle (none
+    skipped), every result re-scored from its tuple."""
+    wl = W.workload("torus64", num_requests=10_000)
+    reqs = wl.requests
+    sample = _config3_sample(reqs, wl.topology.n)
+    res, compared = _run_and_compare(M, ctx, wl.topology, reqs, idx=sample, max_maps=0)
+    assert compared == len(sample)
+    names = {reqs.patterns[reqs.pattern_index[i]].name for i in sample if int(res[i]["status"]) == 0}
+    assert {f"tree-{k}" for k in range(2, 17)} <= names and {f"ring-{k}" for k in range(4, 17, 2)} <= names
+    check_result_properties(O.Instance.from_topology(wl.topology), wl.topology.n, reqs, res)
+    assert int(res["count"].sum()) > 10**11
 
 
 def _random_busy_requests(rng, topo_n, patterns, count, lo_frac, hi_frac, alpha=1, beta=1):
