@@ -111,9 +111,10 @@ enum mapa_policy_flags { MAPA_POLICY_BW_SENSITIVE = 1u, MAPA_POLICY_ANYTIME = 2u
 /* flags & MAPA_POLICY_ANYTIME (with alpha, beta >= 0, not with
  * MAPA_POLICY_BW_SENSITIVE, in either mode) changes what a request past the
  * context's work budget (mapa_ctx_set_work_budget) returns: instead of
- * MAPA_E_BUDGET, the best match of the request's seed dive (the bounded
- * mode's, which an anytime request runs in exhaustive mode too without
- * letting it cut anything), with status MAPA_INEXACT, its
+ * MAPA_E_BUDGET, the best match of the request's seed dive (in bounded mode
+ * the dive that seeds its cut-offs; in exhaustive mode a dive run after the
+ * enumeration, for the requests past the budget only), with status
+ * MAPA_INEXACT, its
  * score, AggBW and PreservedBW recomputed from the tuple, count 0.  For such
  * a request the dive runs up to 256 k steps and is guided towards a match
  * rather than a high score: candidates that violate two necessary conditions
@@ -122,7 +123,8 @@ enum mapa_policy_flags { MAPA_POLICY_BW_SENSITIVE = 1u, MAPA_POLICY_ANYTIME = 2u
  * free neighbours as j has later pattern neighbours), the child with the
  * most free neighbours is taken first, at most 1024 steps are spent below
  * one phi(0) before the next is tried, and once a match is found the dive
- * continues best score first.  The fallback depends on the request alone,
+ * continues best score first for at most 1024 more steps.  The fallback
+ * depends on the request alone,
  * so it is the same on every run and in every batch.  It is committed like
  * MAPA_OK (mapa_allocate, sequential batches, the served loop).  With no
  * match from the dive the result is MAPA_E_BUDGET.  A request that finishes
@@ -141,10 +143,19 @@ typedef struct {
 /* One request of a batch (64 bytes, no pointers, so an array of them can live
  * in host or device memory).  busy: vertices unavailable to this request
  * (see the flags of mapa_allocate_batch for how it combines with the
- * device occupancy). */
+ * device occupancy).
+ * root_lo, root_hi: with root_hi > 0, only the matches whose image of
+ * pattern vertex 0 lies in [root_lo, root_hi) are enumerated -- one share
+ * of a request split by the value of phi(0), e.g. across GPUs.  Each match
+ * is counted in exactly one share (the lexicographically smallest map of
+ * its class, the one enumerated, has one phi(0)), so mapa_result_merge of
+ * the shares of a partition of [0, n) gives the unsplit result.  root_hi = 0
+ * (the default) enumerates everything.  The allocation-free call refuses
+ * split requests (MAPA_E_INVALID). */
 typedef struct {
     int32_t pattern_id;
-    int32_t reserved;
+    uint16_t root_lo;
+    uint16_t root_hi;
     mapa_policy policy;
     uint32_t busy[MAPA_MASK_WORDS];
 } mapa_request;
@@ -240,6 +251,17 @@ int mapa_release(mapa_ctx ctx, int32_t topo_id, int64_t job_id);
  * out[i].status), or a negative error for the call as a whole. */
 int mapa_allocate_batch(mapa_ctx ctx, int32_t topo_id, int32_t nreq, const mapa_request *reqs,
                         mapa_result *out, uint32_t flags);
+
+/* Host-only reduction of the shares of one split request (root_lo/root_hi
+ * of mapa_request; no GPU needed): the best share by score, then the
+ * lexicographically smallest tuple (the same compare the enumeration uses
+ * within a share), with count the sum of the shares' counts.  A share with
+ * a negative status makes that status the result (the first in parts
+ * order); otherwise the result is MAPA_INEXACT if any share is, else
+ * MAPA_OK if any share found a match, else MAPA_NO_FIT.  out may alias no
+ * element of parts.  Not in the paper: the exchange step of splitting one
+ * request across GPUs (one result per share, gathered and reduced). */
+int mapa_result_merge(int32_t nparts, const mapa_result *parts, mapa_result *out);
 
 /* ---- serving ------------------------------------------------------------ */
 

@@ -222,6 +222,7 @@ typedef struct {
     int32_t best_phi[OR_MAX_K];
     int aborted;
     uint64_t max_nodes, nodes; /* search-node cap of oracle_decide_capped (0 = none) */
+    int32_t root_lo, root_hi;  /* phi(0) in [root_lo, root_hi) (oracle_decide_rooted) */
 } match_state;
 
 static void visit_match(match_state *s)
@@ -259,6 +260,7 @@ static void extend(match_state *s, int32_t i)
     }
     for (int32_t x = 0; x < s->n; ++x) {
         if (!s->free_v[x] || s->used[x]) continue;
+        if (i == 0 && (x < s->root_lo || x >= s->root_hi)) continue;
         int ok = 1;
         for (int32_t a = 0; a < i && ok; ++a)
             if (s->padj[a][i] && s->wmat[s->phi[a] * s->n + x] <= 0) ok = 0;
@@ -313,6 +315,8 @@ int oracle_decide_capped(int32_t n, const int32_t *wmat, const uint8_t *busy, in
     s->beta = beta;
     s->max_maps = max_maps;
     s->max_nodes = max_nodes;
+    s->root_lo = 0;
+    s->root_hi = n;
     extend(s, 0);
 
     out->maps = s->maps;
@@ -327,6 +331,56 @@ int oracle_decide_capped(int32_t n, const int32_t *wmat, const uint8_t *busy, in
     } else {
         out->status = OR_OK;
         out->classes = s->maps / out->aut;
+        out->score = s->best_score;
+        out->agg = s->best_agg;
+        out->pres = s->best_pres;
+        for (int32_t i = 0; i < k; ++i) out->tuple[i] = (uint8_t)s->best_phi[i];
+    }
+    int32_t st = out->status;
+    free(s);
+    return st;
+}
+
+/* ------------------------------------------------------------------ */
+/* One share of a split request: the matches with phi(0) in [root_lo,    */
+/* root_hi) only.  Same search as oracle_decide (every map, no symmetry  */
+/* breaking); out->maps counts the share's maps, out->classes stays 0    */
+/* (a share need not hold whole automorphism classes).                   */
+
+int oracle_decide_rooted(int32_t n, const int32_t *wmat, const uint8_t *busy, int32_t k, int32_t m,
+                         const int32_t *pa, const int32_t *pb, int64_t alpha, int64_t beta, int32_t root_lo,
+                         int32_t root_hi, oracle_result *out)
+{
+    memset(out, 0, sizeof(*out));
+    out->k = k;
+    uint8_t padj[OR_MAX_K][OR_MAX_K];
+    if (n < 1 || n > OR_MAX_N || build_pattern(k, m, pa, pb, padj) != OR_OK) {
+        out->status = OR_INVALID;
+        return OR_INVALID;
+    }
+    match_state *s = (match_state *)calloc(1, sizeof(match_state));
+    if (!s) {
+        out->status = OR_INVALID;
+        return OR_INVALID;
+    }
+    s->n = n;
+    s->wmat = wmat;
+    for (int32_t v = 0; v < n; ++v) s->free_v[v] = busy[v] ? 0 : 1;
+    s->k = k;
+    s->m = m;
+    s->pa = pa;
+    s->pb = pb;
+    s->padj = padj;
+    s->alpha = alpha;
+    s->beta = beta;
+    s->root_lo = root_lo;
+    s->root_hi = root_hi;
+    extend(s, 0);
+    out->maps = s->maps;
+    if (!s->have_best) {
+        out->status = OR_NO_MATCH;
+    } else {
+        out->status = OR_OK;
         out->score = s->best_score;
         out->agg = s->best_agg;
         out->pres = s->best_pres;

@@ -94,6 +94,9 @@ def load(path: str | None = None):
         lib.oracle_decide_capped.argtypes = lib.oracle_decide.argtypes[:10] + [ctypes.c_uint64,
                                                                                 ctypes.POINTER(_Result)]
         lib.oracle_decide_capped.restype = ctypes.c_int
+        lib.oracle_decide_rooted.argtypes = lib.oracle_decide.argtypes[:9] + [ctypes.c_int32, ctypes.c_int32,
+                                                                               ctypes.POINTER(_Result)]
+        lib.oracle_decide_rooted.restype = ctypes.c_int
         lib.oracle_decide_bounded.argtypes = lib.oracle_decide.argtypes
         lib.oracle_decide_bounded.restype = ctypes.c_int
         lib.oracle_effbw.argtypes = [ctypes.c_int64, ctypes.c_int64, ctypes.c_int64]
@@ -158,6 +161,19 @@ class Instance:
         self.lib.oracle_decide_capped(self.n, self._wp, busy_p, int(k), len(pa_a), pa_p, pb_p, int(alpha), int(beta),
                                       int(max_maps), int(max_nodes), ctypes.byref(res))
         return Decision(res.status, res.score, res.agg, res.pres, res.maps, res.aut, res.classes,
+                        tuple(res.tuple[:k]) if res.status == STATUS_OK else ())
+
+    def decide_rooted(self, busy, k: int, pa, pb, alpha: int, beta: int, root_lo: int, root_hi: int) -> Decision:
+        """One share of a split request: only the maps with phi(0) in
+        [root_lo, root_hi).  ``maps`` counts the share's maps; ``classes``
+        and ``aut`` stay 0 (a share need not hold whole classes)."""
+        busy_a, busy_p = _u8(np.asarray(busy, dtype=bool))
+        pa_a, pa_p = _i32(pa)
+        pb_a, pb_p = _i32(pb)
+        res = _Result()
+        self.lib.oracle_decide_rooted(self.n, self._wp, busy_p, int(k), len(pa_a), pa_p, pb_p, int(alpha), int(beta),
+                                      int(root_lo), int(root_hi), ctypes.byref(res))
+        return Decision(res.status, res.score, res.agg, res.pres, res.maps, 0, 0,
                         tuple(res.tuple[:k]) if res.status == STATUS_OK else ())
 
     def decide_bounded(self, busy, k: int, pa, pb, alpha: int = 1, beta: int = 1, max_nodes: int = 0) -> Decision:

@@ -542,6 +542,46 @@ int mapa_ctx_set_work_budget(mapa_ctx ctx, uint64_t max_partials) {
     return MAPA_OK;
 }
 
+int mapa_result_merge(int32_t nparts, const mapa_result *parts, mapa_result *out) {
+    if (nparts < 1 || !parts || !out) return MAPA_E_INVALID;
+    mapa_result best;
+    memset(&best, 0, sizeof(best));
+    best.k = parts[0].k;
+    bool have = false, inexact = false;
+    uint64_t count = 0;
+    for (int32_t i = 0; i < nparts; ++i) {
+        const mapa_result &p = parts[i];
+        if (p.k != best.k) return MAPA_E_INVALID;  // shares of different requests
+        if (p.status < 0) {
+            memset(out, 0, sizeof(*out));
+            out->status = p.status;
+            out->k = p.k;
+            return MAPA_OK;
+        }
+        count += p.count;
+        if (p.status != MAPA_OK && p.status != MAPA_INEXACT) continue;
+        inexact |= p.status == MAPA_INEXACT;
+        // larger score first, then the lexicographically smaller tuple
+        bool take = !have || p.score > best.score;
+        if (have && p.score == best.score)
+            take = std::lexicographical_compare(p.verts, p.verts + p.k, best.verts, best.verts + best.k);
+        if (take) {
+            best = p;
+            have = true;
+        }
+    }
+    best.status = !have ? MAPA_NO_FIT : (inexact ? MAPA_INEXACT : MAPA_OK);
+    if (!have) {
+        memset(&best, 0, sizeof(best));
+        best.status = MAPA_NO_FIT;
+        best.k = parts[0].k;
+    }
+    best.count = count;
+    best.job_id = 0;
+    *out = best;
+    return MAPA_OK;
+}
+
 int mapa_pattern_analyze(int32_t k, int32_t m, const int32_t *a, const int32_t *b, uint64_t *aut_order,
                          uint32_t *back_masks, uint32_t *lo_masks) {
     if (m < 0 || (m > 0 && (!a || !b))) return MAPA_E_INVALID;

@@ -356,7 +356,7 @@ int plan_layout(Engine *e, int slot, int32_t group_size, int k, int T, int W, bo
     const uint64_t lvl0 = static_cast<uint64_t>(std::max(group_size, 1));
     uint64_t per_entry = 0;
     for (int ell = 1; ell <= lay->L; ++ell) per_entry += entry_bytes(ell, W);
-    const uint64_t scr_x1024 = device_mode ? 32 : 48;  // control bytes per 1024 entries of a level
+    const uint64_t scr_x1024 = device_mode ? 32 : 176;  // control bytes per 1024 entries of a level
     const uint64_t fixed = lvl0 * entry_bytes(0, W) + (lvl0 / 256 + 4) * 48 + 64 * 1024 + 4096 * (lay->L + 2);
     uint64_t E = 0;
     if (lay->L >= 1) {
@@ -380,7 +380,7 @@ int plan_layout(Engine *e, int slot, int32_t group_size, int k, int T, int W, bo
         return at;
     };
     uint64_t off_level[kMaxK + 1][4];
-    uint64_t off_scr[kMaxK + 1][3];
+    uint64_t off_scr[kMaxK + 1][4];
     for (int ell = 0; ell <= lay->L; ++ell) {
         const uint64_t c = ell == 0 ? lvl0 : E;
         const int nwt = (ell + 3) / 4;
@@ -393,6 +393,7 @@ int plan_layout(Engine *e, int slot, int32_t group_size, int k, int T, int W, bo
             off_scr[ell][0] = bump(nb * kWarps * 4);
             off_scr[ell][1] = bump(nb * 8);
             off_scr[ell][2] = bump((nb + 1) * 8);
+            off_scr[ell][3] = bump(nb * 32 * 4);
         }
     }
     // Level l of a group holds at most group_size * n^l entries (each entry
@@ -419,6 +420,7 @@ int plan_layout(Engine *e, int slot, int32_t group_size, int k, int T, int W, bo
     for (int ell = 0; ell <= lay->L; ++ell) {
         LevelView &lv = lay->level[ell];
         lv.cap = ell == 0 ? lvl0 : E;
+        lv.root = ell == 0;
         lv.S = reinterpret_cast<int32_t *>(base + off_level[ell][0]);
         lv.r = reinterpret_cast<uint32_t *>(base + off_level[ell][1]);
         lv.R = reinterpret_cast<uint32_t *>(base + off_level[ell][2]);
@@ -427,6 +429,7 @@ int plan_layout(Engine *e, int slot, int32_t group_size, int k, int T, int W, bo
             lay->warp_cnt[ell] = reinterpret_cast<uint32_t *>(base + off_scr[ell][0]);
             lay->blk_cnt[ell] = reinterpret_cast<unsigned long long *>(base + off_scr[ell][1]);
             lay->blk_off[ell] = reinterpret_cast<unsigned long long *>(base + off_scr[ell][2]);
+            lay->cut_bits[ell] = reinterpret_cast<uint32_t *>(base + off_scr[ell][3]);
         }
         if (device_mode && ell < lay->L)
             lay->status[ell] = reinterpret_cast<unsigned long long *>(base + off_status[ell]);
@@ -500,7 +503,7 @@ static int run_group(Engine *e, const TopoDevice &t, const GroupRun &gr_in, bool
 // to `size` requests.
 static int group_arrays(Engine *e, int slot, int32_t size, GroupArgs *g, std::string *err) {
     const uint64_t n = static_cast<uint64_t>(std::max(size, 1));
-    const uint64_t bytes = align_up(n * 4, 256) * 6 + align_up(n * 8, 256) * 3 + align_up(n * 32, 256) * 2;
+    const uint64_t bytes = align_up(n * 4, 256) * 7 + align_up(n * 8, 256) * 3 + align_up(n * 32, 256) * 2;
     Slot &sl = e->slots[slot];
     uint64_t have = sl.group_bytes;
     if (have < bytes) e->clear_graphs();
@@ -523,6 +526,7 @@ static int group_arrays(Engine *e, int slot, int32_t size, GroupArgs *g, std::st
     g->work = reinterpret_cast<unsigned long long *>(take(n * 8));
     g->dive_s = reinterpret_cast<int32_t *>(take(n * 4));
     g->dive_t = reinterpret_cast<uint32_t *>(take(n * 32));
+    g->seed_thr = reinterpret_cast<int32_t *>(take(n * 4));
     g->best_t = reinterpret_cast<uint32_t *>(take(n * 32));
     return MAPA_OK;
 }
@@ -640,7 +644,9 @@ int engine_run_batch(Engine *e, const TopoDevice &t, const std::vector<PatternAr
             int32_t ovf = 0;
             memcpy(&ovf, e->h_pinned + 16, sizeof(int32_t));
             if (ovf) {
-                rc = run_group(e, t, gr, false, err);
+                GroupRun redo = gr;
+                redo.redo = true;
+                rc = run_group(e, t, redo, false, err);
                 if (rc != MAPA_OK) return rc;
             }
             k_commit<<<1, 32, 0, e->stream>>>(out_dev + i, t.occupancy, t.owner, t.next_job, nullptr);
@@ -721,6 +727,7 @@ int engine_run_batch(Engine *e, const TopoDevice &t, const std::vector<PatternAr
         gr.g.work = a.work;
         gr.g.dive_s = a.dive_s;
         gr.g.dive_t = a.dive_t;
+        gr.g.seed_thr = a.seed_thr;
         gr.overflow = e->overflow + i;
     }
     // Every group of the batch, device-driven.  A batch whose shape was seen
@@ -828,6 +835,7 @@ int engine_run_batch(Engine *e, const TopoDevice &t, const std::vector<PatternAr
         // its results are in place before anything later on that stream
         GroupRun redo = runs[i];
         redo.stream = nullptr;
+        redo.redo = true;
         rc = run_group(e, t, redo, false, err);
         if (rc != MAPA_OK) return rc;
     }

@@ -18,7 +18,8 @@ namespace mapa {
     do {                                                                                 \
         cudaError_t e_ = (x);                                                            \
         if (e_ != cudaSuccess) {                                                         \
-            if (err) *err = std::string(#x) + ": " + cudaGetErrorString(e_);             \
+            if (err) *err = std::string(#x) + ": " + cudaGetErrorString(e_) + " (" +     \
+                            __FILE__ + ":" + std::to_string(__LINE__) + ")";             \
             return MAPA_E_CUDA;                                                          \
         }                                                                                \
     } while (0)
@@ -120,6 +121,7 @@ struct GroupRun {
     int32_t *overflow;      // device flag for this group (device-driven path)
     bool bounded = false;   // some request of the group is in bounded mode (g.thr set)
     bool sens = false;      // the group's requests are bandwidth-sensitive
+    bool redo = false;      // rerun of a group whose device-driven run overflowed (dive results kept)
     int slot = 0;           // arena of the group
     cudaStream_t stream = nullptr;  // stream of its launches (nullptr = the engine's)
 };

@@ -71,12 +71,15 @@ struct TopoArgs {
 //   r[i]                      request index within the group
 //   R[w * cap + i]            free vertices not yet used (word w)
 //   T[j * cap + i]            tuple bytes 4j..4j+3 (phi of pattern vertices)
+//   root != 0 (level 0 only): T[i] holds the request's range of phi(0),
+//   root_lo | root_hi << 16 (root_hi = 0: no restriction)
 struct LevelView {
     int32_t *S;
     uint32_t *r;
     uint32_t *R;
     uint32_t *T;
     uint64_t cap;
+    int32_t root;
 };
 
 // Per-request state of a group being enumerated.
@@ -109,6 +112,9 @@ struct GroupArgs {
     // = none) and its tuple bytes.
     int32_t *dive_s;           // [size]
     uint32_t *dive_t;          // [size * 8]
+    // The threshold the seed dive set (restored when a group whose frontier
+    // overflowed is redone on the chunked path, which then skips the dive).
+    int32_t *seed_thr;         // [size]
     // Bandwidth-sensitive group (Algorithm 1, first branch): scores are the
     // link-count index (x * R + y) * R + z of the match, ranked through
     // effbw_rank; sens_ok = 0 when the pattern has more edges than R - 1.

@@ -278,6 +278,19 @@ __device__ __forceinline__ void level_masks(const LevelView &L, uint32_t p, uint
     }
 }
 
+// Range of phi(0) of a split request (level 0 only; see LevelView): narrows
+// the candidates of pattern vertex 0 to [root_lo, root_hi).  Call only where
+// pattern vertex 0 is being placed.
+template <int W>
+__device__ __forceinline__ void root_range(const LevelView &L, uint32_t p, uint32_t (&A)[W], int &lb) {
+    if (!L.root) return;
+    const uint32_t t = L.T[p];
+    const int hi = static_cast<int>(t >> 16);
+    if (hi == 0) return;
+    lb = max(lb, static_cast<int>(t & 0xFFFFu) - 1);
+    and_below<W>(A, hi);
+}
+
 // Score increments (see the file header).  CT > 0: the class count is known at
 // compile time and alpha*w_c, beta*w_c live in registers.
 template <int W, int CT>
@@ -484,6 +497,7 @@ __device__ __forceinline__ void tail_precompute(const LevelView &in, uint64_t p,
                                                 const uint32_t *s_adj, TailPre<W, T> &pre) {
 #pragma unroll
     for (int t = 0; t < T; ++t) level_masks<W>(in, p, ta.back_old[t], ta.lo_old[t], s_adj, pre.A[t], pre.B[t], pre.lb[t]);
+    root_range<W>(in, static_cast<uint32_t>(p), pre.A[0], pre.lb[0]);
 }
 
 // Walks tail level t (pattern vertex ell + t) below the tail prefix tv[0..t-1].
@@ -537,7 +551,7 @@ __device__ __forceinline__ bool tail_walk(const SmemTopo &s, const Scorer<W, CT>
 
 // Per request: free set F, root entry (S = beta * W(F), R = F), accumulators.
 template <int W>
-__global__ void k_setup(TopoArgs topo, GroupArgs g, LevelView L0, unsigned long long *count0) {
+__global__ void k_setup(TopoArgs topo, GroupArgs g, LevelView L0, unsigned long long *count0, int redo) {
     const SmemTopo s = stage_topology<W>(topo, true);
     const int lane = threadIdx.x & 31;
     const int gw = static_cast<int>((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
@@ -581,11 +595,14 @@ __global__ void k_setup(TopoArgs topo, GroupArgs g, LevelView L0, unsigned long 
             L0.r[i] = static_cast<uint32_t>(i);
 #pragma unroll
             for (int w = 0; w < W; ++w) L0.R[w * L0.cap + i] = state == 0 ? F[w] : 0u;
+            L0.T[i] = q.root_hi ? (static_cast<uint32_t>(q.root_lo) | (static_cast<uint32_t>(q.root_hi) << 16)) : 0u;
             g.alpha[i] = al;
             g.beta[i] = be;
-            if (g.thr) g.thr[i] = INT_MIN;
+            // a redo keeps the seed dive's threshold and fallback match
+            if (g.thr) g.thr[i] = redo && g.seed_thr ? g.seed_thr[i] : INT_MIN;
             if (g.work) g.work[i] = 0ull;
-            if (g.dive_s) g.dive_s[i] = INT_MIN;
+            if (!redo && g.dive_s) g.dive_s[i] = INT_MIN;
+            if (!redo && g.seed_thr) g.seed_thr[i] = INT_MIN;
             g.key[i] = 0ull;
             g.count[i] = 0ull;
             g.best_valid[i] = state;
@@ -684,7 +701,8 @@ __device__ __forceinline__ void distance_balls(const SmemTopo &s, const uint32_t
 
 template <int W, int CT>
 __device__ bool dive_warp(const SmemTopo &s, const PatternArgs &pat, int32_t S0, const uint32_t (&F)[W], int32_t al,
-                          int32_t be, int lane, int steps, bool guided, int32_t &inc, bool &found, int &rec_v) {
+                          int32_t be, int lane, int steps, bool guided, int root_lo, int root_hi, int32_t &inc,
+                          bool &found, int &rec_v) {
     const Scorer<W, CT> sc(s, al, be);
     const int k = pat.k;
     int32_t my_S = S0;
@@ -697,6 +715,10 @@ __device__ bool dive_warp(const SmemTopo &s, const PatternArgs &pat, int32_t S0,
         root_cand[w] = F[w];  // pattern vertex 0: no earlier neighbour, no constraint
         ball[w] = 0u;
     }
+    if (root_hi > 0) {  // a share of a split request: phi(0) in [root_lo, root_hi)
+        and_above<W>(root_cand, root_lo - 1);
+        and_below<W>(root_cand, root_hi);
+    }
     if (guided) degree_filter<W>(s, root_cand, F, pat.fdeg[0], lane);
 #pragma unroll
     for (int w = 0; w < W; ++w) my_rem[w] = lane == 0 ? root_cand[w] : 0u;
@@ -707,8 +729,10 @@ __device__ bool dive_warp(const SmemTopo &s, const PatternArgs &pat, int32_t S0,
     // guided: until the first match, at most kRootSteps steps below one
     // choice of phi(0), then the next one (an abandoned subtree means the
     // dive no longer proves that no match exists)
-    constexpr int kRootSteps = 1024;
-    int root_steps = 0;
+    // guided: after the first match, at most kImproveSteps more steps to
+    // improve on it
+    constexpr int kRootSteps = 1024, kImproveSteps = 1024;
+    int root_steps = 0, found_at = 0;
     bool abandoned = false;
     for (int step = 0; step < steps; ++step) {
         if (guided && !found && j > 0 && ++root_steps > kRootSteps) {
@@ -716,6 +740,7 @@ __device__ bool dive_warp(const SmemTopo &s, const PatternArgs &pat, int32_t S0,
             root_steps = 0;
             abandoned = true;
         }
+        if (guided && found && step - found_at > kImproveSteps) return false;
         uint32_t rem[W], R[W];
         bool any = false;
 #pragma unroll
@@ -773,6 +798,7 @@ __device__ bool dive_warp(const SmemTopo &s, const PatternArgs &pat, int32_t S0,
             my_v = bv;
         }
         if (j + 1 == k) {
+            if (!found) found_at = step;
             if (!found || best > inc) rec_v = my_v;  // lanes < k hold the path, lane j its last vertex
             inc = found ? max(inc, best) : best;
             found = true;
@@ -841,13 +867,20 @@ __device__ bool dive_warp(const SmemTopo &s, const PatternArgs &pat, int32_t S0,
     return false;
 }
 
-// Per bounded or anytime request (one warp each): the seed dive.  thr = the
-// best complete score it found (bounded mode: the seed of the cut-offs);
-// INT_MAX when it finished the whole search space without a match (there is
-// none); INT_MIN otherwise (no cut-offs).  An anytime request also keeps the
-// dive's best match as its fallback.
+// Per bounded request (one warp each): the seed dive.  thr = the best
+// complete score it found (the seed of the cut-offs); INT_MAX when it
+// finished the whole search space without a match (there is none); INT_MIN
+// otherwise (no cut-offs).  An anytime request also keeps the dive's best
+// match as its fallback.
 template <int W, int CT>
-__global__ void __launch_bounds__(kTpb) k_dive(TopoArgs topo, PatternArgs pat, GroupArgs g, LevelView L0, int steps) {
+//
+// fallback = 1 (run after the enumeration, exhaustive mode): only anytime
+// requests that went past the work budget dive, for their fallback match
+// alone (no threshold is written); nothing runs when the device-driven pass
+// overflowed (*overflow: the chunked redo decides the group instead).
+__global__ void __launch_bounds__(kTpb) k_dive(TopoArgs topo, PatternArgs pat, GroupArgs g, LevelView L0, int steps,
+                                               int fallback, const int32_t *overflow) {
+    if (fallback && overflow && *overflow) return;
     const SmemTopo s = stage_topology<W>(topo, true);
     const int lane = threadIdx.x & 31;
     const int gw = static_cast<int>((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
@@ -859,7 +892,9 @@ __global__ void __launch_bounds__(kTpb) k_dive(TopoArgs topo, PatternArgs pat, G
         // an anytime request keeps the dive's match as its fallback, so it
         // gets enough steps for several complete descents
         const bool anytime = (q.policy.flags & MAPA_POLICY_ANYTIME) != 0 && g.dive_s != nullptr;
-        if (g.sens || !(bounded || anytime) || g.best_valid[i] != 0 || al < 0 || be < 0) continue;
+        if (g.sens || al < 0 || be < 0) continue;
+        if (!fallback && (!bounded || g.best_valid[i] != 0)) continue;
+        if (fallback && (bounded || !anytime || !g.work || g.work[i] <= g.work_budget || g.best_valid[i] < 0)) continue;
         uint32_t F[W];
 #pragma unroll
         for (int w = 0; w < W; ++w) F[w] = L0.R[w * L0.cap + i];
@@ -867,11 +902,15 @@ __global__ void __launch_bounds__(kTpb) k_dive(TopoArgs topo, PatternArgs pat, G
         bool found;
         int rec_v;
         const int my_steps = anytime ? max(steps, 256 * pat.k) : steps;
-        const bool done = dive_warp<W, CT>(s, pat, L0.S[i], F, al, be, lane, my_steps, anytime, inc, found, rec_v);
+        const bool done = dive_warp<W, CT>(s, pat, L0.S[i], F, al, be, lane, my_steps, anytime, q.root_lo, q.root_hi,
+                                           inc, found, rec_v);
         // a finished dive without a match proves there is none (cut every
         // partial, in either mode); a found score seeds the cut-offs of the
         // bounded mode only (an exhaustive request must count every match)
-        if (lane == 0) g.thr[i] = found ? (bounded ? inc : INT_MIN) : (done ? INT_MAX : INT_MIN);
+        if (lane == 0 && !fallback) {
+            g.thr[i] = found ? inc : (done ? INT_MAX : INT_MIN);
+            if (g.seed_thr) g.seed_thr[i] = g.thr[i];
+        }
         if (anytime && found) {
 #pragma unroll
             for (int w = 0; w < 8; ++w) {
@@ -887,10 +926,17 @@ __global__ void __launch_bounds__(kTpb) k_dive(TopoArgs topo, PatternArgs pat, G
 }
 
 // Count pass of the host-driven (chunked) path: children per warp and block.
+// With thresholds (bounded mode, work budget) it also records which parents
+// it cut, one bit per parent in cut_bits[block * 32 + warp * kIpt + j], bit
+// lane: the write pass applies exactly these decisions, because a request's
+// threshold can change between this pass and a later chunk's write pass (the
+// work budget marks requests while deeper levels of earlier chunks run), and
+// the write pass must produce exactly the children counted here.
 template <int W>
 __global__ void __launch_bounds__(kTpb) k_count(TopoArgs topo, LevelView in, uint64_t P, uint32_t back, uint32_t lo,
                                                 uint32_t *warp_cnt, unsigned long long *blk_cnt, const int32_t *thr,
-                                                const int32_t *alpha, const int32_t *beta, LevelBound lbd) {
+                                                const int32_t *alpha, const int32_t *beta, LevelBound lbd,
+                                                uint32_t *cut_bits) {
     const SmemTopo s = stage_topology<W>(topo, thr != nullptr);
     __shared__ uint32_t s_w[kWarps];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -900,10 +946,12 @@ __global__ void __launch_bounds__(kTpb) k_count(TopoArgs topo, LevelView in, uin
     for (int j = 0; j < kIpt; ++j) {
         const uint64_t p = wbase + j * 32 + lane;
         int cnt = 0;
+        bool cut = false;
         if (p < P) {
             uint32_t A[W], B[W], c[W];
             int lb;
             level_masks<W>(in, p, back, lo, s.adj, A, B, lb);
+            root_range<W>(in, static_cast<uint32_t>(p), A, lb);
             uint32_t R[W];
 #pragma unroll
             for (int w = 0; w < W; ++w) {
@@ -914,8 +962,15 @@ __global__ void __launch_bounds__(kTpb) k_count(TopoArgs topo, LevelView in, uin
             cnt = popc_mask<W>(c);
             if (thr && cnt) {
                 const uint32_t r = in.r[p];
-                if (cut_off<W>(s, R, in.S[p], alpha[r], beta[r], thr[r], lbd)) cnt = 0;
+                if (cut_off<W>(s, R, in.S[p], alpha[r], beta[r], thr[r], lbd)) {
+                    cnt = 0;
+                    cut = true;
+                }
             }
+        }
+        if (thr) {
+            const unsigned bits = __ballot_sync(kFull, cut);
+            if (lane == 0) cut_bits[static_cast<uint64_t>(blockIdx.x) * 32 + warp * kIpt + j] = bits;
         }
         wsum += warp_sum_int(cnt);
     }
@@ -988,6 +1043,7 @@ __device__ __forceinline__ void parent_state(const SmemTopo &s, const LevelView 
     uint32_t A[W];
     int lb;
     level_masks<W>(in, p, back, lo, s.adj, A, B, lb);
+    root_range<W>(in, p, A, lb);
 #pragma unroll
     for (int w = 0; w < W; ++w) {
         R[w] = in.R[col_at(in, w, p)];
@@ -1004,7 +1060,7 @@ __global__ void __launch_bounds__(kTpb) k_write(TopoArgs topo, LevelView in, uin
                                                 uint32_t lo, LevelView out, const uint32_t *warp_cnt,
                                                 const unsigned long long *blk_off, uint64_t blk_first,
                                                 const int32_t *alpha, const int32_t *beta, const int32_t *thr,
-                                                LevelBound lbd) {
+                                                const uint32_t *cut_bits) {
     const SmemTopo s = stage_topology<W>(topo, true);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const uint64_t b = blk_first + blockIdx.x;
@@ -1023,7 +1079,8 @@ __global__ void __launch_bounds__(kTpb) k_write(TopoArgs topo, LevelView in, uin
             parent_state<W>(s, in, p, back, lo, cand, B, R, S, r);
             al = alpha[r];
             be = beta[r];
-            if (thr && popc_mask<W>(cand) && cut_off<W>(s, R, S, al, be, thr[r], lbd)) {
+            // the count pass's cut decision, not a new one (see k_count)
+            if (thr && ((cut_bits[b * 32 + warp * kIpt + j] >> lane) & 1u)) {
 #pragma unroll
                 for (int w = 0; w < W; ++w) cand[w] = 0u;
             }
@@ -1388,6 +1445,7 @@ __device__ __forceinline__ void short_tail_first(const SmemTopo &s, const LevelV
                                                  const TailArgs &ta, ShortTailState<W, T> &st) {
     st.S = in.S[p];
     level_masks<W>(in, p, ta.back_old[0], ta.lo_old[0], s.adj, st.A, st.B, st.lb);
+    root_range<W>(in, p, st.A, st.lb);
 #pragma unroll
     for (int w = 0; w < W; ++w) {
         st.R[w] = in.R[col_at(in, w, p)];
@@ -1726,6 +1784,7 @@ __global__ void __launch_bounds__(kTpb) k_last_coop3(TopoArgs topo, LevelView in
             uint32_t A1[W];
             int lb1;
             level_masks<W>(in, p, ta.back_old[0], ta.lo_old[0], s.adj, A1, B1, lb1);
+            root_range<W>(in, p, A1, lb1);
             level_masks<W>(in, p, ta.back_old[1], ta.lo_old[1], s.adj, A2, B2, lb2);
             level_masks<W>(in, p, ta.back_old[2], ta.lo_old[2], s.adj, A3, B3, lb3);
 #pragma unroll

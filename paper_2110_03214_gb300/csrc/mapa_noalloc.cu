@@ -151,6 +151,7 @@ __device__ int32_t na_request_state(const mapa_request &q, int32_t pattern_id, i
     // left after its cut-offs; this kernel has no cut-offs, so it cannot give
     // the same answer and refuses the combination.
     if (q.policy.mode == MAPA_MODE_BOUNDED && q.policy.max_embeddings > 0) return -3;
+    if (q.root_hi != 0) return -3;  // shares of a split request are decided by the batched call
     const long long mag = (llabs(static_cast<long long>(q.policy.alpha)) + llabs(static_cast<long long>(q.policy.beta))) *
                           static_cast<long long>(total_weight);
     return mag >= (1LL << 31) ? -2 : 0;

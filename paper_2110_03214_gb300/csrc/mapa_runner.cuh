@@ -20,6 +20,7 @@ struct LayoutPlan {
     uint32_t *warp_cnt[kMaxK + 1];
     unsigned long long *blk_cnt[kMaxK + 1];
     unsigned long long *blk_off[kMaxK + 1];
+    uint32_t *cut_bits[kMaxK + 1];  // count pass's cut decisions, 32 words per block
     // device-driven path: level counts, tile tickets, look-back status words
     unsigned long long *counts = nullptr;   // [L + 1]
     unsigned int *tiles = nullptr;          // [L + 1]
@@ -132,14 +133,15 @@ struct Runner {
 
     int setup(unsigned long long *count0) {
         const unsigned sgrid = static_cast<unsigned>(std::min<uint64_t>(ceil_div(g.size, kWarps), 4096));
-        k_setup<W><<<sgrid, kTpb, smem_all, st>>>(targs, g, lay.level[0], count0);
+        k_setup<W><<<sgrid, kTpb, smem_all, st>>>(targs, g, lay.level[0], count0, gr.redo ? 1 : 0);
         MAPA_CUDA_TRY(cudaGetLastError());
         e->st.kernel_launches += 1;
-        if (g.thr && !gr.sens) {
-            // bounded mode: seed scores for the cut-offs; anytime requests:
-            // their fallback match (one warp per request; others skip)
+        MAPA_CUDA_TRY(cudaGetLastError());
+        if (gr.bounded && !gr.sens && !gr.redo) {
+            // bounded mode: seed scores for the cut-offs (and the fallback
+            // match of anytime requests); one warp per request, others skip
             const unsigned dgrid = static_cast<unsigned>(std::min<uint64_t>(ceil_div(g.size, kWarps), 4096));
-            k_dive<W, CT><<<dgrid, kTpb, smem_all, st>>>(targs, pat, g, lay.level[0], e->dive_steps);
+            k_dive<W, CT><<<dgrid, kTpb, smem_all, st>>>(targs, pat, g, lay.level[0], e->dive_steps, 0, nullptr);
             MAPA_CUDA_TRY(cudaGetLastError());
             e->st.kernel_launches += 1;
         }
@@ -158,6 +160,14 @@ struct Runner {
     }
 
     int finalize() {
+        if (g.work && !gr.sens) {
+            // exhaustive anytime requests past the budget: their fallback dive
+            const unsigned dgrid = static_cast<unsigned>(std::min<uint64_t>(ceil_div(g.size, kWarps), 4096));
+            k_dive<W, CT><<<dgrid, kTpb, smem_all, st>>>(targs, pat, g, lay.level[0], e->dive_steps, 1,
+                                                         gr.redo ? nullptr : gr.overflow);
+            MAPA_CUDA_TRY(cudaGetLastError());
+            e->st.kernel_launches += 1;
+        }
         const unsigned fgrid = static_cast<unsigned>(std::min<uint64_t>(ceil_div(g.size, 128), 4096));
         k_finalize<W><<<fgrid, 128, smem_all, st>>>(t.args(), pat, g);  // real weights: AggBW, PreservedBW
         MAPA_CUDA_TRY(cudaGetLastError());
@@ -220,6 +230,7 @@ struct Runner {
             k_last<W, CT, T, false><<<grid, kTpb, smem_all, st>>>(
                 targs, in, count_dev, count_host, ta, g.alpha, g.beta, g.key, g.count, tile_ctr, e->d_stats, g.thr);
         }
+        MAPA_CUDA_TRY(cudaGetLastError());
         if (e->timing) MAPA_CUDA_TRY(cudaEventRecord(ev1, st));
         const unsigned rgrid = static_cast<unsigned>(std::min<uint64_t>(ceil_div(g.size, 256), 1024));
         k_resolve<W, CT, T><<<rgrid, 256, smem_all, st>>>(targs, in, count_dev, count_host, ta, g);
@@ -283,7 +294,8 @@ struct Runner {
         }
         k_count<W><<<static_cast<unsigned>(nb), kTpb, g.thr ? smem_all : smem_adj, st>>>(
             targs, in, P, pat.back[ell], pat.lo[ell], lay.warp_cnt[ell], lay.blk_cnt[ell], g.thr, g.alpha, g.beta,
-            bound_at(ell));
+            bound_at(ell), lay.cut_bits[ell]);
+        MAPA_CUDA_TRY(cudaGetLastError());
         launch_scan(lay.blk_cnt[ell], lay.blk_off[ell], nb, st);
         MAPA_CUDA_TRY(cudaGetLastError());
         if (e->timing) MAPA_CUDA_TRY(cudaEventRecord(cev1, st));
@@ -320,7 +332,7 @@ struct Runner {
             }
             k_write<W, CT><<<static_cast<unsigned>(b1 - b0), kTpb, smem_all, st>>>(
                 targs, in, P, ell, pat.back[ell], pat.lo[ell], out, lay.warp_cnt[ell], lay.blk_off[ell], b0,
-                g.alpha, g.beta, g.thr, bound_at(ell));
+                g.alpha, g.beta, g.thr, lay.cut_bits[ell]);
             MAPA_CUDA_TRY(cudaGetLastError());
             if (e->timing) MAPA_CUDA_TRY(cudaEventRecord(wev1, st));
             e->st.kernel_launches += 1;

@@ -41,9 +41,9 @@ MAX_K = 32
 
 REQUEST_DTYPE = np.dtype(
     {
-        "names": ["pattern_id", "reserved", "alpha", "beta", "mode", "flags", "max_embeddings", "busy"],
-        "formats": ["<i4", "<i4", "<i4", "<i4", "<i4", "<i4", "<u8", ("<u4", (8,))],
-        "offsets": [0, 4, 8, 12, 16, 20, 24, 32],
+        "names": ["pattern_id", "root_lo", "root_hi", "alpha", "beta", "mode", "flags", "max_embeddings", "busy"],
+        "formats": ["<i4", "<u2", "<u2", "<i4", "<i4", "<i4", "<i4", "<u8", ("<u4", (8,))],
+        "offsets": [0, 4, 6, 8, 12, 16, 20, 24, 32],
         "itemsize": 64,
     }
 )
@@ -157,6 +157,7 @@ def _load() -> ctypes.CDLL:
         "mapa_ctx_set_timing": ([vp, ctypes.c_int], ctypes.c_int),
         "mapa_ctx_set_work_budget": ([vp, u64], ctypes.c_int),
         "mapa_measure_int_peak": ([vp, i32, ctypes.POINTER(ctypes.c_double)], ctypes.c_int),
+        "mapa_result_merge": ([i32, vp, vp], ctypes.c_int),
         "mapa_serve_open": ([vp, i32, i32, u32, ctypes.POINTER(vp)], ctypes.c_int),
         "mapa_serve_submit": ([vp, vp, i32], ctypes.c_int),
         "mapa_serve_poll": ([vp, vp, i32, ctypes.POINTER(ctypes.c_int32), i32], ctypes.c_int),
@@ -186,6 +187,7 @@ SYMBOLS = (
     "mapa_ctx_set_timing", "mapa_allocate_batch_noalloc", "mapa_serve_open", "mapa_serve_submit",
     "mapa_serve_poll", "mapa_serve_drain", "mapa_serve_counters", "mapa_serve_close", "mapa_autotune",
     "mapa_effbw_predict", "mapa_simulate", "mapa_ctx_set_work_budget", "mapa_measure_int_peak",
+    "mapa_result_merge",
 )
 
 
@@ -318,6 +320,17 @@ def mapa_stats_reset(ctx) -> None:
 
 def mapa_ctx_set_timing(ctx, on: bool) -> None:
     _check(ctx, lib.mapa_ctx_set_timing(ctx, 1 if on else 0))
+
+
+def mapa_result_merge(parts) -> np.ndarray:
+    """Reduces the results of the shares of one split request (RESULT_DTYPE
+    array) to one result."""
+    parts = np.ascontiguousarray(parts, dtype=RESULT_DTYPE)
+    out = np.zeros(1, RESULT_DTYPE)
+    rc = lib.mapa_result_merge(parts.shape[0], parts.ctypes.data, out.ctypes.data)
+    if rc != MAPA_OK:
+        raise MapaError(rc, "mapa_result_merge failed")
+    return out[0]
 
 
 def mapa_measure_int_peak(ctx, kind: int) -> float:

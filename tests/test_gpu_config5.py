@@ -273,3 +273,25 @@ def test_anytime_past_budget(M, env):
         assert not ctx.occupancy(tid).any()
     finally:
         ctx.set_work_budget(0)
+
+
+def test_budget_with_chunked_frontier(M):
+    """The work budget on the chunked path: with a 1 GiB frontier cap the
+    served-snapshot requests' levels are produced in many chunks, and a
+    request can pass its budget between the count pass of a level and a
+    later chunk's write pass; the results equal those with a 16 GiB cap."""
+    wl = W.workload("boards256", num_requests=300)
+    out = []
+    for cap in (16 << 30, 1 << 30):
+        with M.Context(0, frontier_mem_cap=cap) as ctx:
+            tid = ctx.topology_load(wl.topology)
+            pids = [ctx.pattern_load(p) for p in wl.requests.patterns]
+            reqs = ctx.requests(wl.requests, pids)
+            reqs["flags"] |= M.MAPA_POLICY_ANYTIME
+            ctx.set_work_budget(1 << 20)
+            out.append(ctx.allocate_batch(tid, reqs))
+            st = ctx.stats()
+            assert st["expand_launches"] > 0
+    assert np.array_equal(out[0], out[1])
+    statuses = set(int(x) for x in out[0]["status"])
+    assert {M.MAPA_INEXACT, M.MAPA_NO_FIT} <= statuses

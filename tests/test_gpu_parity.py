@@ -361,3 +361,60 @@ def test_every_tail_depth_gives_the_same_results(M, monkeypatch, name, num):
     idx = list(range(0, len(wl.requests), max(1, len(wl.requests) // 40)))
     for i, d in zip(idx, oracle_decisions(inst, wl.topology.n, wl.requests, idx)):
         assert_same(out[3][i], d, wl.requests.patterns[wl.requests.pattern_index[i]].k, where=f"request {i}")
+
+
+@pytest.mark.parametrize("name,num,mode", [("regular32", 600, 0), ("regular32", 600, 1), ("torus64", 800, 0),
+                                           ("cube_mesh8", 300, 0)])
+def test_root_split_shares_merge_to_unsplit(M, ctx, name, num, mode):
+    """One request split into shares by the range of phi(0) (root_lo,
+    root_hi), all shares decided in one batch and reduced with
+    mapa_result_merge: status, score, AggBW, PreservedBW, count and tuple
+    equal the unsplit decision (each match class is enumerated in exactly
+    one share)."""
+    wl = W.workload(name, num_requests=num)
+    n = wl.topology.n
+    tid, pids = _load(ctx, wl)
+    reqs = ctx.requests(wl.requests, pids, mode=mode)
+    whole = ctx.allocate_batch(tid, reqs)
+    cuts = [0, n // 5, n // 2, (3 * n) // 4, n]
+    shares = np.repeat(reqs, 4)
+    for j in range(4):
+        shares["root_lo"][j::4] = cuts[j]
+        shares["root_hi"][j::4] = cuts[j + 1]
+    parts = ctx.allocate_batch(tid, shares)
+    for i in range(len(reqs)):
+        got = M.mapa_result_merge(parts[4 * i:4 * i + 4])
+        k = int(whole[i]["k"])
+        want = whole[i]
+        assert (int(got["status"]), int(got["score"]), int(got["agg"]), int(got["pres"]), int(got["count"])) == \
+            (int(want["status"]), int(want["score"]), int(want["agg"]), int(want["pres"]), int(want["count"])), i
+        assert np.array_equal(got["verts"][:k], want["verts"][:k]), i
+    assert int((whole["status"] == 0).sum()) > 0
+
+
+def test_root_split_when_the_tail_starts_at_vertex_zero(M, monkeypatch):
+    """Patterns whose fused tail covers pattern vertex 0 (k = 1; k = 3 with a
+    tail depth of 3): the share's range of phi(0) is applied inside the tail
+    kernels (short tail, cooperative depth-3 tail, generic tail in bounded
+    mode)."""
+    monkeypatch.setenv("MAPA_TAIL_DEPTH", "3")
+    topo = W.workload("regular32", num_requests=1).topology
+    pats = [W.pattern("ring", 1), W.pattern("clique", 3), W.pattern("path", 3), W.pattern("tree", 3)]
+    reqs_w = _random_busy_requests(W.Rng(77, 1), topo.n, pats, 200, 0.0, 0.5)
+    with M.Context(0) as c:
+        tid = c.topology_load(topo)
+        pids = [c.pattern_load(p) for p in pats]
+        for mode in (0, 1):
+            reqs = c.requests(reqs_w, pids, mode=mode)
+            whole = c.allocate_batch(tid, reqs)
+            shares = np.repeat(reqs, 3)
+            for j, (lo, hi) in enumerate(((0, 7), (7, 20), (20, 32))):
+                shares["root_lo"][j::3] = lo
+                shares["root_hi"][j::3] = hi
+            parts = c.allocate_batch(tid, shares)
+            for i in range(len(reqs)):
+                got = M.mapa_result_merge(parts[3 * i:3 * i + 3])
+                k = int(whole[i]["k"])
+                assert (int(got["status"]), int(got["score"]), int(got["count"])) == \
+                    (int(whole[i]["status"]), int(whole[i]["score"]), int(whole[i]["count"])), (mode, i)
+                assert np.array_equal(got["verts"][:k], whole[i]["verts"][:k]), (mode, i)

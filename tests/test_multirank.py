@@ -111,3 +111,76 @@ def test_two_ranks_decide_their_shards():
         assert total_ms == 20.0 and e2e_s == 1.5 and emb == 2001.0
     assert out[0][2] == out[1][2]
     assert out[0][3].shape == out[1][3].shape and not np.array_equal(out[0][3], out[1][3])
+
+
+def _rank_split(rank, world, port, q):
+    """One large request split by phi(0): rank r decides its share of the
+    vertex range through the oracle; rank 0 gathers one result per share
+    (the exchange step) and reduces them with the library's merge."""
+    import sys
+
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    sys.path.insert(0, root)
+    import bench
+    from oracle import oracle as O
+    from paper_2110_03214_gb300 import mapa as M
+    from paper_2110_03214_gb300 import workloads as W
+
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    wl = W.workload("regular32", num_requests=12)
+    inst = O.Instance.from_topology(wl.topology)
+    lo, hi = bench.shard_slice(32, rank, world)
+    mine = []
+    for i in range(len(wl.requests)):
+        p = wl.requests.patterns[wl.requests.pattern_index[i]]
+        d = inst.decide_rooted(W.busy_to_bool(wl.requests.busy[i], 32), p.k, p.a, p.b, 1, 1, lo, hi)
+        mine.append((d.status, d.score, d.agg, d.pres, d.maps, d.tuple, p.k))
+    gathered = [None] * world if rank == 0 else None
+    dist.gather_object(mine, gathered, dst=0)
+    merged = None
+    if rank == 0:
+        merged = []
+        for i in range(len(wl.requests)):
+            parts = np.zeros(world, M.RESULT_DTYPE)
+            for r in range(world):
+                st, score, agg, pres, maps, tup, k = gathered[r][i]
+                parts[r]["status"] = M.MAPA_OK if st == O.STATUS_OK else M.MAPA_NO_FIT
+                parts[r]["score"], parts[r]["agg"], parts[r]["pres"] = score, agg, pres
+                parts[r]["count"], parts[r]["k"] = maps, k
+                parts[r]["verts"][: len(tup)] = tup
+            m = M.mapa_result_merge(parts)
+            merged.append((int(m["status"]), int(m["score"]), int(m["count"]), tuple(int(x) for x in m["verts"][: k])))
+    q.put((rank, merged))
+    dist.barrier()
+    dist.destroy_process_group()
+
+
+def test_two_ranks_split_one_request():
+    world = 2
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_rank_split, args=(r, world, port, q)) for r in range(world)]
+    for p in procs:
+        p.start()
+    out = {}
+    for _ in range(world):
+        r, merged = q.get(timeout=300)
+        out[r] = merged
+    for p in procs:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    from oracle import oracle as O
+    from paper_2110_03214_gb300 import workloads as W
+
+    wl = W.workload("regular32", num_requests=12)
+    inst = O.Instance.from_topology(wl.topology)
+    for i, got in enumerate(out[0]):
+        p = wl.requests.patterns[wl.requests.pattern_index[i]]
+        d = inst.decide(W.busy_to_bool(wl.requests.busy[i], 32), p.k, p.a, p.b, 1, 1)
+        assert got[2] == d.maps
+        if d.status == O.STATUS_OK:
+            assert got[0] == 0 and got[1] == d.score and got[3] == d.tuple
+        else:
+            assert got[0] == 1

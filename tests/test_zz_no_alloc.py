@@ -141,9 +141,9 @@ def test_request_branches_match_batched(env, case):
 
 
 def test_refused_request_kinds_are_invalid(env):
-    """Bandwidth-sensitive requests, and bounded ones carrying a match budget,
-    are refused per request (MAPA_E_INVALID); the rest of the call is decided
-    as the batched entry point decides it."""
+    """Bandwidth-sensitive requests, bounded ones carrying a match budget and
+    shares of a split request are refused per request (MAPA_E_INVALID); the
+    rest of the call is decided as the batched entry point decides it."""
     torch, M, ctx = env
     wl = W.workload("regular32", num_requests=256)
     tid, pids, reqs = _by_pattern(ctx, wl)
@@ -151,9 +151,12 @@ def test_refused_request_kinds_are_invalid(env):
     refused = np.zeros(len(sel), bool)
     refused[0::3] = True
     refused[1::5] = True
+    refused[2::7] = True
     sel["flags"][0::3] = M.MAPA_POLICY_BW_SENSITIVE
     sel["mode"][1::5] = M.MAPA_MODE_BOUNDED
     sel["max_embeddings"][1::5] = 1000
+    sel["root_lo"][2::7] = 3  # a share of a split request
+    sel["root_hi"][2::7] = 17
     got = _noalloc(torch, M, ctx, tid, pids[1], sel)
     assert (got["status"][refused] == M.MAPA_E_INVALID).all()
     assert (got["count"][refused] == 0).all()
