@@ -486,6 +486,8 @@ def measure_batch(M, W, torch, a, name, rank, world, dist, local, plain_requests
     else:
         tuned = M.mapa_autotune(ctx.h, tid, reqs, len(pids))
         tail_depths = {wl.requests.patterns[i].name: int(tuned[p]) for i, p in enumerate(pids)}
+        tail_depths["level_limits"] = {wl.requests.patterns[i].name: M.mapa_autotune_level_limit(ctx.h, tid, p)
+                                       for i, p in enumerate(pids)}
 
     for _ in range(a.warmup):
         flush.zero_()

@@ -116,18 +116,20 @@ enum mapa_policy_flags { MAPA_POLICY_BW_SENSITIVE = 1u, MAPA_POLICY_ANYTIME = 2u
  * enumeration, for the requests past the budget only), with status
  * MAPA_INEXACT, its
  * score, AggBW and PreservedBW recomputed from the tuple, count 0.  For such
- * a request the dive runs up to 256 k steps and is guided towards a match
+ * a request the dive runs up to 128 k steps and is guided towards a match
  * rather than a high score: candidates that violate two necessary conditions
  * of any match are skipped (the image of pattern vertex j lies within its
  * pattern distance from phi(0) in the free graph, and has at least as many
  * free neighbours as j has later pattern neighbours), the child with the
  * most free neighbours is taken first, at most 1024 steps are spent below
  * one phi(0) before the next is tried, and once a match is found the dive
- * continues best score first for at most 1024 more steps.  The fallback
+ * continues best score first for at most 256 more steps.  The fallback
  * depends on the request alone,
  * so it is the same on every run and in every batch.  It is committed like
  * MAPA_OK (mapa_allocate, sequential batches, the served loop).  With no
- * match from the dive the result is MAPA_E_BUDGET.  A request that finishes
+ * match from the dive the result is MAPA_E_BUDGET, or MAPA_NO_FIT when the
+ * dive finished its whole search (which then proves that no match
+ * exists).  A request that finishes
  * within the budget gets its exact result (MAPA_OK or MAPA_NO_FIT) as
  * without the flag.  The paper's policy is exact; this is a bounded-cost
  * fallback for free sets too large to enumerate. */
@@ -417,6 +419,14 @@ typedef struct {
  * chosen for each (0 for patterns absent from the batch).  Nothing is
  * committed. */
 int mapa_autotune(mapa_ctx ctx, int32_t topo_id, int32_t nreq, const mapa_request *reqs, int32_t *chosen);
+
+/* The autotuner also times, at the chosen depth, limits of 4M and 1M entries
+ * on a stored level (default: as many as the frontier cap allows) and keeps
+ * one that is clearly faster: on frontiers that do not fit, smaller levels
+ * are produced in chunks that stay in L2 between the count and write passes.
+ * Results never change with the limit.  *entries receives the limit kept for
+ * (topo_id, pattern_id), 0 for none. */
+int mapa_autotune_level_limit(mapa_ctx ctx, int32_t topo_id, int32_t pattern_id, uint64_t *entries);
 
 /* Copies the counters into *out. */
 int mapa_stats_get(mapa_ctx ctx, mapa_stats *out);

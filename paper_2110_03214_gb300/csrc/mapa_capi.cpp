@@ -542,6 +542,12 @@ int mapa_ctx_set_work_budget(mapa_ctx ctx, uint64_t max_partials) {
     return MAPA_OK;
 }
 
+int mapa_autotune_level_limit(mapa_ctx ctx, int32_t topo_id, int32_t pattern_id, uint64_t *entries) {
+    if (!ctx || !entries) return MAPA_E_INVALID;
+    *entries = mapa::engine_tuned_chunk(ctx->engine, topo_id, pattern_id);
+    return MAPA_OK;
+}
+
 int mapa_result_merge(int32_t nparts, const mapa_result *parts, mapa_result *out) {
     if (nparts < 1 || !parts || !out) return MAPA_E_INVALID;
     mapa_result best;

@@ -325,6 +325,10 @@ void engine_set_timing(Engine *e, bool on) { e->timing = on; }
 
 void engine_set_work_budget(Engine *e, uint64_t max_partials) { e->work_budget = max_partials; }
 
+uint64_t engine_tuned_chunk(const Engine *e, int32_t topo_id, int32_t pattern_id) {
+    return chunk_limit(e, topo_id, pattern_id);
+}
+
 int engine_stage(Engine *e, int32_t nreq, mapa_request **reqs_dev, mapa_result **out_dev, std::string *err) {
     if (nreq > e->stage_cap) {
         cudaFree(e->stage_reqs);
@@ -350,7 +354,7 @@ int engine_stage(Engine *e, int32_t nreq, mapa_request **reqs_dev, mapa_result *
 // bytes.  Level 0 holds the group's roots; levels 1..L share capacity E.
 
 int plan_layout(Engine *e, int slot, int32_t group_size, int k, int T, int W, bool device_mode, int n,
-                LayoutPlan *lay, std::string *err) {
+                LayoutPlan *lay, std::string *err, uint64_t max_entries) {
     lay->L = k - T;
     const uint64_t cap = e->frontier_cap;
     const uint64_t lvl0 = static_cast<uint64_t>(std::max(group_size, 1));
@@ -366,6 +370,8 @@ int plan_layout(Engine *e, int slot, int32_t group_size, int k, int T, int W, bo
         }
         E = (cap - fixed) * 1024 / (per_entry * 1024 + scr_x1024 * lay->L + 1);
         E = std::min<uint64_t>(E, kMaxLevelEntries);
+        // a tuned level-size limit, never below one tile of children
+        if (max_entries) E = std::min<uint64_t>(E, std::max<uint64_t>(max_entries, uint64_t(kTile) * n));
         E = E / kTile * kTile;
         if (E < static_cast<uint64_t>(kTile) * static_cast<uint64_t>(n)) {
             if (err) *err = "frontier memory cap too small (needs room for one tile of children per level)";
@@ -503,7 +509,7 @@ static int run_group(Engine *e, const TopoDevice &t, const GroupRun &gr_in, bool
 // to `size` requests.
 static int group_arrays(Engine *e, int slot, int32_t size, GroupArgs *g, std::string *err) {
     const uint64_t n = static_cast<uint64_t>(std::max(size, 1));
-    const uint64_t bytes = align_up(n * 4, 256) * 7 + align_up(n * 8, 256) * 3 + align_up(n * 32, 256) * 2;
+    const uint64_t bytes = align_up(n * 4, 256) * 6 + align_up(n * 8, 256) * 3 + align_up(n * 32, 256) * 2;
     Slot &sl = e->slots[slot];
     uint64_t have = sl.group_bytes;
     if (have < bytes) e->clear_graphs();
@@ -526,7 +532,6 @@ static int group_arrays(Engine *e, int slot, int32_t size, GroupArgs *g, std::st
     g->work = reinterpret_cast<unsigned long long *>(take(n * 8));
     g->dive_s = reinterpret_cast<int32_t *>(take(n * 4));
     g->dive_t = reinterpret_cast<uint32_t *>(take(n * 32));
-    g->seed_thr = reinterpret_cast<int32_t *>(take(n * 4));
     g->best_t = reinterpret_cast<uint32_t *>(take(n * 32));
     return MAPA_OK;
 }
@@ -727,7 +732,6 @@ int engine_run_batch(Engine *e, const TopoDevice &t, const std::vector<PatternAr
         gr.g.work = a.work;
         gr.g.dive_s = a.dive_s;
         gr.g.dive_t = a.dive_t;
-        gr.g.seed_thr = a.seed_thr;
         gr.overflow = e->overflow + i;
     }
     // Every group of the batch, device-driven.  A batch whose shape was seen
@@ -773,6 +777,7 @@ int engine_run_batch(Engine *e, const TopoDevice &t, const std::vector<PatternAr
             key.push_back(gr.g.req_index - e->order);
             key.push_back(gr.bounded);
             key.push_back(gr.sens);
+            key.push_back(static_cast<int64_t>(chunk_limit(e, t.id, gr.pat->id)));
         }
         auto it = e->graphs.find(key);
         const bool repeat = it != e->graphs.end() || e->shapes_seen.count(key) > 0;
@@ -787,7 +792,8 @@ int engine_run_batch(Engine *e, const TopoDevice &t, const std::vector<PatternAr
             // plan every group once outside capture so no allocation happens inside it
             for (const GroupRun &gr : runs) {
                 LayoutPlan lay;
-                rc = plan_layout(e, gr.slot, gr.g.size, gr.pat->k, gr.tail, t.W, true, t.n, &lay, err);
+                rc = plan_layout(e, gr.slot, gr.g.size, gr.pat->k, gr.tail, t.W, true, t.n, &lay, err,
+                                 chunk_limit(e, t.id, gr.pat->id));
                 if (rc != MAPA_OK) return rc;
             }
             const mapa_stats before = e->st;
@@ -1033,6 +1039,28 @@ int engine_autotune(Engine *e, const TopoDevice &t, const std::vector<PatternArg
         if (best_t) {
             e->tail_table[{t.id, p}] = best_t;
             chosen[p] = best_t;
+            // then the level-size limit at that depth: none, 4M or 1M entries
+            uint64_t best_c = 0;
+            for (uint64_t lim : {uint64_t(1) << 22, uint64_t(1) << 20}) {
+                if (rc != MAPA_OK) break;
+                e->chunk_table[{t.id, p}] = lim;
+                float ms_min = 0.f;
+                for (int rep = 0; rep < 3 && rc == MAPA_OK; ++rep) {
+                    cudaEventRecord(ev0, e->stream);
+                    rc = engine_run_batch(e, t, patterns, n, d_reqs, d_out, false, err);
+                    cudaEventRecord(ev1, e->stream);
+                    cudaEventSynchronize(ev1);
+                    float ms = 0.f;
+                    cudaEventElapsedTime(&ms, ev0, ev1);
+                    if (rep == 1 || (rep > 1 && ms < ms_min)) ms_min = ms;
+                }
+                if (rc == MAPA_OK && ms_min < 0.97f * best_ms) {  // keep a limit only for a clear gain
+                    best_ms = ms_min;
+                    best_c = lim;
+                }
+            }
+            if (best_c) e->chunk_table[{t.id, p}] = best_c;
+            else e->chunk_table.erase({t.id, p});
         }
     }
     e->st = saved;

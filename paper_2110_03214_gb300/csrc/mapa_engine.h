@@ -72,6 +72,10 @@ struct Engine {
     uint64_t work_budget = 0;    // stored partial matches a request may produce (0 = no limit)
     bool tail_sorted = false;    // short fused tail: parents of a tile ordered by estimated subtree size (MAPA_TAIL_SORT=1)
     std::map<std::pair<int32_t, int32_t>, int> tail_table;  // (topology, pattern) -> tuned depth
+    // (topology, pattern) -> tuned largest entries of a stored level (0 = as
+    // many as the frontier cap allows): smaller levels make the chunked path
+    // produce a level in smaller chunks that stay in L2 between passes
+    std::map<std::pair<int32_t, int32_t>, uint64_t> chunk_table;
     // Captured launch sequences of independent batches, keyed by batch shape.
     bool use_graphs = true;
     struct GraphEntry {
@@ -121,7 +125,7 @@ struct GroupRun {
     int32_t *overflow;      // device flag for this group (device-driven path)
     bool bounded = false;   // some request of the group is in bounded mode (g.thr set)
     bool sens = false;      // the group's requests are bandwidth-sensitive
-    bool redo = false;      // rerun of a group whose device-driven run overflowed (dive results kept)
+    bool redo = false;      // rerun of a group whose device-driven run overflowed (on the chunked path)
     int slot = 0;           // arena of the group
     cudaStream_t stream = nullptr;  // stream of its launches (nullptr = the engine's)
 };

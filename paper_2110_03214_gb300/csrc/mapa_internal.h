@@ -112,9 +112,6 @@ struct GroupArgs {
     // = none) and its tuple bytes.
     int32_t *dive_s;           // [size]
     uint32_t *dive_t;          // [size * 8]
-    // The threshold the seed dive set (restored when a group whose frontier
-    // overflowed is redone on the chunked path, which then skips the dive).
-    int32_t *seed_thr;         // [size]
     // Bandwidth-sensitive group (Algorithm 1, first branch): scores are the
     // link-count index (x * R + y) * R + z of the match, ranked through
     // effbw_rank; sens_ok = 0 when the pattern has more edges than R - 1.
@@ -180,6 +177,7 @@ int engine_autotune(Engine *e, const TopoDevice &t, const std::vector<PatternArg
 void engine_stats_reset(Engine *e);
 void engine_set_timing(Engine *e, bool on);
 void engine_set_work_budget(Engine *e, uint64_t max_partials);
+uint64_t engine_tuned_chunk(const Engine *e, int32_t topo_id, int32_t pattern_id);
 
 // Allocation-free single-kernel decision (mapa_noalloc.cu).
 int noalloc_decide(const TopoDevice &t, const PatternArgs &pat, int32_t pattern_id, int32_t nreq,

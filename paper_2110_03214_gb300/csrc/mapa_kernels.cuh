@@ -56,6 +56,8 @@ constexpr unsigned long long kFlagAgg = 1ull << 62;
 constexpr unsigned long long kFlagPrefix = 2ull << 62;
 constexpr unsigned long long kValueMask = (1ull << 62) - 1;
 constexpr unsigned kSpinLimit = 1u << 24;
+// dive_s of an anytime request whose fallback dive proved it has no match
+constexpr int32_t kDiveNoMatch = INT_MIN + 1;
 
 // Device stats slots (summed over a batch, read once at its end).
 enum StatSlot {
@@ -551,7 +553,7 @@ __device__ __forceinline__ bool tail_walk(const SmemTopo &s, const Scorer<W, CT>
 
 // Per request: free set F, root entry (S = beta * W(F), R = F), accumulators.
 template <int W>
-__global__ void k_setup(TopoArgs topo, GroupArgs g, LevelView L0, unsigned long long *count0, int redo) {
+__global__ void k_setup(TopoArgs topo, GroupArgs g, LevelView L0, unsigned long long *count0) {
     const SmemTopo s = stage_topology<W>(topo, true);
     const int lane = threadIdx.x & 31;
     const int gw = static_cast<int>((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
@@ -598,11 +600,9 @@ __global__ void k_setup(TopoArgs topo, GroupArgs g, LevelView L0, unsigned long 
             L0.T[i] = q.root_hi ? (static_cast<uint32_t>(q.root_lo) | (static_cast<uint32_t>(q.root_hi) << 16)) : 0u;
             g.alpha[i] = al;
             g.beta[i] = be;
-            // a redo keeps the seed dive's threshold and fallback match
-            if (g.thr) g.thr[i] = redo && g.seed_thr ? g.seed_thr[i] : INT_MIN;
+            if (g.thr) g.thr[i] = INT_MIN;
             if (g.work) g.work[i] = 0ull;
-            if (!redo && g.dive_s) g.dive_s[i] = INT_MIN;
-            if (!redo && g.seed_thr) g.seed_thr[i] = INT_MIN;
+            if (g.dive_s) g.dive_s[i] = INT_MIN;
             g.key[i] = 0ull;
             g.count[i] = 0ull;
             g.best_valid[i] = state;
@@ -731,7 +731,7 @@ __device__ bool dive_warp(const SmemTopo &s, const PatternArgs &pat, int32_t S0,
     // dive no longer proves that no match exists)
     // guided: after the first match, at most kImproveSteps more steps to
     // improve on it
-    constexpr int kRootSteps = 1024, kImproveSteps = 1024;
+    constexpr int kRootSteps = 1024, kImproveSteps = 256;
     int root_steps = 0, found_at = 0;
     bool abandoned = false;
     for (int step = 0; step < steps; ++step) {
@@ -901,16 +901,16 @@ __global__ void __launch_bounds__(kTpb) k_dive(TopoArgs topo, PatternArgs pat, G
         int32_t inc;
         bool found;
         int rec_v;
-        const int my_steps = anytime ? max(steps, 256 * pat.k) : steps;
+        const int my_steps = anytime ? max(steps, 128 * pat.k) : steps;
         const bool done = dive_warp<W, CT>(s, pat, L0.S[i], F, al, be, lane, my_steps, anytime, q.root_lo, q.root_hi,
                                            inc, found, rec_v);
         // a finished dive without a match proves there is none (cut every
         // partial, in either mode); a found score seeds the cut-offs of the
         // bounded mode only (an exhaustive request must count every match)
-        if (lane == 0 && !fallback) {
-            g.thr[i] = found ? inc : (done ? INT_MAX : INT_MIN);
-            if (g.seed_thr) g.seed_thr[i] = g.thr[i];
-        }
+        if (lane == 0 && !fallback) g.thr[i] = found ? inc : (done ? INT_MAX : INT_MIN);
+        // a fallback dive that finished its whole search without a match
+        // proves there is none: the request is a no-fit, not a budget end
+        if (fallback && done && !found && lane == 0) g.dive_s[i] = kDiveNoMatch;
         if (anytime && found) {
 #pragma unroll
             for (int w = 0; w < 8; ++w) {
@@ -933,7 +933,7 @@ __global__ void __launch_bounds__(kTpb) k_dive(TopoArgs topo, PatternArgs pat, G
 // work budget marks requests while deeper levels of earlier chunks run), and
 // the write pass must produce exactly the children counted here.
 template <int W>
-__global__ void __launch_bounds__(kTpb) k_count(TopoArgs topo, LevelView in, uint64_t P, uint32_t back, uint32_t lo,
+__global__ void __launch_bounds__(kTpb, W >= 4 ? 4 : 1) k_count(TopoArgs topo, LevelView in, uint64_t P, uint32_t back, uint32_t lo,
                                                 uint32_t *warp_cnt, unsigned long long *blk_cnt, const int32_t *thr,
                                                 const int32_t *alpha, const int32_t *beta, LevelBound lbd,
                                                 uint32_t *cut_bits) {
@@ -1056,7 +1056,7 @@ __device__ __forceinline__ void parent_state(const SmemTopo &s, const LevelView 
 
 // Write pass of the host-driven (chunked) path.
 template <int W, int CT>
-__global__ void __launch_bounds__(kTpb) k_write(TopoArgs topo, LevelView in, uint64_t P, int ell, uint32_t back,
+__global__ void __launch_bounds__(kTpb, W >= 4 ? 4 : 1) k_write(TopoArgs topo, LevelView in, uint64_t P, int ell, uint32_t back,
                                                 uint32_t lo, LevelView out, const uint32_t *warp_cnt,
                                                 const unsigned long long *blk_off, uint64_t blk_first,
                                                 const int32_t *alpha, const int32_t *beta, const int32_t *thr,
@@ -1995,13 +1995,15 @@ __global__ void k_finalize(TopoArgs topo, PatternArgs pat, GroupArgs g) {
         // ones they are depends on the other requests sharing its chunks,
         // while the dive depends on the request alone.)
         const bool over = state >= 0 && g.work && g.work[i] > g.work_budget;
+        bool proven_none = false;
         const uint32_t *tw = g.best_t + static_cast<uint64_t>(i) * 8;
         int32_t want = g.best_s[i];
         bool have = state == 1;
         if (over) {
             res.count = 0;
             const bool anytime = (q.policy.flags & MAPA_POLICY_ANYTIME) && g.dive_s && !g.sens;
-            have = anytime && g.dive_s[i] != INT_MIN;
+            proven_none = anytime && g.dive_s[i] == kDiveNoMatch;
+            have = anytime && g.dive_s[i] != INT_MIN && !proven_none;
             if (have) {
                 tw = g.dive_t + static_cast<uint64_t>(i) * 8;
                 want = g.dive_s[i];
@@ -2013,6 +2015,8 @@ __global__ void k_finalize(TopoArgs topo, PatternArgs pat, GroupArgs g) {
         } else if (state == -3) {
             res.status = MAPA_E_INVALID;
             res.count = 0;
+        } else if (over && proven_none) {
+            res.status = MAPA_NO_FIT;
         } else if (over && !have) {
             res.status = MAPA_E_BUDGET;
         } else if (!over && q.policy.max_embeddings > 0 && res.count > q.policy.max_embeddings) {

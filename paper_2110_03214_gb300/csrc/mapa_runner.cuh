@@ -31,7 +31,13 @@ struct LayoutPlan {
 };
 
 int plan_layout(Engine *e, int slot, int32_t group_size, int k, int T, int W, bool device_mode, int n,
-                LayoutPlan *lay, std::string *err);
+                LayoutPlan *lay, std::string *err, uint64_t max_entries = 0);
+
+// Tuned level-size limit of a (topology, pattern) (0 = none).
+inline uint64_t chunk_limit(const Engine *e, int32_t topo_id, int32_t pattern_id) {
+    const auto it = e->chunk_table.find({topo_id, pattern_id});
+    return it == e->chunk_table.end() ? 0 : it->second;
+}
 void launch_scan(const unsigned long long *cnt, unsigned long long *off, uint64_t nb, cudaStream_t s);
 
 inline TailArgs make_tail_args(const PatternArgs &pat, int T, int W, int C) {
@@ -133,11 +139,11 @@ struct Runner {
 
     int setup(unsigned long long *count0) {
         const unsigned sgrid = static_cast<unsigned>(std::min<uint64_t>(ceil_div(g.size, kWarps), 4096));
-        k_setup<W><<<sgrid, kTpb, smem_all, st>>>(targs, g, lay.level[0], count0, gr.redo ? 1 : 0);
+        k_setup<W><<<sgrid, kTpb, smem_all, st>>>(targs, g, lay.level[0], count0);
         MAPA_CUDA_TRY(cudaGetLastError());
         e->st.kernel_launches += 1;
         MAPA_CUDA_TRY(cudaGetLastError());
-        if (gr.bounded && !gr.sens && !gr.redo) {
+        if (gr.bounded && !gr.sens) {
             // bounded mode: seed scores for the cut-offs (and the fallback
             // match of anytime requests); one warp per request, others skip
             const unsigned dgrid = static_cast<unsigned>(std::min<uint64_t>(ceil_div(g.size, kWarps), 4096));
@@ -244,7 +250,7 @@ struct Runner {
     int run_device() {
         int rc = allow_smem();
         if (rc != MAPA_OK) return rc;
-        rc = plan_layout(e, gr.slot, g.size, pat.k, T, W, true, t.n, &lay, err);
+        rc = plan_layout(e, gr.slot, g.size, pat.k, T, W, true, t.n, &lay, err, chunk_limit(e, t.id, pat.id));
         if (rc != MAPA_OK) return rc;
         MAPA_CUDA_TRY(cudaMemsetAsync(lay.ctrl, 0, lay.ctrl_bytes, st));
         rc = setup(lay.counts);
@@ -352,7 +358,7 @@ struct Runner {
     int run_host() {
         int rc = allow_smem();
         if (rc != MAPA_OK) return rc;
-        rc = plan_layout(e, gr.slot, g.size, pat.k, T, W, false, t.n, &lay, err);
+        rc = plan_layout(e, gr.slot, g.size, pat.k, T, W, false, t.n, &lay, err, chunk_limit(e, t.id, pat.id));
         if (rc != MAPA_OK) return rc;
         rc = setup(nullptr);
         if (rc != MAPA_OK) return rc;

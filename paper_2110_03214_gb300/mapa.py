@@ -158,6 +158,7 @@ def _load() -> ctypes.CDLL:
         "mapa_ctx_set_work_budget": ([vp, u64], ctypes.c_int),
         "mapa_measure_int_peak": ([vp, i32, ctypes.POINTER(ctypes.c_double)], ctypes.c_int),
         "mapa_result_merge": ([i32, vp, vp], ctypes.c_int),
+        "mapa_autotune_level_limit": ([vp, i32, i32, ctypes.POINTER(ctypes.c_uint64)], ctypes.c_int),
         "mapa_serve_open": ([vp, i32, i32, u32, ctypes.POINTER(vp)], ctypes.c_int),
         "mapa_serve_submit": ([vp, vp, i32], ctypes.c_int),
         "mapa_serve_poll": ([vp, vp, i32, ctypes.POINTER(ctypes.c_int32), i32], ctypes.c_int),
@@ -187,7 +188,7 @@ SYMBOLS = (
     "mapa_ctx_set_timing", "mapa_allocate_batch_noalloc", "mapa_serve_open", "mapa_serve_submit",
     "mapa_serve_poll", "mapa_serve_drain", "mapa_serve_counters", "mapa_serve_close", "mapa_autotune",
     "mapa_effbw_predict", "mapa_simulate", "mapa_ctx_set_work_budget", "mapa_measure_int_peak",
-    "mapa_result_merge",
+    "mapa_result_merge", "mapa_autotune_level_limit",
 )
 
 
@@ -320,6 +321,12 @@ def mapa_stats_reset(ctx) -> None:
 
 def mapa_ctx_set_timing(ctx, on: bool) -> None:
     _check(ctx, lib.mapa_ctx_set_timing(ctx, 1 if on else 0))
+
+
+def mapa_autotune_level_limit(ctx, topo_id: int, pattern_id: int) -> int:
+    out = ctypes.c_uint64()
+    _check(ctx, lib.mapa_autotune_level_limit(ctx, topo_id, pattern_id, ctypes.byref(out)))
+    return int(out.value)
 
 
 def mapa_result_merge(parts) -> np.ndarray:

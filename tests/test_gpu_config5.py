@@ -295,3 +295,25 @@ def test_budget_with_chunked_frontier(M):
     assert np.array_equal(out[0], out[1])
     statuses = set(int(x) for x in out[0]["status"])
     assert {M.MAPA_INEXACT, M.MAPA_NO_FIT} <= statuses
+
+
+@pytest.mark.parametrize("mode", [0, 1])
+def test_anytime_with_shared_group_arrays(M, mode):
+    """With per-kernel timing on, the pattern groups of a batch run one after
+    another in one slot, sharing its per-request arrays, as they do whenever
+    a batch has more groups than slots; an overflowed group redone on the
+    chunked path must not see another group's state.  The anytime results
+    under the work budget equal those of the concurrent run."""
+    wl = W.workload("boards256", num_requests=300)
+    with M.Context(0) as ctx:
+        tid = ctx.topology_load(wl.topology)
+        pids = [ctx.pattern_load(p) for p in wl.requests.patterns]
+        reqs = ctx.requests(wl.requests, pids, mode=mode)
+        reqs["flags"] |= M.MAPA_POLICY_ANYTIME
+        ctx.set_work_budget(1 << 20)
+        want = ctx.allocate_batch(tid, reqs)
+        ctx.set_timing(True)
+        got = ctx.allocate_batch(tid, reqs)
+        ctx.set_timing(False)
+    assert np.array_equal(got, want)
+    assert int((want["status"] == M.MAPA_INEXACT).sum()) > 0
