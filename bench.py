@@ -281,13 +281,13 @@ def _oracle_sample(wl, budget_s: float, threads: int, start: int = 0, max_nodes:
 
 
 def _oracle_node_cap(settings) -> int:
-    """Search-node cap of the oracle's timed sample when the GPU runs under a
-    work budget: 2^22 nodes per request (one to two seconds of one host core
-    on the 256-vertex graph), so the sample stays within its time limit.  The
-    oracle enumerates every map (no symmetry breaking), so this is less
-    search than the GPU's budget allows; the figure is matches scored per
-    second either way."""
-    return 1 << 22 if settings["work_budget"] else 0
+    """Search-node cap of the oracle's timed sample: 2^22 nodes per request
+    under a GPU work budget (one to two seconds of one host core on the
+    256-vertex graph), 2^26 otherwise (a request with a large search space,
+    such as ring-16 on an idle torus, would run for hours), so the sample
+    stays within its time limit.  A capped request still counts the matches
+    it scored; the figure is matches scored (or decisions) per second."""
+    return 1 << 22 if settings["work_budget"] else 1 << 26
 
 
 def shard_workload(W, name: str, num_requests, rank: int):

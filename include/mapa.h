@@ -116,7 +116,7 @@ enum mapa_policy_flags { MAPA_POLICY_BW_SENSITIVE = 1u, MAPA_POLICY_ANYTIME = 2u
  * enumeration, for the requests past the budget only), with status
  * MAPA_INEXACT, its
  * score, AggBW and PreservedBW recomputed from the tuple, count 0.  For such
- * a request the dive runs up to 128 k steps and is guided towards a match
+ * a request the dive runs up to 256 k steps and is guided towards a match
  * rather than a high score: candidates that violate two necessary conditions
  * of any match are skipped (the image of pattern vertex j lies within its
  * pattern distance from phi(0) in the free graph, and has at least as many

@@ -901,7 +901,7 @@ __global__ void __launch_bounds__(kTpb) k_dive(TopoArgs topo, PatternArgs pat, G
         int32_t inc;
         bool found;
         int rec_v;
-        const int my_steps = anytime ? max(steps, 128 * pat.k) : steps;
+        const int my_steps = anytime ? max(steps, 256 * pat.k) : steps;
         const bool done = dive_warp<W, CT>(s, pat, L0.S[i], F, al, be, lane, my_steps, anytime, q.root_lo, q.root_hi,
                                            inc, found, rec_v);
         // a finished dive without a match proves there is none (cut every

@@ -399,6 +399,14 @@ inline int dispatch_group(Engine *e, const TopoDevice &t, const GroupRun &gr, bo
             case 3: return dispatch_tail<W, 3>(e, t, gr, device, err);
             default: break;
         }
+    } else {
+        // wider masks: the two- and three-class graphs (the dragonfly and
+        // boards workloads) get unrolled score increments too
+        switch (t.C) {
+            case 2: return dispatch_tail<W, 2>(e, t, gr, device, err);
+            case 3: return dispatch_tail<W, 3>(e, t, gr, device, err);
+            default: break;
+        }
     }
     return dispatch_tail<W, 0>(e, t, gr, device, err);
 }
