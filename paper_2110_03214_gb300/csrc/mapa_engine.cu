@@ -264,6 +264,7 @@ Engine *engine_create(int device, uint64_t frontier_cap, std::string *err) {
     if (const char *ov = std::getenv("MAPA_TAIL_BLOCKS_PER_SM")) en->tail_blocks_per_sm = std::atoi(ov);
     if (const char *ov = std::getenv("MAPA_GRAPHS")) en->use_graphs = std::atoi(ov) != 0;
     if (const char *ov = std::getenv("MAPA_TAIL_SORT")) en->tail_sorted = std::atoi(ov) != 0;
+    if (const char *ov = std::getenv("MAPA_CHUNK_SINGLE_PASS")) en->chunk_single_pass = std::atoi(ov) != 0;
     if (const char *ov = std::getenv("MAPA_DIVE_STEPS")) en->dive_steps = std::max(0, std::min(std::atoi(ov), 1 << 20));
     if (const char *ov = std::getenv("MAPA_BOUND_DEGREE_MIN_M")) en->degree_min_m = std::max(0, std::atoi(ov));
     if (cudaStreamCreateWithFlags(&en->own_stream, cudaStreamNonBlocking) != cudaSuccess ||
@@ -360,7 +361,7 @@ int plan_layout(Engine *e, int slot, int32_t group_size, int k, int T, int W, bo
     const uint64_t lvl0 = static_cast<uint64_t>(std::max(group_size, 1));
     uint64_t per_entry = 0;
     for (int ell = 1; ell <= lay->L; ++ell) per_entry += entry_bytes(ell, W);
-    const uint64_t scr_x1024 = device_mode ? 32 : 176;  // control bytes per 1024 entries of a level
+    const uint64_t scr_x1024 = device_mode ? 32 : 208;  // control bytes per 1024 entries of a level
     const uint64_t fixed = lvl0 * entry_bytes(0, W) + (lvl0 / 256 + 4) * 48 + 64 * 1024 + 4096 * (lay->L + 2);
     uint64_t E = 0;
     if (lay->L >= 1) {
@@ -413,8 +414,13 @@ int plan_layout(Engine *e, int slot, int32_t group_size, int k, int T, int W, bo
     const uint64_t off_counts = bump(8ull * (lay->L + 1));
     const uint64_t off_tiles = bump(4ull * (lay->L + 1));
     uint64_t off_status[kMaxK + 1];
-    if (device_mode)
-        for (int ell = 0; ell < lay->L; ++ell) off_status[ell] = bump(8ull * (lay->bound[ell] / kTpb + 2));
+    // look-back status words: device mode sized by the level bound, host
+    // mode (chunks of at most a level's capacity) by the capacity
+    for (int ell = 0; ell < lay->L; ++ell) {
+        const uint64_t c = device_mode ? lay->bound[ell] : (ell == 0 ? lvl0 : E);
+        off_status[ell] = bump(8ull * (c / kTpb + 2));
+    }
+    const uint64_t off_hctrl = bump(32ull * (lay->L + 1));
     const uint64_t ctrl_end = total;
     Slot &sl = e->slots[slot];
     uint64_t have = sl.arena_bytes;
@@ -437,9 +443,9 @@ int plan_layout(Engine *e, int slot, int32_t group_size, int k, int T, int W, bo
             lay->blk_off[ell] = reinterpret_cast<unsigned long long *>(base + off_scr[ell][2]);
             lay->cut_bits[ell] = reinterpret_cast<uint32_t *>(base + off_scr[ell][3]);
         }
-        if (device_mode && ell < lay->L)
-            lay->status[ell] = reinterpret_cast<unsigned long long *>(base + off_status[ell]);
+        if (ell < lay->L) lay->status[ell] = reinterpret_cast<unsigned long long *>(base + off_status[ell]);
     }
+    lay->hctrl = reinterpret_cast<unsigned long long *>(base + off_hctrl);
     lay->counts = reinterpret_cast<unsigned long long *>(base + off_counts);
     lay->tiles = reinterpret_cast<unsigned int *>(base + off_tiles);
     lay->ctrl = base + ctrl_begin;

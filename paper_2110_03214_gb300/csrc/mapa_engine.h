@@ -70,6 +70,7 @@ struct Engine {
     int dive_steps = 32;         // bounded mode: node expansions of a request's seed dive
     int degree_min_m = 6;        // bounded mode: degree term only where >= this many pattern vertices remain
     uint64_t work_budget = 0;    // stored partial matches a request may produce (0 = no limit)
+    bool chunk_single_pass = true;  // chunked levels by single-pass k_expand (MAPA_CHUNK_SINGLE_PASS=0: count + write)
     bool tail_sorted = false;    // short fused tail: parents of a tile ordered by estimated subtree size (MAPA_TAIL_SORT=1)
     std::map<std::pair<int32_t, int32_t>, int> tail_table;  // (topology, pattern) -> tuned depth
     // (topology, pattern) -> tuned largest entries of a stored level (0 = as

@@ -1149,8 +1149,17 @@ __global__ void __launch_bounds__(kTpb) k_expand(TopoArgs topo, LevelView in, Le
                                                  const int32_t *alpha, const int32_t *beta, int32_t *err,
                                                  unsigned long long *stats, unsigned long long child_bytes,
                                                  unsigned long long parent_bytes, const int32_t *thr,
-                                                 LevelBound lbd) {
-    const unsigned long long P = *count_in;
+                                                 LevelBound lbd, unsigned long long count_host, uint64_t p0,
+                                                 unsigned int *stop, unsigned long long *resume) {
+    // Chunked use (host-driven path; stop and resume non-null): the P
+    // parents from p0 on are expanded tile by tile until the children no
+    // longer fit; the first tile that does not fit records (tile << 32 |
+    // children written before it) in *resume (atomicMin) and lowers *stop.
+    // A tile picked after that skips its parents but still takes part in
+    // the look-back, with a total of cap_out + 1, so no later tile fits and
+    // none waits on it.  The written tiles are a prefix of the range, so
+    // the host continues from the first unwritten parent.
+    const unsigned long long P = count_in ? *count_in : count_host;
     const unsigned long long ntiles = (P + kTpb - 1) / kTpb;
     if (ntiles == 0) {
         if (blockIdx.x == 0 && threadIdx.x == 0) *count_out = 0ull;
@@ -1159,23 +1168,28 @@ __global__ void __launch_bounds__(kTpb) k_expand(TopoArgs topo, LevelView in, Le
     if (static_cast<unsigned long long>(blockIdx.x) >= ntiles) return;  // no tile will be left for this block
     const SmemTopo s = stage_topology<W>(topo, true);
     __shared__ unsigned int s_tile;
+    __shared__ int s_skip;
     __shared__ int s_wtot[kWarps];
     __shared__ unsigned long long s_excl;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     for (;;) {
-        if (threadIdx.x == 0) s_tile = atomicAdd(tile_ctr, 1u);
+        if (threadIdx.x == 0) {
+            s_tile = atomicAdd(tile_ctr, 1u);
+            s_skip = stop != nullptr && s_tile > *reinterpret_cast<volatile unsigned int *>(stop);
+        }
         __syncthreads();
         const unsigned long long t = s_tile;
         if (t >= ntiles) break;
-        const uint64_t p = t * kTpb + threadIdx.x;
+        const bool skip = s_skip != 0;  // past a tile that did not fit
+        const uint64_t p = p0 + t * kTpb + threadIdx.x;
         uint32_t cand[W], B[W], R[W];
         int32_t S = 0;
         uint32_t r = 0;
 #pragma unroll
         for (int w = 0; w < W; ++w) cand[w] = B[w] = R[w] = 0u;
         int32_t al = 0, be = 0;
-        if (p < P) {
-            parent_state<W>(s, in, p, back, lo, cand, B, R, S, r);
+        if (p < p0 + P && !skip) {
+            parent_state<W>(s, in, static_cast<uint32_t>(p), back, lo, cand, B, R, S, r);
             al = alpha[r];
             be = beta[r];
             if constexpr (Bnd) {
@@ -1198,14 +1212,19 @@ __global__ void __launch_bounds__(kTpb) k_expand(TopoArgs topo, LevelView in, Le
             ttot += v;
         }
         if (warp == 0) {
-            const unsigned long long ex = look_back(status, t, static_cast<unsigned long long>(ttot), lane, err);
+            const unsigned long long agg = skip ? cap_out + 1 : static_cast<unsigned long long>(ttot);
+            const unsigned long long ex = look_back(status, t, agg, lane, err);
             if (lane == 0) s_excl = ex;
         }
         __syncthreads();
         const unsigned long long excl = s_excl;
-        const bool fits = excl + static_cast<unsigned long long>(ttot) <= cap_out;
+        const bool fits = !skip && excl + static_cast<unsigned long long>(ttot) <= cap_out;
         if (threadIdx.x == 0) {
-            if (!fits) atomicExch(overflow, 1);
+            if (!fits && overflow) atomicExch(overflow, 1);
+            if (!fits && resume) {
+                atomicMin(resume, (t << 32) | min(excl, 0xFFFFFFFFull));
+                atomicMin(stop, static_cast<unsigned int>(t));
+            }
             if (t == ntiles - 1) {
                 const unsigned long long total = excl + static_cast<unsigned long long>(ttot);
                 *count_out = fits ? total : 0ull;
@@ -1217,8 +1236,8 @@ __global__ void __launch_bounds__(kTpb) k_expand(TopoArgs topo, LevelView in, Le
             }
         }
         if (fits)
-            emit_children<W, CT>(s, in, out, ell, t * kTpb + static_cast<uint64_t>(warp) * 32, lane, cand, B, R, S, r,
-                                 cnt, incl, wtot, excl + woff, alpha, beta);
+            emit_children<W, CT>(s, in, out, ell, p0 + t * kTpb + static_cast<uint64_t>(warp) * 32, lane, cand, B, R,
+                                 S, r, cnt, incl, wtot, excl + woff, alpha, beta);
         __syncthreads();
     }
 }

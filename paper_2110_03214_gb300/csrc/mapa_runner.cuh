@@ -25,6 +25,9 @@ struct LayoutPlan {
     unsigned long long *counts = nullptr;   // [L + 1]
     unsigned int *tiles = nullptr;          // [L + 1]
     unsigned long long *status[kMaxK + 1];  // [bound_l / kTpb + 2] per level l < L
+    // host-driven single-pass chunks, per level: tile counter, stop tile,
+    // resume record, child count (4 words)
+    unsigned long long *hctrl = nullptr;
     uint64_t bound[kMaxK + 1];              // upper bound on the entries of level l (<= its capacity)
     char *ctrl = nullptr;                   // contiguous control region (zeroed per run)
     uint64_t ctrl_bytes = 0;
@@ -269,7 +272,8 @@ struct Runner {
             expand<<<grid, kTpb, smem_all, st>>>(
                 targs, lay.level[ell], lay.level[ell + 1], ell, pat.back[ell], pat.lo[ell], lay.counts + ell,
                 lay.counts + ell + 1, lay.level[ell + 1].cap, lay.tiles + ell, lay.status[ell], gr.overflow, g.alpha,
-                g.beta, e->d_error, e->d_stats, entry_bytes(ell + 1, W), entry_bytes(ell, W), g.thr, bound_at(ell));
+                g.beta, e->d_error, e->d_stats, entry_bytes(ell + 1, W), entry_bytes(ell, W), g.thr, bound_at(ell),
+                0ull, 0, nullptr, nullptr);
             MAPA_CUDA_TRY(cudaGetLastError());
             if (e->timing) MAPA_CUDA_TRY(cudaEventRecord(ev1, st));
             e->st.kernel_launches += 1;
@@ -280,6 +284,71 @@ struct Runner {
         rc = last_level(lay.counts + lay.L, 0ull, lay.tiles + lay.L, lay.bound[lay.L]);
         if (rc != MAPA_OK) return rc;
         return finalize();
+    }
+
+    // ---- host-driven, single pass per chunk: k_expand writes the children
+    // of a prefix of the parents [p0, p0 + P) that fits the level capacity
+    // and reports where it stopped; that chunk is descended depth first,
+    // then the level continues from the first unwritten parent.  Parents are
+    // read once (a tile that did not fit is read again in the next chunk).
+    int process_sp(int ell, uint64_t P) {
+        if (P == 0) return MAPA_OK;
+        if (ell == lay.L) {
+            MAPA_CUDA_TRY(cudaMemsetAsync(lay.tiles, 0, sizeof(unsigned int), st));
+            return last_level(nullptr, P, lay.tiles, P);
+        }
+        const LevelView &in = lay.level[ell];
+        const LevelView &out = lay.level[ell + 1];
+        unsigned long long *ctl = lay.hctrl + 4 * ell;  // tile counter, stop, resume, child count
+        static int nb_expand = 0;
+        if (!nb_expand) nb_expand = blocks_per_sm(k_expand<W, CT, false>, smem_all);
+        auto expand = g.thr ? k_expand<W, CT, true> : k_expand<W, CT, false>;
+        uint64_t p0 = 0;
+        while (p0 < P) {
+            const uint64_t pc = P - p0;
+            const uint64_t nt = ceil_div(pc, kTpb);
+            MAPA_CUDA_TRY(cudaMemsetAsync(lay.status[ell], 0, 8 * (nt + 2), st));
+            MAPA_CUDA_TRY(cudaMemsetAsync(ctl, 0, 8, st));
+            MAPA_CUDA_TRY(cudaMemsetAsync(ctl + 1, 0xFF, 16, st));
+            const unsigned grid = static_cast<unsigned>(
+                std::max<uint64_t>(1, std::min<uint64_t>(nt, uint64_t(e->sm_count) * nb_expand)));
+            cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+            if (e->timing) {
+                e->timed_pair(1, &ev0, &ev1);
+                MAPA_CUDA_TRY(cudaEventRecord(ev0, st));
+            }
+            expand<<<grid, kTpb, smem_all, st>>>(
+                targs, in, out, ell, pat.back[ell], pat.lo[ell], nullptr, ctl + 3, out.cap,
+                reinterpret_cast<unsigned int *>(ctl), lay.status[ell], nullptr, g.alpha, g.beta, e->d_error, nullptr,
+                entry_bytes(ell + 1, W), entry_bytes(ell, W), g.thr, bound_at(ell), pc, p0,
+                reinterpret_cast<unsigned int *>(ctl + 1), ctl + 2);
+            MAPA_CUDA_TRY(cudaGetLastError());
+            if (e->timing) MAPA_CUDA_TRY(cudaEventRecord(ev1, st));
+            MAPA_CUDA_TRY(
+                cudaMemcpyAsync(e->h_pinned, ctl + 2, 2 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, st));
+            MAPA_CUDA_TRY(cudaStreamSynchronize(st));
+            const unsigned long long resume = e->h_pinned[0], written_all = e->h_pinned[1];
+            uint64_t consumed = pc, children = written_all;
+            if (resume != ~0ull) {
+                consumed = (resume >> 32) * kTpb;
+                children = resume & 0xFFFFFFFFull;
+            }
+            if (consumed == 0) {
+                if (err) *err = "internal: one tile's children exceed the level capacity";
+                return MAPA_E_NOMEM;
+            }
+            e->st.kernel_launches += 1;
+            e->st.expand_launches += 1;
+            e->st.spill_entries += children;
+            e->st.spill_bytes += 2 * children * entry_bytes(ell + 1, W);
+            e->st.expand_bytes += consumed * entry_bytes(ell, W) + children * entry_bytes(ell + 1, W);
+            int rc = budget(out, nullptr, children);
+            if (rc != MAPA_OK) return rc;
+            rc = process_sp(ell + 1, children);
+            if (rc != MAPA_OK) return rc;
+            p0 += consumed;
+        }
+        return MAPA_OK;
     }
 
     // ---- host-driven: counts read back per level, children produced in
@@ -362,7 +431,8 @@ struct Runner {
         if (rc != MAPA_OK) return rc;
         rc = setup(nullptr);
         if (rc != MAPA_OK) return rc;
-        rc = process(0, static_cast<uint64_t>(g.size));
+        rc = e->chunk_single_pass ? process_sp(0, static_cast<uint64_t>(g.size))
+                                  : process(0, static_cast<uint64_t>(g.size));
         if (rc != MAPA_OK) return rc;
         return finalize();
     }
