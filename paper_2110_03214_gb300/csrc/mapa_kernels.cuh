@@ -1142,7 +1142,7 @@ __device__ __forceinline__ unsigned long long look_back(unsigned long long *stat
 // the capacity is written, *count_out = 0 and *overflow = 1 (the host then
 // redoes the group with the chunked path).
 template <int W, int CT, bool Bnd>
-__global__ void __launch_bounds__(kTpb) k_expand(TopoArgs topo, LevelView in, LevelView out, int ell, uint32_t back,
+__global__ void __launch_bounds__(kTpb, W >= 4 ? 4 : 1) k_expand(TopoArgs topo, LevelView in, LevelView out, int ell, uint32_t back,
                                                  uint32_t lo, const unsigned long long *count_in,
                                                  unsigned long long *count_out, unsigned long long cap_out,
                                                  unsigned int *tile_ctr, unsigned long long *status, int32_t *overflow,
