@@ -461,15 +461,23 @@ __device__ __forceinline__ bool cut_off_warp(const SmemTopo &s, const uint32_t (
 #pragma unroll
     for (int w = 0; w < W; ++w)
         if ((R[w] >> lane) & 1u) keep4(t, twice_floor_loss<W>(s, R, 32 * w + lane, cap));
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        int32_t other[4];
-#pragma unroll
-        for (int j = 0; j < 4; ++j) other[j] = __shfl_xor_sync(kFull, t[j], o);
-#pragma unroll
-        for (int j = 0; j < 4; ++j) keep4(t, other[j]);
+    // the four smallest of the warp: each round takes the least head of the
+    // lanes' sorted lists and pops it from the lowest lane holding it (the
+    // same multiset as merging the lists pairwise)
+    int32_t low[4] = {INT_MAX, INT_MAX, INT_MAX, INT_MAX};
+    const int rounds = min(lb.m, 4);
+    for (int j = 0; j < rounds; ++j) {
+        const int32_t m = __reduce_min_sync(kFull, t[0]);
+        low[j] = m;
+        const uint32_t holders = __ballot_sync(kFull, t[0] == m);
+        if (lane == __ffs(holders) - 1) {
+            t[0] = t[1];
+            t[1] = t[2];
+            t[2] = t[3];
+            t[3] = INT_MAX;
+        }
     }
-    return cut_second(base2, be, t, lb.m, thr);
+    return cut_second(base2, be, low, lb.m, thr);
 }
 
 // ----------------------------------------------------------------------------
@@ -621,6 +629,10 @@ static __global__ void k_budget(LevelView lv, const unsigned long long *count_de
     if (P == 0ull) return;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < g.size; i += gridDim.x * blockDim.x) {
         auto first_at_least = [&](uint32_t key) {
+            // the ends first: a group of one request (a served chain step)
+            // needs no search at all
+            if (lv.r[P - 1] < key) return P;
+            if (lv.r[0] >= key) return 0ull;
             unsigned long long lo = 0ull, hi = P;
             while (lo < hi) {
                 const unsigned long long mid = (lo + hi) >> 1;
@@ -782,16 +794,14 @@ __device__ bool dive_warp(const SmemTopo &s, const PatternArgs &pat, int32_t S0,
                     broom = room;
                 }
             }
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-            const int32_t ob = __shfl_xor_sync(kFull, best, o);
-            const int ov = __shfl_xor_sync(kFull, bv, o);
-            const int orr = __shfl_xor_sync(kFull, broom, o);
-            if (orr > broom || (orr == broom && (ob > best || (ob == best && ov < bv)))) {
-                best = ob;
-                bv = ov;
-                broom = orr;
-            }
+        // the warp's pick: most room, then best score, then smaller vertex
+        // (lanes without a child hold room -1)
+        {
+            const int mr = __reduce_max_sync(kFull, broom);
+            const int32_t ms = __reduce_max_sync(kFull, broom == mr ? best : INT_MIN);
+            bv = __reduce_min_sync(kFull, (broom == mr && best == ms) ? bv : INT_MAX);
+            best = ms;
+            broom = mr;
         }
         if (lane == j) {
             clear_bit<W>(my_rem, bv);
@@ -1996,11 +2006,15 @@ __device__ __forceinline__ int32_t link_weight(const SmemTopo &s, int W, int x, 
 
 // Writes every request's result: the chosen tuple's AggBW (Eq. 1) and
 // PreservedBW (Eq. 3) recomputed from their definitions on the bitsets and
-// checked against the enumerated score.
+// checked against the enumerated score.  One warp per request: the lanes
+// split the scan of the free set behind PreservedBW, lane 0 writes.
 template <int W>
 __global__ void k_finalize(TopoArgs topo, PatternArgs pat, GroupArgs g) {
     const SmemTopo s = stage_topology<W>(topo, true);
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < g.size; i += gridDim.x * blockDim.x) {
+    const int lane = threadIdx.x & 31;
+    const int gw = static_cast<int>((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+    const int nw = static_cast<int>((gridDim.x * blockDim.x) >> 5);
+    for (int i = gw; i < g.size; i += nw) {
         const int32_t bi = g.req_index[i];
         const mapa_request &q = g.reqs[bi];
         mapa_result res;
@@ -2063,7 +2077,7 @@ __global__ void k_finalize(TopoArgs topo, PatternArgs pat, GroupArgs g) {
             }
             for (int j = 0; j < pat.k; ++j) clear_bit<W>(rem, t[j]);
             long long twice = 0;
-            for (int v = 0; v < s.n; ++v) {
+            for (int v = lane; v < s.n; v += 32) {
                 if (!((rem[v >> 5] >> (v & 31)) & 1u)) continue;
                 const uint32_t *x = s.cls + static_cast<size_t>(v) * s.C * W;
                 for (int c = 0; c < s.C; ++c) {
@@ -2073,6 +2087,8 @@ __global__ void k_finalize(TopoArgs topo, PatternArgs pat, GroupArgs g) {
                     twice += static_cast<long long>(s.wc[c]) * pc;
                 }
             }
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) twice += __shfl_xor_sync(kFull, twice, o);
             const long long pres = twice / 2;
             res.status = over ? MAPA_INEXACT : MAPA_OK;
             if (g.sens) {
@@ -2084,12 +2100,12 @@ __global__ void k_finalize(TopoArgs topo, PatternArgs pat, GroupArgs g) {
                         const int c = link_class(s, W, t[__ffs(m) - 1], t[v]);
                         if (c >= 0) idx += g.effbw_code[c];
                     }
-                if (g.effbw_rank[idx] != g.best_s[i]) atomicExch(g.error, kDevScoreMismatch);
+                if (lane == 0 && g.effbw_rank[idx] != g.best_s[i]) atomicExch(g.error, kDevScoreMismatch);
                 res.score = g.effbw_milli[idx];
             } else {
                 const long long score =
                     static_cast<long long>(g.alpha[i]) * agg + static_cast<long long>(g.beta[i]) * pres;
-                if (score != want) atomicExch(g.error, kDevScoreMismatch);
+                if (lane == 0 && score != want) atomicExch(g.error, kDevScoreMismatch);
                 res.score = want;
             }
             res.agg = static_cast<int32_t>(agg);
@@ -2097,7 +2113,7 @@ __global__ void k_finalize(TopoArgs topo, PatternArgs pat, GroupArgs g) {
             for (int j = 0; j < pat.k; ++j) res.verts[j] = t[j];
         }
         if (q.policy.mode == MAPA_MODE_BOUNDED) res.count = 0;
-        g.out[bi] = res;
+        if (lane == 0) g.out[bi] = res;
     }
 }
 

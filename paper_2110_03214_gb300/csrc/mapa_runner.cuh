@@ -177,7 +177,7 @@ struct Runner {
             MAPA_CUDA_TRY(cudaGetLastError());
             e->st.kernel_launches += 1;
         }
-        const unsigned fgrid = static_cast<unsigned>(std::min<uint64_t>(ceil_div(g.size, 128), 4096));
+        const unsigned fgrid = static_cast<unsigned>(std::min<uint64_t>(ceil_div(g.size, 4), 4096));
         k_finalize<W><<<fgrid, 128, smem_all, st>>>(t.args(), pat, g);  // real weights: AggBW, PreservedBW
         MAPA_CUDA_TRY(cudaGetLastError());
         e->st.kernel_launches += 1;

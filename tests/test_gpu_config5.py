@@ -317,3 +317,24 @@ def test_anytime_with_shared_group_arrays(M, mode):
         ctx.set_timing(False)
     assert np.array_equal(got, want)
     assert int((want["status"] == M.MAPA_INEXACT).sum()) > 0
+
+
+def test_budget_size_does_not_change_the_boards_decisions(M):
+    """On the boards stream no ring-32 or tree-31 enumeration finishes within
+    a work budget of 2^16 or of 2^20 partial matches, and every clique-8
+    no-fit is proven far below either: the two budgets give the same result
+    for every request (the benchmark's boards line runs at 2^16)."""
+    wl = W.workload("boards256", num_requests=300)
+    with M.Context(0) as ctx:
+        tid = ctx.topology_load(wl.topology)
+        pids = [ctx.pattern_load(p) for p in wl.requests.patterns]
+        reqs = ctx.requests(wl.requests, pids)
+        reqs["flags"] |= M.MAPA_POLICY_ANYTIME
+        got = []
+        for b in (1 << 16, 1 << 20):
+            ctx.set_work_budget(b)
+            got.append(ctx.allocate_batch(tid, reqs))
+        ctx.set_work_budget(0)
+    assert np.array_equal(got[0], got[1])
+    st = got[0]["status"]
+    assert int((st == M.MAPA_INEXACT).sum()) > 50 and int((st == M.MAPA_NO_FIT).sum()) >= 90
