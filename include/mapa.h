@@ -276,13 +276,20 @@ int mapa_result_merge(int32_t nparts, const mapa_result *parts, mapa_result *out
  * and the requests from the first overlap on are decided again in the same
  * round, one after another against the live occupancy (a device-side chain:
  * each is committed before the next is decided), so no request is decided
- * more than twice.  Departures
- * return a job's vertices before later arrivals are decided.  Requests that
- * arrive while a round is on the GPU wait for the next round, so the device
- * works on everything that is pending, up to an admission window that
- * doubles after a round whose parallel decisions all committed and shrinks
- * after one that met an overlap or a wait (at most max_batch).  max_batch = 1
- * gives the plain per-request form (one request per round). */
+ * more than twice.  The chain runs in segments of n/4 requests (1 to 8 for a
+ * round of n), and each segment's decisions are published when it ends.
+ * Admission: the window doubles after a round whose parallel decisions all
+ * committed and shrinks after one that met an overlap or a wait (at most
+ * max_batch); after a parallel pass of which fewer than half committed, the
+ * next large rounds (1, 2, 4 ... 64 of them) skip it and go straight to the
+ * chain, up to 64 requests each.  Lifetimes are kept on the device: a commit
+ * stamps its vertices with the device clock plus the job's lifetime, and
+ * after every chain decision the vertices whose time has passed are freed
+ * before the next one, so a job holds its accelerators for its lifetime
+ * whatever the round length.  DEPART events return a job's vertices before
+ * later arrivals are decided.  Requests that arrive while a round is on the
+ * GPU wait for the next round.  max_batch = 1 gives the plain per-request
+ * form (one request per round). */
 
 enum mapa_event_kind { MAPA_EVENT_ARRIVE = 0, MAPA_EVENT_DEPART = 1 };
 
@@ -290,8 +297,8 @@ enum mapa_event_kind { MAPA_EVENT_ARRIVE = 0, MAPA_EVENT_DEPART = 1 };
  *   at_ns:       arrival time in ns after mapa_serve_open (0 = immediately).
  *                Events of one submit call must have non-decreasing at_ns.
  *   ARRIVE:      pattern_id, policy; lifetime_ns > 0 makes the server release
- *                the job lifetime_ns after it is committed (0 = keep until a
- *                DEPART event names it).
+ *                the job lifetime_ns after it is committed, by the device
+ *                clock (0 = keep until a DEPART event names it).
  *   DEPART:      job_id of a committed job. */
 typedef struct {
     int64_t request_id;

@@ -264,6 +264,7 @@ void free_topo(mapa::TopoDevice &t) {
     cudaFree(t.wc);
     cudaFree(t.occupancy);
     cudaFree(t.owner);
+    cudaFree(t.expire);
     cudaFree(t.next_job);
     cudaFree(t.scratch);
     cudaFree(t.wc_effbw);
@@ -372,6 +373,7 @@ int mapa_topology_load(mapa_ctx ctx, int32_t n, int32_t m, const int32_t *u, con
     if (cudaMalloc(&t.adj, adj.size() * 4) != cudaSuccess || cudaMalloc(&t.clsv, clsv.size() * 4) != cudaSuccess ||
         cudaMalloc(&t.wc, std::max(C, 1) * 4) != cudaSuccess || cudaMalloc(&t.occupancy, 8 * 4) != cudaSuccess ||
         cudaMalloc(&t.owner, n * sizeof(int64_t)) != cudaSuccess ||
+        cudaMalloc(&t.expire, n * sizeof(int64_t)) != cudaSuccess ||
         cudaMalloc(&t.next_job, sizeof(unsigned long long)) != cudaSuccess ||
         cudaMalloc(&t.scratch, 64) != cudaSuccess || cudaMalloc(&t.wc_effbw, std::max(C, 1) * 4) != cudaSuccess) {
         free_topo(t);
@@ -385,6 +387,7 @@ int mapa_topology_load(mapa_ctx ctx, int32_t n, int32_t m, const int32_t *u, con
     if (C > 0) CTX_CUDA(ctx, cudaMemcpyAsync(t.wc_effbw, codes.data(), C * 4, cudaMemcpyHostToDevice, st));
     CTX_CUDA(ctx, cudaMemsetAsync(t.occupancy, 0, 8 * 4, st));
     CTX_CUDA(ctx, cudaMemsetAsync(t.owner, 0, n * sizeof(int64_t), st));
+    CTX_CUDA(ctx, cudaMemsetAsync(t.expire, 0, n * sizeof(int64_t), st));
     CTX_CUDA(ctx, cudaMemsetAsync(t.next_job, 0, sizeof(unsigned long long), st));
     CTX_CUDA(ctx, cudaStreamSynchronize(st));
     te.live = true;

@@ -73,11 +73,53 @@ void launch_scan(const unsigned long long *cnt, unsigned long long *off, uint64_
     k_scan<<<1, 1024, 0, s>>>(cnt, off, nb);
 }
 
+__device__ __forceinline__ long long device_clock_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return static_cast<long long>(t);
+}
+
+// Frees (one warp) every held vertex whose job's end time has passed and
+// logs it with log position pos.
+__device__ void expire_pass(int n, uint32_t *occ, int64_t *owner, int64_t *expire, const ServeLife &lf, int32_t pos,
+                            int lane) {
+    const long long now = device_clock_ns();
+    for (int v = lane; v < n; v += 32) {
+        const long long end = expire[v];
+        if (end == 0 || end > now) continue;
+        expire[v] = 0;
+        const long long job = owner[v];
+        if (job == 0) continue;
+        owner[v] = 0;
+        atomicAnd(occ + (v >> 5), ~(1u << (v & 31)));
+        const uint32_t slot = atomicAdd(lf.n_log, 1u);
+        if (slot < lf.cap) {
+            lf.log_job[slot] = job;
+            lf.log_pos[slot] = pos;
+        }
+    }
+}
+
+// Marks the k vertices of res busy under job (with its end time, 0 = none).
+__device__ __forceinline__ void hold(const mapa_result &res, uint32_t *occ, int64_t *owner, int64_t *expire,
+                                     long long job, long long end) {
+    for (int i = 0; i < res.k; ++i) {
+        const int v = res.verts[i];
+        occ[v >> 5] |= 1u << (v & 31);
+        owner[v] = job;
+        expire[v] = end;
+    }
+}
+
+__global__ void k_expire(int n, uint32_t *occ, int64_t *owner, int64_t *expire, ServeLife lf) {
+    expire_pass(n, occ, owner, expire, lf, -1, threadIdx.x & 31);
+}
+
 // State management (Sec. 3.6): mark the chosen vertices busy under a new job id.
 // With `blocked` (FIFO waiting): once a request of the chain did not fit,
 // it and every later one are marked deferred (reserved = kDeferred) and
 // nothing more is committed.
-__global__ void k_commit(mapa_result *res, uint32_t *occ, int64_t *owner, unsigned long long *next_job,
+__global__ void k_commit(mapa_result *res, uint32_t *occ, int64_t *owner, int64_t *expire, unsigned long long *next_job,
                          int32_t *blocked) {
     if (threadIdx.x != 0 || blockIdx.x != 0) return;
     if (blocked) {
@@ -89,50 +131,53 @@ __global__ void k_commit(mapa_result *res, uint32_t *occ, int64_t *owner, unsign
     }
     if (res->status != MAPA_OK && res->status != MAPA_INEXACT) return;
     const long long job = static_cast<long long>(atomicAdd(next_job, 1ull)) + 1;
-    for (int i = 0; i < res->k; ++i) {
-        const int v = res->verts[i];
-        occ[v >> 5] |= 1u << (v & 31);
-        owner[v] = job;
-    }
+    hold(*res, occ, owner, expire, job, 0);
     res->job_id = job;
 }
 
-// One step of a commit chain, last kernel of the step: commits the decision
-// at batch position *cursor as k_commit does, logs the step's overflow flag
-// for that position and clears it, and moves the cursor to the next request.
+// One step of a commit chain, last kernel of the step (one warp): commits the
+// decision at batch position *cursor as k_commit does (with its end time when
+// lifetimes are kept on the device), logs the step's overflow flag for that
+// position and clears it, moves the cursor to the next request, and then
+// frees the vertices whose lifetime has ended before the next decision.
 // Every kernel of a step reads its request through the cursor, so the launch
 // sequence of a step is the same for every request of a pattern and can be
 // replayed from one captured graph.
-__global__ void k_commit_step(mapa_result *out, int32_t *chain, uint32_t *occ, int64_t *owner,
-                              unsigned long long *next_job, int32_t *blocked, int32_t *ovf_log) {
-    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+__global__ void k_commit_step(int n, mapa_result *out, int32_t *chain, uint32_t *occ, int64_t *owner, int64_t *expire,
+                              unsigned long long *next_job, int32_t *blocked, int32_t *ovf_log, ServeLife lf) {
+    const int lane = threadIdx.x & 31;
     const int32_t pos = chain[0];
-    mapa_result *res = out + pos;
-    ovf_log[pos] = chain[1];
-    chain[1] = 0;
-    chain[0] = pos + 1;
-    if (blocked) {
-        if (*blocked || res->status == MAPA_NO_FIT) {
-            *blocked = 1;
-            res->reserved = kDeferred;
-            return;
+    __syncwarp();
+    if (lane == 0) {
+        mapa_result *res = out + pos;
+        ovf_log[pos] = chain[1];
+        chain[1] = 0;
+        chain[0] = pos + 1;
+        bool commit = true;
+        if (blocked) {
+            if (*blocked || res->status == MAPA_NO_FIT) {
+                *blocked = 1;
+                res->reserved = kDeferred;
+                commit = false;
+            }
+        }
+        if (commit && (res->status == MAPA_OK || res->status == MAPA_INEXACT)) {
+            const long long job = static_cast<long long>(atomicAdd(next_job, 1ull)) + 1;
+            const long long life = lf.life ? lf.life[pos] : 0;
+            hold(*res, occ, owner, expire, job, life > 0 ? device_clock_ns() + life : 0);
+            res->job_id = job;
         }
     }
-    if (res->status != MAPA_OK && res->status != MAPA_INEXACT) return;
-    const long long job = static_cast<long long>(atomicAdd(next_job, 1ull)) + 1;
-    for (int i = 0; i < res->k; ++i) {
-        const int v = res->verts[i];
-        occ[v >> 5] |= 1u << (v & 31);
-        owner[v] = job;
-    }
-    res->job_id = job;
+    __syncwarp();
+    if (lf.life) expire_pass(n, occ, owner, expire, lf, pos + 1, lane);
 }
 
 // State management (Sec. 3.6): return a job's vertices to the free pool.
-__global__ void k_release(int n, long long job, uint32_t *occ, int64_t *owner, int32_t *freed) {
+__global__ void k_release(int n, long long job, uint32_t *occ, int64_t *owner, int64_t *expire, int32_t *freed) {
     for (int v = threadIdx.x; v < n; v += blockDim.x) {
         if (owner[v] == job) {
             owner[v] = 0;
+            expire[v] = 0;
             atomicAnd(occ + (v >> 5), ~(1u << (v & 31)));
             atomicAdd(freed, 1);
         }
@@ -146,9 +191,11 @@ __global__ void k_release(int n, long long job, uint32_t *occ, int64_t *owner, i
 // server decides those again, in order, against the live occupancy);
 // with fifo_wait, conflict[i] = 2 from the first request that did not fit on
 // (it and everything behind it wait at the head of the queue).
-__global__ void k_commit_round(mapa_result *res, int32_t n, uint32_t *occ, int64_t *owner,
-                               unsigned long long *next_job, int32_t *conflict, int32_t fifo_wait) {
+__global__ void k_commit_round(mapa_result *res, int32_t n, uint32_t *occ, int64_t *owner, int64_t *expire,
+                               unsigned long long *next_job, int32_t *conflict, int32_t fifo_wait,
+                               const int64_t *life) {
     if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    const long long now = device_clock_ns();
     uint32_t cur[MAPA_MASK_WORDS];
     for (int w = 0; w < MAPA_MASK_WORDS; ++w) cur[w] = occ[w];
     int32_t stop = 0;
@@ -173,20 +220,26 @@ __global__ void k_commit_round(mapa_result *res, int32_t n, uint32_t *occ, int64
         }
         const long long job = static_cast<long long>(atomicAdd(next_job, 1ull)) + 1;
         for (int w = 0; w < MAPA_MASK_WORDS; ++w) cur[w] |= mask[w];
-        for (int j = 0; j < res[i].k; ++j) owner[res[i].verts[j]] = job;
+        const long long lt = life ? life[i] : 0;
+        for (int j = 0; j < res[i].k; ++j) {
+            owner[res[i].verts[j]] = job;
+            expire[res[i].verts[j]] = lt > 0 ? now + lt : 0;
+        }
         res[i].job_id = job;
     }
     for (int w = 0; w < MAPA_MASK_WORDS; ++w) occ[w] = cur[w];
 }
 
 // Returns the vertices of several jobs to the free pool (Sec. 3.6).
-__global__ void k_release_many(int n, const int64_t *jobs, int32_t njobs, uint32_t *occ, int64_t *owner) {
+__global__ void k_release_many(int n, const int64_t *jobs, int32_t njobs, uint32_t *occ, int64_t *owner,
+                               int64_t *expire) {
     for (int v = threadIdx.x; v < n; v += blockDim.x) {
         const int64_t o = owner[v];
         if (o == 0) continue;
         for (int j = 0; j < njobs; ++j) {
             if (o == jobs[j]) {
                 owner[v] = 0;
+                expire[v] = 0;
                 atomicAnd(occ + (v >> 5), ~(1u << (v & 31)));
                 break;
             }
@@ -660,7 +713,7 @@ int engine_run_batch(Engine *e, const TopoDevice &t, const std::vector<PatternAr
                 rc = run_group(e, t, redo, false, err);
                 if (rc != MAPA_OK) return rc;
             }
-            k_commit<<<1, 32, 0, e->stream>>>(out_dev + i, t.occupancy, t.owner, t.next_job, nullptr);
+            k_commit<<<1, 32, 0, e->stream>>>(out_dev + i, t.occupancy, t.owner, t.expire, t.next_job, nullptr);
             MAPA_CUDA_TRY(cudaGetLastError());
             e->st.kernel_launches += 1;
         }
@@ -861,7 +914,9 @@ int engine_run_batch(Engine *e, const TopoDevice &t, const std::vector<PatternAr
 // MAPA_E_NOMEM (its commit would not be trustworthy).
 int engine_run_chain(Engine *e, const TopoDevice &t, const std::vector<PatternArgs> &patterns, int32_t n,
                      const int32_t *pattern_ids, const uint8_t *kinds, const mapa_request *reqs_dev,
-                     mapa_result *out_dev, bool fifo_wait, mapa_result *out_host, std::string *err) {
+                     mapa_result *out_dev, bool fifo_wait, mapa_result *out_host, const ServeLife *life,
+                     std::string *err) {
+    const ServeLife lf = life ? *life : ServeLife{};
     MAPA_CUDA_TRY(cudaSetDevice(e->device));
     if (n <= 0) return MAPA_OK;
     const int32_t npat = static_cast<int32_t>(patterns.size());
@@ -890,8 +945,8 @@ int engine_run_chain(Engine *e, const TopoDevice &t, const std::vector<PatternAr
     auto step = [&](const GroupRun &gr) -> int {
         const int r = run_group(e, t, gr, true, err);
         if (r != MAPA_OK) return r;
-        k_commit_step<<<1, 32, 0, e->stream>>>(out_dev, e->d_chain, t.occupancy, t.owner, t.next_job, blocked,
-                                                e->overflow);
+        k_commit_step<<<1, 32, 0, e->stream>>>(t.n, out_dev, e->d_chain, t.occupancy, t.owner, t.expire, t.next_job,
+                                                blocked, e->overflow, lf);
         MAPA_CUDA_TRY(cudaGetLastError());
         e->st.kernel_launches += 1;
         return MAPA_OK;
@@ -914,7 +969,8 @@ int engine_run_chain(Engine *e, const TopoDevice &t, const std::vector<PatternAr
                                           reinterpret_cast<int64_t>(sl.arena), static_cast<int64_t>(sl.arena_bytes),
                                           reinterpret_cast<int64_t>(sl.group_mem), reinterpret_cast<int64_t>(e->overflow),
                                           reinterpret_cast<int64_t>(e->stream),
-                                          static_cast<int64_t>(e->work_budget)};
+                                          static_cast<int64_t>(e->work_budget),
+                                          reinterpret_cast<int64_t>(lf.life), reinterpret_cast<int64_t>(lf.log_job)};
         auto it = e->graphs.find(key);
         if (it == e->graphs.end() && e->shapes_seen.count(key)) {
             if (e->graphs.size() >= 64) e->clear_graphs();
@@ -962,6 +1018,13 @@ int engine_run_chain(Engine *e, const TopoDevice &t, const std::vector<PatternAr
     if (out_host)
         MAPA_CUDA_TRY(
             cudaMemcpyAsync(out_host, out_dev, sizeof(mapa_result) * n, cudaMemcpyDeviceToHost, e->stream));
+    if (lf.host_n_log) {
+        MAPA_CUDA_TRY(cudaMemcpyAsync(lf.host_n_log, lf.n_log, sizeof(uint32_t), cudaMemcpyDeviceToHost, e->stream));
+        MAPA_CUDA_TRY(cudaMemcpyAsync(lf.host_log_job, lf.log_job, sizeof(int64_t) * lf.host_first,
+                                      cudaMemcpyDeviceToHost, e->stream));
+        MAPA_CUDA_TRY(cudaMemcpyAsync(lf.host_log_pos, lf.log_pos, sizeof(int32_t) * lf.host_first,
+                                      cudaMemcpyDeviceToHost, e->stream));
+    }
     rc = end_batch(e, err);
     if (rc != MAPA_OK) return rc;
     for (int32_t i = 0; i < n; ++i)
@@ -973,10 +1036,10 @@ int engine_run_chain(Engine *e, const TopoDevice &t, const std::vector<PatternAr
 }
 
 int engine_commit_round(Engine *e, const TopoDevice &t, mapa_result *out_dev, int32_t n, int32_t *conflict_dev,
-                        bool fifo_wait, std::string *err) {
+                        bool fifo_wait, const ServeLife *life, std::string *err) {
     if (n <= 0) return MAPA_OK;
-    k_commit_round<<<1, 32, 0, e->stream>>>(out_dev, n, t.occupancy, t.owner, t.next_job, conflict_dev,
-                                            fifo_wait ? 1 : 0);
+    k_commit_round<<<1, 32, 0, e->stream>>>(out_dev, n, t.occupancy, t.owner, t.expire, t.next_job, conflict_dev,
+                                            fifo_wait ? 1 : 0, life ? life->life : nullptr);
     MAPA_CUDA_TRY(cudaGetLastError());
     e->st.kernel_launches += 1;
     return MAPA_OK;
@@ -984,7 +1047,14 @@ int engine_commit_round(Engine *e, const TopoDevice &t, mapa_result *out_dev, in
 
 int engine_release_many(Engine *e, const TopoDevice &t, const int64_t *jobs_dev, int32_t njobs, std::string *err) {
     if (njobs <= 0) return MAPA_OK;
-    k_release_many<<<1, 256, 0, e->stream>>>(t.n, jobs_dev, njobs, t.occupancy, t.owner);
+    k_release_many<<<1, 256, 0, e->stream>>>(t.n, jobs_dev, njobs, t.occupancy, t.owner, t.expire);
+    MAPA_CUDA_TRY(cudaGetLastError());
+    e->st.kernel_launches += 1;
+    return MAPA_OK;
+}
+
+int engine_expire(Engine *e, const TopoDevice &t, const ServeLife &life, std::string *err) {
+    k_expire<<<1, 32, 0, e->stream>>>(t.n, t.occupancy, t.owner, t.expire, life);
     MAPA_CUDA_TRY(cudaGetLastError());
     e->st.kernel_launches += 1;
     return MAPA_OK;
@@ -1080,7 +1150,8 @@ int engine_autotune(Engine *e, const TopoDevice &t, const std::vector<PatternArg
 int engine_release(Engine *e, const TopoDevice &t, int64_t job_id, int32_t *freed, std::string *err) {
     MAPA_CUDA_TRY(cudaSetDevice(e->device));
     MAPA_CUDA_TRY(cudaMemsetAsync(t.scratch, 0, sizeof(int32_t), e->stream));
-    k_release<<<1, 256, 0, e->stream>>>(t.n, static_cast<long long>(job_id), t.occupancy, t.owner, t.scratch);
+    k_release<<<1, 256, 0, e->stream>>>(t.n, static_cast<long long>(job_id), t.occupancy, t.owner, t.expire,
+                                        t.scratch);
     MAPA_CUDA_TRY(cudaGetLastError());
     MAPA_CUDA_TRY(cudaMemcpyAsync(freed, t.scratch, sizeof(int32_t), cudaMemcpyDeviceToHost, e->stream));
     MAPA_CUDA_TRY(cudaStreamSynchronize(e->stream));

@@ -154,6 +154,7 @@ struct TopoDevice {
     int32_t *wc = nullptr;
     uint32_t *occupancy = nullptr;  // [8]
     int64_t *owner = nullptr;       // [n] job id holding each vertex, 0 = free
+    int64_t *expire = nullptr;      // [n] device-clock ns when the vertex's job ends (0 = held until released)
     unsigned long long *next_job = nullptr;
     int32_t *scratch = nullptr;     // small per-topology scratch (release count)
     int32_t *wc_effbw = nullptr;    // [C] effbw_class_code of each class weight
@@ -190,8 +191,32 @@ int engine_release(Engine *e, const TopoDevice &t, int64_t job_id, int32_t *free
 // Internal mark (mapa_result.reserved) of a chain decision deferred by FIFO waiting.
 constexpr int32_t kDeferred = 2;
 
+// Lifetimes kept on the device (served loop): life[i] is the lifetime in ns
+// of the job that request i of the call commits (0 = until released); the
+// job's vertices end at the device clock of the commit plus life[i].  Before
+// each later decision of a chain the vertices whose end has passed are freed
+// and every freed (job, vertex) is appended to the log with the chain
+// position it was freed before (n = after the last decision, -1 = freed by
+// engine_expire).  The log holds cap entries; n_log counts every entry, so
+// *n_log > cap means entries were lost (a caller error: cap too small).
+struct ServeLife {
+    const int64_t *life = nullptr;
+    int64_t *log_job = nullptr;
+    int32_t *log_pos = nullptr;
+    uint32_t *n_log = nullptr;
+    uint32_t cap = 0;
+    // optional pinned host copies engine_run_chain fills before it returns:
+    // the count and the first host_first entries
+    uint32_t *host_n_log = nullptr;
+    int64_t *host_log_job = nullptr;
+    int32_t *host_log_pos = nullptr;
+    uint32_t host_first = 0;
+};
+
 int engine_commit_round(Engine *e, const TopoDevice &t, mapa_result *out_dev, int32_t n, int32_t *conflict_dev,
-                        bool fifo_wait, std::string *err);
+                        bool fifo_wait, const ServeLife *life, std::string *err);
+// Frees every vertex whose job's lifetime has ended (log position -1).
+int engine_expire(Engine *e, const TopoDevice &t, const ServeLife &life, std::string *err);
 // kinds[i]: bit 0 = request i is in bounded mode, bit 1 = bandwidth-sensitive
 // (nullptr = neither, for every request).
 constexpr uint8_t kKindBounded = 1, kKindSensitive = 2;
@@ -199,7 +224,8 @@ constexpr uint8_t kKindBounded = 1, kKindSensitive = 2;
 // the call returns.
 int engine_run_chain(Engine *e, const TopoDevice &t, const std::vector<PatternArgs> &patterns, int32_t n,
                      const int32_t *pattern_ids, const uint8_t *kinds, const mapa_request *reqs_dev,
-                     mapa_result *out_dev, bool fifo_wait, mapa_result *out_host, std::string *err);
+                     mapa_result *out_dev, bool fifo_wait, mapa_result *out_host, const ServeLife *life,
+                     std::string *err);
 int engine_release_many(Engine *e, const TopoDevice &t, const int64_t *jobs_dev, int32_t njobs, std::string *err);
 
 // Scratch for staging host batches.

@@ -12,8 +12,13 @@
 //      overlap (FIFO, Sec. 4); the requests from the first overlap on are
 //      decided again in the same round, in order, by a device-side chain
 //      against the live occupancy (see decide_round).
-// The occupancy lives on the device; the worker keeps a host copy of it that
-// it updates from the committed and released vertex sets.
+// The occupancy lives on the device, and so do the lifetimes: a commit
+// stamps its vertices with the device clock plus the job's lifetime, and
+// every chain step frees the vertices whose time has passed before the next
+// decision, logging what it freed.  The worker keeps a host copy of the
+// occupancy that it updates from the committed vertex sets and that log; its
+// own schedule of lifetimes only tells it when to look (and releases a job
+// itself should the device not have done so a millisecond later).
 #include <algorithm>
 #include <atomic>
 #include <chrono>
@@ -69,10 +74,13 @@ struct mapa_server_s {
     std::string error_msg;
 
     // worker-only state
-    std::multimap<int64_t, int64_t> expiries;      // due time -> job (lifetimes)
+    std::multimap<int64_t, int64_t> expiries;      // host time a lifetime ends -> job (when to look)
+    std::unordered_map<int64_t, std::multimap<int64_t, int64_t>::iterator> expiry_of;  // job -> its entry
     std::multimap<int64_t, Pending> departs;       // explicit DEPART events by time
     bool blocked = false;                          // head of the queue waits for a departure
     int32_t window = 0;                            // requests admitted per round (adaptive)
+    int32_t spec_skip = 0;                         // large rounds left that go straight to the chain
+    int32_t spec_backoff = 0;                      // their number after the next parallel pass that fails
     std::unordered_map<int64_t, Job> live;         // committed jobs
     uint32_t occ[MAPA_MASK_WORDS] = {};            // host copy of the device occupancy
     std::atomic<uint64_t> rounds{0}, decisions{0}, conflicts{0};
@@ -87,6 +95,11 @@ struct mapa_server_s {
     int32_t *h_conflict = nullptr;
     int64_t *h_jobs = nullptr;
     int32_t jobs_cap = 0;
+    // device lifetimes: per request of a call, and the log of freed vertices
+    int64_t *d_life = nullptr, *h_life = nullptr;
+    int64_t *d_log_job = nullptr, *h_log_job = nullptr;
+    int32_t *d_log_pos = nullptr, *h_log_pos = nullptr;
+    uint32_t *d_log_n = nullptr, *h_log_n = nullptr;
 
     int64_t now_ns() const {
         return std::chrono::duration_cast<std::chrono::nanoseconds>(Clock::now() - t0).count();
@@ -114,10 +127,22 @@ void fail(mapa_server srv, int code, const std::string &msg) {
     srv->cv_done.notify_all();
 }
 
-// Requests a serving chain decides between two host checks of its FIFO-wait flag.
-constexpr int32_t kChainSegment = 32;
+// Longest run of requests a serving chain decides between two host checks
+// of its FIFO-wait flag; each segment's decisions are published when it
+// ends, so a round of n requests runs segments of n/4 (1..8): a small round
+// publishes every decision at once, a long one saves host round trips.
+constexpr int32_t kChainSegment = 8;
 // Rounds smaller than this skip the parallel pass and go straight to the chain.
 constexpr int32_t kSpeculateMin = 16;
+// Requests admitted per round while the parallel pass is backed off.
+constexpr int32_t kChainRound = 64;
+// Longest back-off of the parallel pass, in rounds.
+constexpr int32_t kMaxBackoff = 64;
+// Entries of the log of vertices freed on the device: one chain segment or
+// one expiry pass frees each vertex at most once per step.
+constexpr uint32_t kLogCap = 256 * (kChainSegment + 2);
+// Entries read back with the log's count (more take a second copy).
+constexpr uint32_t kLogFirst = 256;
 
 mapa_served served_of(const Pending &p, int64_t done_ns, const uint32_t *snap) {
     mapa_served s;
@@ -166,6 +191,92 @@ int release_jobs(mapa_server srv, const std::vector<int64_t> &jobs, std::string 
     return mapa::engine_release_many(ctx->engine, t, srv->d_jobs, static_cast<int32_t>(jobs.size()), err);
 }
 
+mapa::ServeLife life_args(mapa_server srv) {
+    mapa::ServeLife lf;
+    lf.life = srv->d_life;
+    lf.log_job = srv->d_log_job;
+    lf.log_pos = srv->d_log_pos;
+    lf.n_log = srv->d_log_n;
+    lf.cap = kLogCap;
+    return lf;
+}
+
+// Empties the device log (enqueued).
+int clear_log(mapa_server srv, std::string *err) {
+    if (cudaMemsetAsync(srv->d_log_n, 0, sizeof(uint32_t), mapa::engine_stream(srv->ctx->engine)) != cudaSuccess) {
+        if (err) *err = "log reset failed";
+        return MAPA_E_CUDA;
+    }
+    return MAPA_OK;
+}
+
+// Reads the device log back (synchronises the stream): (position, job) pairs
+// in the order the device wrote them.  copied: the count and the first
+// kLogFirst entries are already in the pinned host copies.
+int read_log(mapa_server srv, std::vector<std::pair<int32_t, int64_t>> &entries, std::string *err,
+             bool copied = false) {
+    cudaStream_t st = mapa::engine_stream(srv->ctx->engine);
+    entries.clear();
+    if (!copied &&
+        (cudaMemcpyAsync(srv->h_log_n, srv->d_log_n, sizeof(uint32_t), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+         cudaMemcpyAsync(srv->h_log_job, srv->d_log_job, sizeof(int64_t) * kLogFirst, cudaMemcpyDeviceToHost, st) !=
+             cudaSuccess ||
+         cudaMemcpyAsync(srv->h_log_pos, srv->d_log_pos, sizeof(int32_t) * kLogFirst, cudaMemcpyDeviceToHost, st) !=
+             cudaSuccess ||
+         cudaStreamSynchronize(st) != cudaSuccess)) {
+        if (err) *err = "log copy failed";
+        return MAPA_E_CUDA;
+    }
+    const uint32_t n = *srv->h_log_n;
+    if (n > kLogCap) {
+        if (err) *err = "the device log of freed vertices overflowed";
+        return MAPA_E_STATE;
+    }
+    if (n > kLogFirst) {
+        const size_t rest = n - kLogFirst;
+        if (cudaMemcpyAsync(srv->h_log_job + kLogFirst, srv->d_log_job + kLogFirst, sizeof(int64_t) * rest,
+                            cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+            cudaMemcpyAsync(srv->h_log_pos + kLogFirst, srv->d_log_pos + kLogFirst, sizeof(int32_t) * rest,
+                            cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+            cudaStreamSynchronize(st) != cudaSuccess) {
+            if (err) *err = "log copy failed";
+            return MAPA_E_CUDA;
+        }
+    }
+    for (uint32_t i = 0; i < n; ++i) entries.emplace_back(srv->h_log_pos[i], srv->h_log_job[i]);
+    return MAPA_OK;
+}
+
+// A job the device freed: forget it and clear its vertices from mask m.
+// Returns false when the job is not (or no longer) live.
+bool forget_job(mapa_server srv, int64_t job, uint32_t *m) {
+    auto it = srv->live.find(job);
+    if (it == srv->live.end()) return false;
+    for (int v : it->second.verts) m[v >> 5] &= ~(1u << (v & 31));
+    srv->live.erase(it);
+    auto e = srv->expiry_of.find(job);
+    if (e != srv->expiry_of.end()) {
+        srv->expiries.erase(e->second);
+        srv->expiry_of.erase(e);
+    }
+    return true;
+}
+
+// Frees on the device every vertex whose lifetime has ended and applies the
+// log to the host state (host mask m); sets *freed when anything was freed.
+int expire_on_device(mapa_server srv, uint32_t *m, bool *freed, std::string *err) {
+    mapa_ctx ctx = srv->ctx;
+    const mapa::TopoDevice &t = ctx->topos[srv->topo_id].dev;
+    int rc = clear_log(srv, err);
+    if (rc == MAPA_OK) rc = mapa::engine_expire(ctx->engine, t, life_args(srv), err);
+    std::vector<std::pair<int32_t, int64_t>> log;
+    if (rc == MAPA_OK) rc = read_log(srv, log, err);
+    if (rc != MAPA_OK) return rc;
+    for (const auto &en : log)
+        if (forget_job(srv, en.second, m) && freed) *freed = true;
+    return MAPA_OK;
+}
+
 void add_mask(uint32_t *m, const mapa_result &r) {
     for (int j = 0; j < r.k; ++j) m[r.verts[j] >> 5] |= 1u << (r.verts[j] & 31);
 }
@@ -187,10 +298,47 @@ int decide_round(mapa_server srv, std::vector<Pending> &round, std::vector<mapa_
     const mapa::TopoDevice &t = ctx->topos[srv->topo_id].dev;
     cudaStream_t st = mapa::engine_stream(ctx->engine);
     const int32_t n = static_cast<int32_t>(round.size());
+    // lifetimes that ended before the round: freed before its snapshot (the
+    // device ends a lifetime no later than the host schedule says)
+    int rc = MAPA_OK;
+    if (!srv->expiries.empty() && srv->expiries.begin()->first <= srv->now_ns())
+        rc = expire_on_device(srv, srv->occ, nullptr, err);
+    if (rc != MAPA_OK) return rc;
     uint32_t snap[MAPA_MASK_WORDS];
     memcpy(snap, srv->occ, sizeof(snap));
-    int rc = MAPA_OK;
-    const bool speculate = n >= kSpeculateMin;
+    // The parallel pass pays when most of its decisions commit; after one
+    // where fewer than half did, the next large rounds skip it (exponential
+    // back-off), since the chain redoes what overlaps anyway.
+    const bool speculate = n >= kSpeculateMin && srv->spec_skip == 0;
+    if (n >= kSpeculateMin && srv->spec_skip > 0) --srv->spec_skip;
+    std::vector<int64_t> done_at(n, -1);
+    // jobs of this round that the device freed before they were published
+    std::unordered_map<int64_t, int32_t> round_job;  // job -> request
+    std::vector<char> gone(n, 0);
+    // Publishes the decisions in idx that are final (not deferred, not yet
+    // out); the host schedule looks for a committed job's end one lifetime
+    // after its publication (the device ends it one lifetime after commit).
+    auto publish = [&](const std::vector<int32_t> &idx, const std::vector<mapa_result> &res,
+                       const std::vector<uint32_t> &snaps, const std::vector<char> &deferred) {
+        const int64_t now = srv->now_ns();
+        for (const int32_t i : idx) {
+            if (deferred[i] || done_at[i] >= 0) continue;
+            done_at[i] = now;
+            mapa_served sv = served_of(round[i], now, &snaps[static_cast<size_t>(i) * MAPA_MASK_WORDS]);
+            sv.result = res[i];
+            out.push_back(sv);
+            srv->decisions += 1;
+            if (placed(res[i].status) && res[i].job_id > 0 && !gone[i]) {
+                Job job;
+                for (int j = 0; j < res[i].k; ++j) job.verts.push_back(res[i].verts[j]);
+                srv->live.emplace(res[i].job_id, std::move(job));
+                if (round[i].ev.lifetime_ns > 0)
+                    srv->expiry_of[res[i].job_id] =
+                        srv->expiries.emplace(now + round[i].ev.lifetime_ns, res[i].job_id);
+            }
+        }
+        finish(srv, out);
+    };
     if (speculate) {
         for (int32_t i = 0; i < n; ++i) {
             mapa_request &q = srv->h_reqs[i];
@@ -198,16 +346,20 @@ int decide_round(mapa_server srv, std::vector<Pending> &round, std::vector<mapa_
             q.pattern_id = round[i].ev.pattern_id;
             q.policy = round[i].ev.policy;
             memcpy(q.busy, snap, sizeof(snap));
+            srv->h_life[i] = round[i].ev.lifetime_ns;
             round[i].rounds += 1;
         }
         if (cudaMemcpyAsync(srv->d_reqs, srv->h_reqs, sizeof(mapa_request) * n, cudaMemcpyHostToDevice, st) !=
-            cudaSuccess) {
+                cudaSuccess ||
+            cudaMemcpyAsync(srv->d_life, srv->h_life, sizeof(int64_t) * n, cudaMemcpyHostToDevice, st) !=
+                cudaSuccess) {
             if (err) *err = "request copy failed";
             return MAPA_E_CUDA;
         }
         rc = mapa::engine_run_batch(ctx->engine, t, ctx->pattern_args, n, srv->d_reqs, srv->d_out, false, err);
         if (rc != MAPA_OK) return rc;
-        rc = mapa::engine_commit_round(ctx->engine, t, srv->d_out, n, srv->d_conflict, srv->fifo_wait, err);
+        const mapa::ServeLife lf = life_args(srv);
+        rc = mapa::engine_commit_round(ctx->engine, t, srv->d_out, n, srv->d_conflict, srv->fifo_wait, &lf, err);
         if (rc != MAPA_OK) return rc;
         if (cudaMemcpyAsync(srv->h_out, srv->d_out, sizeof(mapa_result) * n, cudaMemcpyDeviceToHost, st) !=
                 cudaSuccess ||
@@ -231,8 +383,10 @@ int decide_round(mapa_server srv, std::vector<Pending> &round, std::vector<mapa_
     std::vector<int32_t> chain, chain_pids;
     std::vector<uint8_t> chain_bounded;
     std::vector<char> deferred(n, 0);
+    std::vector<int32_t> first_pass;
     for (int32_t i = 0; i < n; ++i) {
         memcpy(&snaps[static_cast<size_t>(i) * MAPA_MASK_WORDS], snap, sizeof(snap));
+        if (speculate && srv->h_conflict[i] == 0) first_pass.push_back(i);
         if (srv->h_conflict[i] == 1) {
             chain.push_back(i);
             chain_pids.push_back(round[i].ev.pattern_id);
@@ -245,12 +399,15 @@ int decide_round(mapa_server srv, std::vector<Pending> &round, std::vector<mapa_
             add_mask(cur, res[i]);
         }
     }
+    // what the parallel pass committed (and its no-fits) is final now
+    if (!first_pass.empty()) publish(first_pass, res, snaps, deferred);
     // The chain runs in segments; after one that ended waiting (FIFO), the
     // rest of the chain waits too and is not decided.
     const int32_t m_all = static_cast<int32_t>(chain.size());
+    const int32_t seg = std::max(1, std::min(kChainSegment, n / 4));
     bool chain_blocked = false;
-    for (int32_t c0 = 0; c0 < m_all; c0 += kChainSegment) {
-        const int32_t m = std::min(kChainSegment, m_all - c0);
+    for (int32_t c0 = 0; c0 < m_all; c0 += seg) {
+        const int32_t m = std::min(seg, m_all - c0);
         if (chain_blocked) {
             for (int32_t j = 0; j < m; ++j) deferred[chain[c0 + j]] = 1;
             continue;
@@ -260,19 +417,47 @@ int decide_round(mapa_server srv, std::vector<Pending> &round, std::vector<mapa_
             memset(&q, 0, sizeof(q));
             q.pattern_id = round[chain[c0 + j]].ev.pattern_id;
             q.policy = round[chain[c0 + j]].ev.policy;
+            srv->h_life[j] = round[chain[c0 + j]].ev.lifetime_ns;
             round[chain[c0 + j]].rounds += 1;
         }
         if (cudaMemcpyAsync(srv->d_reqs, srv->h_reqs, sizeof(mapa_request) * m, cudaMemcpyHostToDevice, st) !=
-            cudaSuccess) {
+                cudaSuccess ||
+            cudaMemcpyAsync(srv->d_life, srv->h_life, sizeof(int64_t) * m, cudaMemcpyHostToDevice, st) !=
+                cudaSuccess) {
             if (err) *err = "request copy failed";
             return MAPA_E_CUDA;
         }
-        rc = mapa::engine_run_chain(ctx->engine, t, ctx->pattern_args, m, chain_pids.data() + c0,
-                                    chain_bounded.data() + c0, srv->d_reqs, srv->d_out, srv->fifo_wait, srv->h_out,
-                                    err);
+        // each step frees the lifetimes that ended before the next decision
+        mapa::ServeLife lf = life_args(srv);
+        lf.host_n_log = srv->h_log_n;
+        lf.host_log_job = srv->h_log_job;
+        lf.host_log_pos = srv->h_log_pos;
+        lf.host_first = kLogFirst;
+        rc = clear_log(srv, err);
+        if (rc == MAPA_OK)
+            rc = mapa::engine_run_chain(ctx->engine, t, ctx->pattern_args, m, chain_pids.data() + c0,
+                                        chain_bounded.data() + c0, srv->d_reqs, srv->d_out, srv->fifo_wait,
+                                        srv->h_out, &lf, err);
+        std::vector<std::pair<int32_t, int64_t>> log;
+        if (rc == MAPA_OK) rc = read_log(srv, log, err, true);
         if (rc != MAPA_OK) return rc;
+        // replay the segment on the host mask in device order: what was
+        // freed before decision j, then decision j
+        size_t li = 0;
+        auto freed_before = [&](int32_t pos) {
+            for (; li < log.size() && log[li].first <= pos; ++li) {
+                const int64_t job = log[li].second;
+                if (forget_job(srv, job, cur)) continue;
+                auto rj = round_job.find(job);  // committed earlier in this round, not yet published
+                if (rj == round_job.end() || gone[rj->second]) continue;
+                gone[rj->second] = 1;
+                const mapa_result &r = res[rj->second];
+                for (int q = 0; q < r.k; ++q) cur[r.verts[q] >> 5] &= ~(1u << (r.verts[q] & 31));
+            }
+        };
         for (int32_t j = 0; j < m; ++j) {
             const int32_t i = chain[c0 + j];
+            freed_before(j);
             memcpy(&snaps[static_cast<size_t>(i) * MAPA_MASK_WORDS], cur, sizeof(cur));
             res[i] = srv->h_out[j];
             if (res[i].reserved == mapa::kDeferred) {
@@ -281,11 +466,15 @@ int decide_round(mapa_server srv, std::vector<Pending> &round, std::vector<mapa_
                 chain_blocked = true;
                 continue;
             }
-            if (placed(res[i].status)) add_mask(cur, res[i]);
+            if (placed(res[i].status)) {
+                add_mask(cur, res[i]);
+                if (res[i].job_id > 0) round_job[res[i].job_id] = i;
+            }
         }
+        freed_before(m);
         if (speculate) srv->conflicts += static_cast<uint64_t>(m);  // decided again after an overlap
+        publish(std::vector<int32_t>(chain.begin() + c0, chain.begin() + c0 + m), res, snaps, deferred);
     }
-    const int64_t done_ns = srv->now_ns();
     srv->rounds += 1;
     // FIFO waiting: the first request that did not fit and every later one go
     // back to the head of the queue.  A request that did not fit although the
@@ -306,19 +495,11 @@ int decide_round(mapa_server srv, std::vector<Pending> &round, std::vector<mapa_
         }
         requeue.push_back(round[i]);
     }
-    for (int32_t i = 0; i < n; ++i) {
-        if (deferred[i]) continue;
-        mapa_served s = served_of(round[i], done_ns, &snaps[static_cast<size_t>(i) * MAPA_MASK_WORDS]);
-        s.result = res[i];
-        out.push_back(s);
-        srv->decisions += 1;
-        if (placed(res[i].status) && res[i].job_id > 0) {
-            Job job;
-            for (int j = 0; j < res[i].k; ++j) job.verts.push_back(res[i].verts[j]);
-            srv->live.emplace(res[i].job_id, std::move(job));
-            if (round[i].ev.lifetime_ns > 0) srv->expiries.emplace(done_ns + round[i].ev.lifetime_ns, res[i].job_id);
-        }
-    }
+    // the rest (no-fits answered at the end of the round)
+    std::vector<int32_t> rest;
+    for (int32_t i = 0; i < n; ++i)
+        if (!deferred[i] && done_at[i] < 0) rest.push_back(i);
+    if (!rest.empty()) publish(rest, res, snaps, deferred);
     // Admission window: a round whose decisions all committed from the
     // parallel pass doubles it; one that hit an overlap or had to wait
     // shrinks it towards twice what it committed, so contended stretches
@@ -326,6 +507,14 @@ int decide_round(mapa_server srv, std::vector<Pending> &round, std::vector<mapa_
     int32_t prefix = 0;  // decisions the parallel pass committed
     for (int32_t i = 0; i < n; ++i)
         if (speculate && srv->h_conflict[i] == 0) ++prefix;
+    if (speculate) {
+        if (2 * prefix >= n) {
+            srv->spec_backoff = 0;
+        } else {
+            srv->spec_backoff = std::min(kMaxBackoff, std::max(1, 2 * srv->spec_backoff));
+            srv->spec_skip = srv->spec_backoff;
+        }
+    }
     if ((!speculate || chain.empty()) && requeue.empty())
         srv->window = std::min(srv->max_batch, std::max(srv->window, 1) * 2);
     else if (speculate)
@@ -348,16 +537,41 @@ void worker_loop(mapa_server srv) {
     std::vector<Pending> round;
     std::vector<int64_t> departing;
     std::string err;
+    // Host time by which the device must have ended a lifetime before the
+    // worker releases the job itself.
+    constexpr int64_t kLifeGraceNs = 1000000;
     for (;;) {
         round.clear();
         departing.clear();
+        // 1a. lifetimes: the device ends them by its clock; look when one is due
+        bool due = false;
+        {
+            std::lock_guard<std::mutex> lock(srv->mu);
+            if (srv->stop) return;
+            due = !srv->expiries.empty() && srv->expiries.begin()->first <= srv->now_ns();
+        }
+        if (due) {
+            bool freed = false;
+            int rc = expire_on_device(srv, srv->occ, &freed, &err);
+            if (rc != MAPA_OK) {
+                fail(srv, rc, err);
+                return;
+            }
+            if (freed) {
+                std::lock_guard<std::mutex> lock(srv->mu);
+                srv->blocked = false;
+            }
+        }
         {
             std::unique_lock<std::mutex> lock(srv->mu);
             if (srv->stop) return;
             const int64_t now = srv->now_ns();
-            // 1. departures that are due: lifetimes that ran out, then DEPART events
-            while (!srv->expiries.empty() && srv->expiries.begin()->first <= now) {
-                departing.push_back(srv->expiries.begin()->second);
+            // 1b. a lifetime the device has not ended well after its time
+            // (clocks that disagree), then DEPART events
+            while (!srv->expiries.empty() && srv->expiries.begin()->first + kLifeGraceNs <= now) {
+                const int64_t job = srv->expiries.begin()->second;
+                departing.push_back(job);
+                srv->expiry_of.erase(job);
                 srv->expiries.erase(srv->expiries.begin());
             }
             while (!srv->departs.empty() && srv->departs.begin()->first <= now) {
@@ -371,17 +585,20 @@ void worker_loop(mapa_server srv) {
                 out.push_back(d);
                 if (!known) continue;
                 departing.push_back(job);
-                for (auto it = srv->expiries.begin(); it != srv->expiries.end(); ++it)
-                    if (it->second == job) {
-                        srv->expiries.erase(it);
-                        break;
-                    }
+                auto e = srv->expiry_of.find(job);
+                if (e != srv->expiry_of.end()) {
+                    srv->expiries.erase(e->second);
+                    srv->expiry_of.erase(e);
+                }
             }
             if (!departing.empty()) srv->blocked = false;
             // 2. arrivals in order, unless the head of the queue waits for a departure
             if (!srv->blocked) {
+                // while the parallel pass is backed off a round is one chain
+                const int32_t admit =
+                    srv->spec_skip > 0 ? std::max(srv->window, std::min(srv->max_batch, kChainRound)) : srv->window;
                 while (!srv->incoming.empty() && srv->incoming.front().ev.at_ns <= now &&
-                       static_cast<int32_t>(round.size()) < srv->window) {
+                       static_cast<int32_t>(round.size()) < admit) {
                     round.push_back(srv->incoming.front());
                     srv->incoming.pop_front();
                 }
@@ -390,7 +607,9 @@ void worker_loop(mapa_server srv) {
                 int64_t next_due = -1;
                 if (!srv->blocked && !srv->incoming.empty()) next_due = srv->incoming.front().ev.at_ns;
                 if (!srv->expiries.empty()) {
-                    const int64_t e = srv->expiries.begin()->first;
+                    // a lifetime already looked for: wake at its grace time
+                    int64_t e = srv->expiries.begin()->first;
+                    if (e <= now) e += kLifeGraceNs;
                     next_due = next_due < 0 ? e : std::min(next_due, e);
                 }
                 if (!srv->departs.empty()) {
@@ -451,6 +670,14 @@ int mapa_serve_open(mapa_ctx ctx, int32_t topo_id, int32_t max_batch, uint32_t f
         cudaMallocHost(&srv->h_reqs, sizeof(mapa_request) * nb) != cudaSuccess ||
         cudaMallocHost(&srv->h_out, sizeof(mapa_result) * nb) != cudaSuccess ||
         cudaMallocHost(&srv->h_conflict, sizeof(int32_t) * nb) != cudaSuccess ||
+        cudaMalloc(&srv->d_life, sizeof(int64_t) * nb) != cudaSuccess ||
+        cudaMallocHost(&srv->h_life, sizeof(int64_t) * nb) != cudaSuccess ||
+        cudaMalloc(&srv->d_log_job, sizeof(int64_t) * kLogCap) != cudaSuccess ||
+        cudaMalloc(&srv->d_log_pos, sizeof(int32_t) * kLogCap) != cudaSuccess ||
+        cudaMalloc(&srv->d_log_n, sizeof(uint32_t)) != cudaSuccess ||
+        cudaMallocHost(&srv->h_log_job, sizeof(int64_t) * kLogCap) != cudaSuccess ||
+        cudaMallocHost(&srv->h_log_pos, sizeof(int32_t) * kLogCap) != cudaSuccess ||
+        cudaMallocHost(&srv->h_log_n, sizeof(uint32_t)) != cudaSuccess ||
         cudaMemcpyAsync(srv->occ, ctx->topos[topo_id].dev.occupancy, sizeof(srv->occ), cudaMemcpyDeviceToHost, st) !=
             cudaSuccess ||
         cudaStreamSynchronize(st) != cudaSuccess) {
@@ -539,6 +766,14 @@ int mapa_serve_close(mapa_server srv) {
     cudaFree(srv->d_out);
     cudaFree(srv->d_conflict);
     cudaFree(srv->d_jobs);
+    cudaFree(srv->d_life);
+    cudaFree(srv->d_log_job);
+    cudaFree(srv->d_log_pos);
+    cudaFree(srv->d_log_n);
+    if (srv->h_life) cudaFreeHost(srv->h_life);
+    if (srv->h_log_job) cudaFreeHost(srv->h_log_job);
+    if (srv->h_log_pos) cudaFreeHost(srv->h_log_pos);
+    if (srv->h_log_n) cudaFreeHost(srv->h_log_n);
     if (srv->h_reqs) cudaFreeHost(srv->h_reqs);
     if (srv->h_out) cudaFreeHost(srv->h_out);
     if (srv->h_conflict) cudaFreeHost(srv->h_conflict);

@@ -7,7 +7,9 @@
   commits, the others are decided again in order against the live occupancy;
 * departures free vertices for later arrivals; an unknown job is rejected;
 * one request per round (the plain form) reproduces sequential allocation;
-* FIFO waiting: a request that does not fit waits until a lifetime ends.
+* FIFO waiting: a request that does not fit waits until a lifetime ends;
+* lifetimes are kept on the device: a job whose lifetime ends during a
+  round's chain is freed before the chain's next decision.
 """
 
 import numpy as np
@@ -145,3 +147,30 @@ def test_fifo_request_waits_for_a_departure(M):
     # it waited for the first lifetime to end, then took a freed K4
     assert out["done_ns"][2] - out["done_ns"][0] >= life
     assert out["rounds"][2] >= 2
+
+
+def test_lifetimes_end_on_the_device_between_chain_steps(M):
+    """Three clique-4 requests in one round (straight to the chain, which
+    decides them one after another) on the 8-vertex cube mesh, whose two K4
+    differ in weight, each with a 1 ns lifetime: each job ends on the device
+    before the next decision, so all three take the same best K4 against an
+    empty machine, and nothing is held afterwards."""
+    topo = W.hybrid_cube_mesh8(W.Rng(1, 1))
+    with M.Context(0) as ctx:
+        tid = ctx.topology_load(topo)
+        k4 = ctx.pattern_load(W.pattern("clique", 4))
+        ev = M.make_events([k4] * 3, [0] * 3, lifetime_ns=[1] * 3)
+        out, counters = _serve(M, ctx, tid, ev, max_batch=8, flags=M.MAPA_SERVE_REJECT)
+        left = ctx.occupancy(tid)
+        # the same requests held until released: the second takes the other K4
+        ev = M.make_events([k4] * 3, [0] * 3)
+        held, _ = _serve(M, ctx, tid, ev, max_batch=8, flags=M.MAPA_SERVE_REJECT)
+    out = out[np.argsort(out["request_id"])]
+    held = held[np.argsort(held["request_id"])]
+    assert counters["rounds"] == 1
+    assert list(out["result"]["status"]) == [0, 0, 0]
+    tuples = {tuple(int(x) for x in out["result"]["verts"][i][:4]) for i in range(3)}
+    assert len(tuples) == 1
+    assert not out["snapshot"].any() and not np.asarray(left).any()
+    assert list(held["result"]["status"]) == [0, 0, 1]
+    assert tuple(int(x) for x in held["result"]["verts"][0][:4]) in tuples
