@@ -282,7 +282,12 @@ int mapa_result_merge(int32_t nparts, const mapa_result *parts, mapa_result *out
  * committed and shrinks after one that met an overlap or a wait (at most
  * max_batch); after a parallel pass of which fewer than half committed, the
  * next large rounds (1, 2, 4 ... 64 of them) skip it and go straight to the
- * chain, up to 64 requests each.  Lifetimes are kept on the device: a commit
+ * chain, up to 64 requests each.  Under a work budget B
+ * (mapa_ctx_set_work_budget) admission also keeps to the frontier memory of
+ * the context's concurrent groups (4 x frontier_mem_cap): a round admits
+ * requests while the sum of their largest frontiers, (1 + the topology's
+ * largest degree) x B entries of 8 + 4 W + 4 ceil(k/4) bytes each, fits (the
+ * first request of a round always enters).  Lifetimes are kept on the device: a commit
  * stamps its vertices with the device clock plus the job's lifetime, and
  * after every chain decision the vertices whose time has passed are freed
  * before the next one, so a job holds its accelerators for its lifetime

@@ -383,6 +383,10 @@ uint64_t engine_tuned_chunk(const Engine *e, int32_t topo_id, int32_t pattern_id
     return chunk_limit(e, topo_id, pattern_id);
 }
 
+uint64_t engine_frontier_budget(const Engine *e) { return e->frontier_cap * static_cast<uint64_t>(kSlots); }
+
+uint64_t engine_work_budget(const Engine *e) { return e->work_budget; }
+
 int engine_stage(Engine *e, int32_t nreq, mapa_request **reqs_dev, mapa_result **out_dev, std::string *err) {
     if (nreq > e->stage_cap) {
         cudaFree(e->stage_reqs);

@@ -179,6 +179,10 @@ void engine_stats_reset(Engine *e);
 void engine_set_timing(Engine *e, bool on);
 void engine_set_work_budget(Engine *e, uint64_t max_partials);
 uint64_t engine_tuned_chunk(const Engine *e, int32_t topo_id, int32_t pattern_id);
+// Frontier memory the concurrent groups of a batch may hold (all slots) and
+// the context's work budget (stored partial matches per request, 0 = none).
+uint64_t engine_frontier_budget(const Engine *e);
+uint64_t engine_work_budget(const Engine *e);
 
 // Allocation-free single-kernel decision (mapa_noalloc.cu).
 int noalloc_decide(const TopoDevice &t, const PatternArgs &pat, int32_t pattern_id, int32_t nreq,

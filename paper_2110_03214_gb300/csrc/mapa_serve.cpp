@@ -80,6 +80,7 @@ struct mapa_server_s {
     bool blocked = false;                          // head of the queue waits for a departure
     int32_t window = 0;                            // requests admitted per round (adaptive)
     int32_t spec_skip = 0;                         // large rounds left that go straight to the chain
+    int32_t deg_max = 0;                           // largest vertex degree of the topology
     int32_t spec_backoff = 0;                      // their number after the next parallel pass that fails
     std::unordered_map<int64_t, Job> live;         // committed jobs
     uint32_t occ[MAPA_MASK_WORDS] = {};            // host copy of the device occupancy
@@ -189,6 +190,21 @@ int release_jobs(mapa_server srv, const std::vector<int64_t> &jobs, std::string 
         return MAPA_E_CUDA;
     }
     return mapa::engine_release_many(ctx->engine, t, srv->d_jobs, static_cast<int32_t>(jobs.size()), err);
+}
+
+// Frontier memory one request of the pattern can hold under the context's
+// work budget B (0 when there is none): it stores at most B partial matches
+// before it is cut, and the level that crosses B holds at most (1 + the
+// largest degree) x B entries, each 8 + 4 W + 4 ceil(k/4) bytes (score,
+// request, free-set words, tuple words).
+uint64_t frontier_estimate(mapa_server srv, int32_t pattern_id) {
+    mapa_ctx ctx = srv->ctx;
+    const uint64_t B = mapa::engine_work_budget(ctx->engine);
+    if (B == 0 || pattern_id < 0 || pattern_id >= static_cast<int32_t>(ctx->pattern_args.size())) return 0;
+    const int W = ctx->topos[srv->topo_id].dev.W;
+    const int k = ctx->pattern_args[pattern_id].k;
+    const uint64_t entry = 8 + 4 * static_cast<uint64_t>(W) + 4 * static_cast<uint64_t>((k + 3) / 4);
+    return (1 + static_cast<uint64_t>(srv->deg_max)) * B * entry;
 }
 
 mapa::ServeLife life_args(mapa_server srv) {
@@ -597,8 +613,15 @@ void worker_loop(mapa_server srv) {
                 // while the parallel pass is backed off a round is one chain
                 const int32_t admit =
                     srv->spec_skip > 0 ? std::max(srv->window, std::min(srv->max_batch, kChainRound)) : srv->window;
+                // frontier-memory budget: under a work budget, admit while the
+                // round's requests can all hold their largest frontier at once
+                const uint64_t mem_cap = mapa::engine_frontier_budget(srv->ctx->engine);
+                uint64_t mem = 0;
                 while (!srv->incoming.empty() && srv->incoming.front().ev.at_ns <= now &&
                        static_cast<int32_t>(round.size()) < admit) {
+                    const uint64_t est = frontier_estimate(srv, srv->incoming.front().ev.pattern_id);
+                    if (!round.empty() && mem + est > mem_cap) break;
+                    mem += est;
                     round.push_back(srv->incoming.front());
                     srv->incoming.pop_front();
                 }
@@ -662,6 +685,15 @@ int mapa_serve_open(mapa_ctx ctx, int32_t topo_id, int32_t max_batch, uint32_t f
     srv->max_batch = max_batch;
     srv->fifo_wait = (flags & MAPA_SERVE_REJECT) == 0;
     srv->window = max_batch;
+    {
+        const mapa::TopoEntry &te = ctx->topos[topo_id];
+        const int32_t n = te.dev.n;
+        for (int32_t a = 0; a < n; ++a) {
+            int32_t d = 0;
+            for (int32_t b = 0; b < n; ++b) d += (a != b && te.wm[static_cast<size_t>(a) * n + b] != 0) ? 1 : 0;
+            srv->deg_max = std::max(srv->deg_max, d);
+        }
+    }
     const size_t nb = static_cast<size_t>(max_batch);
     cudaStream_t st = mapa::engine_stream(ctx->engine);
     if (cudaMalloc(&srv->d_reqs, sizeof(mapa_request) * nb) != cudaSuccess ||

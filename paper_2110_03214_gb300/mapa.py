@@ -353,9 +353,13 @@ def mapa_ctx_set_work_budget(ctx, max_partials: int) -> None:
 MAPA_SERVE_REJECT = 1
 
 
+_SERVER_CTX: dict = {}  # server handle -> its context (for the error text at close)
+
+
 def mapa_serve_open(ctx, topo_id: int, max_batch: int, flags: int = 0):
     h = ctypes.c_void_p()
     _check(ctx, lib.mapa_serve_open(ctx, topo_id, max_batch, flags, ctypes.byref(h)))
+    _SERVER_CTX[h.value] = ctx
     return h
 
 
@@ -388,9 +392,11 @@ def mapa_serve_counters(srv):
 
 
 def mapa_serve_close(srv) -> None:
+    ctx = _SERVER_CTX.pop(srv.value, None)
     rc = lib.mapa_serve_close(srv)
     if rc != MAPA_OK:
-        raise MapaError(rc, "serving loop ended with an error")
+        why = lib.mapa_last_error(ctx).decode() if ctx is not None else ""
+        raise MapaError(rc, f"serving loop ended with an error: {why}")
 
 
 def make_events(pattern_ids, at_ns, lifetime_ns=0, alpha=1, beta=1, request_ids=None, mode=0, flags=0) -> np.ndarray:

@@ -174,3 +174,29 @@ def test_lifetimes_end_on_the_device_between_chain_steps(M):
     assert not out["snapshot"].any() and not np.asarray(left).any()
     assert list(held["result"]["status"]) == [0, 0, 1]
     assert tuple(int(x) for x in held["result"]["verts"][0][:4]) in tuples
+
+
+def test_admission_keeps_to_the_frontier_memory_budget(M):
+    """Under a work budget a round admits requests only while their largest
+    frontiers fit the context's frontier memory: with B = 2^12 partials on
+    the 32-vertex graph (degree 6: at most 7 B entries of 20 bytes for
+    ring-8, 560 KiB) and a 4 MiB frontier cap (16 MiB for the four
+    concurrent groups), at most 29 of 200 waiting requests enter a round;
+    every decision still equals the one taken alone on its snapshot."""
+    wl = W.workload("regular32", num_requests=200)
+    ring8 = [i for i, p in enumerate(wl.requests.patterns) if p.name == "ring-8"][0]
+    with M.Context(0, frontier_mem_cap=4 << 20) as ctx:
+        ctx.set_work_budget(1 << 12)
+        tid = ctx.topology_load(wl.topology)
+        pids = np.asarray([ctx.pattern_load(p) for p in wl.requests.patterns], np.int32)
+        ev = M.make_events(np.full(200, pids[ring8]), np.zeros(200, np.int64))
+        out, counters = _serve(M, ctx, tid, ev, max_batch=4096, flags=M.MAPA_SERVE_REJECT)
+        out = out[np.argsort(out["request_id"])]
+        alone = M.make_requests(ev["pattern_id"], 1, 1, out["snapshot"])
+        tid2 = ctx.topology_load(wl.topology)
+        ref = ctx.allocate_batch(tid2, alone)
+    assert len(out) == 200
+    assert counters["rounds"] >= 7
+    got = out["result"].copy()
+    got["job_id"] = 0
+    assert np.array_equal(got, ref)
