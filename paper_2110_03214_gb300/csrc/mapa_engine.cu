@@ -318,6 +318,7 @@ Engine *engine_create(int device, uint64_t frontier_cap, std::string *err) {
     if (const char *ov = std::getenv("MAPA_GRAPHS")) en->use_graphs = std::atoi(ov) != 0;
     if (const char *ov = std::getenv("MAPA_TAIL_SORT")) en->tail_sorted = std::atoi(ov) != 0;
     if (const char *ov = std::getenv("MAPA_CHUNK_SINGLE_PASS")) en->chunk_single_pass = std::atoi(ov) != 0;
+    if (const char *ov = std::getenv("MAPA_DIVE_BLOCK")) en->dive_block = std::max(0, std::min(std::atoi(ov), 2));
     if (const char *ov = std::getenv("MAPA_DIVE_STEPS")) en->dive_steps = std::max(0, std::min(std::atoi(ov), 1 << 20));
     if (const char *ov = std::getenv("MAPA_BOUND_DEGREE_MIN_M")) en->degree_min_m = std::max(0, std::atoi(ov));
     if (cudaStreamCreateWithFlags(&en->own_stream, cudaStreamNonBlocking) != cudaSuccess ||

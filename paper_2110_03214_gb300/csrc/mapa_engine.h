@@ -72,6 +72,7 @@ struct Engine {
     uint64_t work_budget = 0;    // stored partial matches a request may produce (0 = no limit)
     bool chunk_single_pass = true;  // chunked levels by single-pass k_expand (MAPA_CHUNK_SINGLE_PASS=0: count + write)
     bool tail_sorted = false;    // short fused tail: parents of a tile ordered by estimated subtree size (MAPA_TAIL_SORT=1)
+    int dive_block = 2;          // guided dives on blocks: 0 never, 1 always, 2 groups below 2 x SMs (MAPA_DIVE_BLOCK)
     std::map<std::pair<int32_t, int32_t>, int> tail_table;  // (topology, pattern) -> tuned depth
     // (topology, pattern) -> tuned largest entries of a stored level (0 = as
     // many as the frontier cap allows): smaller levels make the chunked path

@@ -215,33 +215,45 @@ __device__ __forceinline__ int warp_incl_scan(int v, int lane) {
 // ----------------------------------------------------------------------------
 // Topology in shared memory
 
+// The topology in shared memory: vertex v's adjacency row at adj + v *
+// adj_stride(W), its C class rows at cls + v * cs (class c at c * W).  Both
+// strides are odd, so lanes reading rows of different vertices spread over
+// the 32 banks (a stride of W words would put word w of every vertex in one
+// of 32 / W banks).
 struct SmemTopo {
     const uint32_t *adj;
     const uint32_t *cls;
     const int32_t *wc;
     int n, C;
     int32_t wmin, wmax, dmax;
+    int cs;  // words per vertex of cls: (C W) | 1
 };
 
+__host__ __device__ constexpr int adj_stride(int W) { return W | 1; }
+__host__ __device__ constexpr int cls_stride(int C, int W) { return (C * W) | 1; }
+
 __host__ __device__ inline size_t topo_smem_bytes(int n, int W, int C, bool with_cls) {
-    size_t words = static_cast<size_t>(n) * W;
-    if (with_cls) words += static_cast<size_t>(n) * C * W + C;
+    size_t words = static_cast<size_t>(n) * adj_stride(W);
+    if (with_cls) words += static_cast<size_t>(n) * cls_stride(C, W) + C;
     return words * 4;
 }
 
 template <int W>
 __device__ __forceinline__ SmemTopo stage_topology(const TopoArgs &t, bool with_cls) {
     extern __shared__ uint32_t smem_words[];
+    constexpr int as = adj_stride(W);
+    const int cs = cls_stride(t.C, W);
     uint32_t *adj = smem_words;
-    uint32_t *cls = adj + t.n * W;
-    int32_t *wc = reinterpret_cast<int32_t *>(cls + (with_cls ? t.n * t.C * W : 0));
-    for (int i = threadIdx.x; i < t.n * W; i += blockDim.x) adj[i] = t.adj[i];
+    uint32_t *cls = adj + t.n * as;
+    int32_t *wc = reinterpret_cast<int32_t *>(cls + (with_cls ? t.n * cs : 0));
+    for (int i = threadIdx.x; i < t.n * W; i += blockDim.x) adj[(i / W) * as + i % W] = t.adj[i];
     if (with_cls) {
-        for (int i = threadIdx.x; i < t.n * t.C * W; i += blockDim.x) cls[i] = t.clsv[i];
+        const int row = t.C * W;
+        for (int i = threadIdx.x; i < t.n * row; i += blockDim.x) cls[(i / row) * cs + i % row] = t.clsv[i];
         for (int i = threadIdx.x; i < t.C; i += blockDim.x) wc[i] = t.wc[i];
     }
     __syncthreads();
-    return SmemTopo{adj, cls, wc, t.n, t.C, t.wmin, t.wmax, t.dmax};
+    return SmemTopo{adj, cls, wc, t.n, t.C, t.wmin, t.wmax, t.dmax, cs};
 }
 
 // Offset of entry p in column j of a level: capacities are at most
@@ -270,7 +282,7 @@ __device__ __forceinline__ void level_masks(const LevelView &L, uint32_t p, uint
         back &= back - 1u;
         const int x = tuple_byte(L, p, b);
 #pragma unroll
-        for (int w = 0; w < W; ++w) A[w] &= s_adj[x * W + w];
+        for (int w = 0; w < W; ++w) A[w] &= s_adj[x * adj_stride(W) + w];
         set_bit<W>(B, x);
     }
     while (lo) {
@@ -299,13 +311,13 @@ template <int W, int CT>
 struct Scorer {
     const uint32_t *cls;
     const int32_t *wc;
-    int C;
+    int C, cs;
     int32_t al, be;
     int32_t aw[CT > 0 ? CT : 1];
     int32_t bw[CT > 0 ? CT : 1];
 
     __device__ __forceinline__ Scorer(const SmemTopo &s, int32_t al_, int32_t be_)
-        : cls(s.cls), wc(s.wc), C(CT > 0 ? CT : s.C), al(al_), be(be_) {
+        : cls(s.cls), wc(s.wc), C(CT > 0 ? CT : s.C), cs(s.cs), al(al_), be(be_) {
         if constexpr (CT > 0) {
 #pragma unroll
             for (int c = 0; c < CT; ++c) {
@@ -318,7 +330,7 @@ struct Scorer {
     __device__ __forceinline__ int32_t delta(int v, const uint32_t (&B)[W], const uint32_t (&R)[W]) const {
         int32_t acc = 0;
         if constexpr (CT > 0) {
-            const uint32_t *x = cls + v * (CT * W);
+            const uint32_t *x = cls + v * cls_stride(CT, W);
 #pragma unroll
             for (int c = 0; c < CT; ++c) {
                 int pb = 0, pr = 0;
@@ -331,7 +343,7 @@ struct Scorer {
                 acc += aw[c] * pb - bw[c] * pr;
             }
         } else {
-            const uint32_t *x = cls + static_cast<size_t>(v) * C * W;
+            const uint32_t *x = cls + static_cast<size_t>(v) * cs;
             for (int c = 0; c < C; ++c) {
                 int pb = 0, pr = 0;
 #pragma unroll
@@ -393,7 +405,7 @@ __device__ __forceinline__ void keep4(int32_t (&t)[4], int32_t x) {
 // 2 g(d_u) for vertex u of R.
 template <int W>
 __device__ __forceinline__ int32_t twice_floor_loss(const SmemTopo &s, const uint32_t (&R)[W], int u, int32_t cap) {
-    const uint32_t *x = s.cls + static_cast<size_t>(u) * s.C * W;
+    const uint32_t *x = s.cls + static_cast<size_t>(u) * s.cs;
     int32_t d = 0;
     for (int c = 0; c < s.C; ++c) {
         int pc = 0;
@@ -528,7 +540,7 @@ __device__ __forceinline__ bool tail_walk(const SmemTopo &s, const Scorer<W, CT>
     for (int j = 0; j < t; ++j) {
         if ((ta.back_tail[t] >> j) & 1u) {
 #pragma unroll
-            for (int w = 0; w < W; ++w) c[w] &= s.adj[tv[j] * W + w];
+            for (int w = 0; w < W; ++w) c[w] &= s.adj[tv[j] * adj_stride(W) + w];
             set_bit<W>(B, tv[j]);
         }
         if ((ta.lo_tail[t] >> j) & 1u) lb = max(lb, tv[j]);
@@ -579,7 +591,7 @@ __global__ void k_setup(TopoArgs topo, GroupArgs g, LevelView L0, unsigned long 
         long long acc = 0;
         for (int v = lane; v < s.n; v += 32) {
             if (!((F[v >> 5] >> (v & 31)) & 1u)) continue;
-            const uint32_t *x = s.cls + static_cast<size_t>(v) * s.C * W;
+            const uint32_t *x = s.cls + static_cast<size_t>(v) * s.cs;
             for (int c = 0; c < s.C; ++c) {
                 int pc = 0;
 #pragma unroll
@@ -673,7 +685,7 @@ __device__ __forceinline__ void degree_filter(const SmemTopo &s, uint32_t (&cand
     for (int w = 0; w < W; ++w) {
         bool pass = false;
         if ((cand[w] >> lane) & 1u) {
-            const uint32_t *row = s.adj + (32 * w + lane) * W;
+            const uint32_t *row = s.adj + (32 * w + lane) * adj_stride(W);
             int c = 0;
 #pragma unroll
             for (int x = 0; x < W; ++x) c += __popc(row[x] & R[x]);
@@ -701,7 +713,7 @@ __device__ __forceinline__ void distance_balls(const SmemTopo &s, const uint32_t
         for (int w = 0; w < W; ++w)
             if ((cur[w] >> lane) & 1u)
 #pragma unroll
-                for (int x = 0; x < W; ++x) acc[x] |= s.adj[(32 * w + lane) * W + x];
+                for (int x = 0; x < W; ++x) acc[x] |= s.adj[(32 * w + lane) * adj_stride(W) + x];
 #pragma unroll
         for (int x = 0; x < W; ++x) {
 #pragma unroll
@@ -711,107 +723,175 @@ __device__ __forceinline__ void distance_balls(const SmemTopo &s, const uint32_t
     }
 }
 
-template <int W, int CT>
-__device__ bool dive_warp(const SmemTopo &s, const PatternArgs &pat, int32_t S0, const uint32_t (&F)[W], int32_t al,
-                          int32_t be, int lane, int steps, bool guided, int root_lo, int root_hi, int32_t &inc,
-                          bool &found, int &rec_v) {
-    const Scorer<W, CT> sc(s, al, be);
-    const int k = pat.k;
-    int32_t my_S = S0;
-    int my_v = 0;
+// Node-expansion limits of the guided dive: until the first match, at most
+// kRootSteps steps below one choice of phi(0), then the next one (an
+// abandoned subtree means the dive no longer proves that no match exists);
+// after the first match, at most kImproveSteps more steps to improve on it.
+constexpr int kRootSteps = 1024, kImproveSteps = 256;
+// dive_run outcomes
+constexpr int kDiveDone = 0;     // the search space is finished (proof only when nothing was abandoned)
+constexpr int kDiveCap = 1;      // step limit (or the improvement limit) reached
+constexpr int kDiveRootEnd = 2;  // one-root mode: the root's subtree ended (this step not taken)
+constexpr int kDiveFound = 3;    // one-root mode: the first match (its step taken)
+constexpr int kDiveAbort = 4;    // one-root mode: an earlier choice of phi(0) found a match
+
+// One warp's depth-first dive; lane j holds the node at depth j (pattern
+// vertices 0..j-1 placed): its score, its free set and the children not yet
+// tried; my_v is the vertex chosen for pattern vertex j, rec_v (lane j) the
+// vertex of pattern vertex j in the best complete match so far.
+template <int W>
+struct Dive {
+    int32_t my_S;
+    int my_v, rec_v;
     uint32_t my_R[W], my_rem[W], ball[W];
-    uint32_t root_cand[W];
+    int32_t inc;
+    bool found, abandoned, picked;
+    int j, step, root_steps, found_at;
+};
+
+// Candidates of pattern vertex 0 (warp-uniform): the free set, within the
+// root range of a split request's share, and for a guided dive with enough
+// free neighbours for vertex 0's pattern degree.
+template <int W>
+__device__ __forceinline__ void dive_root_candidates(const SmemTopo &s, const PatternArgs &pat, const uint32_t (&F)[W],
+                                                     bool guided, int root_lo, int root_hi, int lane,
+                                                     uint32_t (&root_cand)[W]) {
 #pragma unroll
-    for (int w = 0; w < W; ++w) {
-        my_R[w] = F[w];
-        root_cand[w] = F[w];  // pattern vertex 0: no earlier neighbour, no constraint
-        ball[w] = 0u;
-    }
+    for (int w = 0; w < W; ++w) root_cand[w] = F[w];  // pattern vertex 0: no earlier neighbour, no constraint
     if (root_hi > 0) {  // a share of a split request: phi(0) in [root_lo, root_hi)
         and_above<W>(root_cand, root_lo - 1);
         and_below<W>(root_cand, root_hi);
     }
     if (guided) degree_filter<W>(s, root_cand, F, pat.fdeg[0], lane);
+}
+
+// A fresh dive whose depth-0 node has the children root_rem left to try.
+template <int W>
+__device__ __forceinline__ void dive_init(Dive<W> &d, const uint32_t (&F)[W], const uint32_t (&root_rem)[W], int32_t S0,
+                                          int lane) {
+    d.my_S = S0;
+    d.my_v = 0;
+    d.rec_v = 0;
 #pragma unroll
-    for (int w = 0; w < W; ++w) my_rem[w] = lane == 0 ? root_cand[w] : 0u;
-    inc = INT_MIN;
-    found = false;
-    rec_v = 0;  // lane j: phi(j) of the best complete match so far
-    int j = 0;
-    // guided: until the first match, at most kRootSteps steps below one
-    // choice of phi(0), then the next one (an abandoned subtree means the
-    // dive no longer proves that no match exists)
-    // guided: after the first match, at most kImproveSteps more steps to
-    // improve on it
-    constexpr int kRootSteps = 1024, kImproveSteps = 256;
-    int root_steps = 0, found_at = 0;
-    bool abandoned = false;
-    for (int step = 0; step < steps; ++step) {
-        if (guided && !found && j > 0 && ++root_steps > kRootSteps) {
-            j = 0;
-            root_steps = 0;
-            abandoned = true;
+    for (int w = 0; w < W; ++w) {
+        d.my_R[w] = F[w];
+        d.my_rem[w] = lane == 0 ? root_rem[w] : 0u;
+        d.ball[w] = 0u;
+    }
+    d.inc = INT_MIN;
+    d.found = d.abandoned = d.picked = false;
+    d.j = d.step = d.root_steps = d.found_at = 0;
+}
+
+// Bounded mode, seed score, and anytime fallback: a depth-first branch and
+// bound, one node expansion per step, until d.step reaches steps.  Children
+// are tried best score first (ties: smaller vertex); a child whose bound
+// cannot beat the best complete score so far is skipped.  d.inc / d.found
+// hold the best complete score.
+// Guided dive (anytime requests): two necessary conditions on any match
+// narrow the candidates of pattern vertex j -- its image lies within
+// distance dist0[j] of phi(0) in the free graph (the pattern path from 0 to
+// j maps onto a walk through free vertices), and has at least fdeg[j] free
+// unused neighbours (its later pattern neighbours need distinct images).
+// Neither removes a vertex of any match, so they only steer the descent away
+// from dead ends; until the first match the child with the most free unused
+// neighbours is taken first (feasibility before score: a score-first
+// descent picks low-degree vertices, which end long patterns in dead ends).
+// one_root: stop when the subtree of the first choice of phi(0) ends (the
+// next choice is not taken) or at its first match (taken); and, when
+// *first (a shared word) drops below my_q, because the search of an earlier
+// choice found a match, which makes this one's steps irrelevant.
+template <int W, int CT>
+__device__ int dive_run(Dive<W> &d, const SmemTopo &s, const PatternArgs &pat, const uint32_t (&F)[W], int32_t al,
+                        int32_t be, int lane, int steps, bool guided, bool one_root, const int *first = nullptr,
+                        int my_q = 0) {
+    const Scorer<W, CT> sc(s, al, be);
+    const int k = pat.k;
+    for (; d.step < steps; ++d.step) {
+        if (one_root && d.picked && d.j == 0) return kDiveRootEnd;
+        if (first && __shfl_sync(kFull, *reinterpret_cast<const volatile int *>(first), 0) < my_q) return kDiveAbort;
+        if (guided && !d.found && d.j > 0 && ++d.root_steps > kRootSteps) {
+            d.abandoned = true;
+            if (one_root) return kDiveRootEnd;
+            d.j = 0;
+            d.root_steps = 0;
         }
-        if (guided && found && step - found_at > kImproveSteps) return false;
+        if (guided && d.found && d.step - d.found_at > kImproveSteps) return kDiveCap;
+        const int j = d.j;
         uint32_t rem[W], R[W];
         bool any = false;
 #pragma unroll
         for (int w = 0; w < W; ++w) {
-            rem[w] = __shfl_sync(kFull, my_rem[w], j);
-            R[w] = __shfl_sync(kFull, my_R[w], j);
+            rem[w] = __shfl_sync(kFull, d.my_rem[w], j);
+            R[w] = __shfl_sync(kFull, d.my_R[w], j);
             any |= rem[w] != 0u;
         }
-        const int32_t S = __shfl_sync(kFull, my_S, j);
+        const int32_t S = __shfl_sync(kFull, d.my_S, j);
         if (!any) {
-            if (j == 0) return !abandoned;
-            --j;
+            if (j == 0) return kDiveDone;
+            --d.j;
             continue;
         }
         uint32_t B[W];
 #pragma unroll
         for (int w = 0; w < W; ++w) B[w] = 0u;
-        for (uint32_t bm = pat.back[j]; bm; bm &= bm - 1u) set_bit<W>(B, __shfl_sync(kFull, my_v, __ffs(bm) - 1));
-        // child order: best score first (ties: smaller vertex); a guided dive
-        // that has no match yet takes the child with the most free unused
-        // neighbours first (feasibility before score; a score-first descent
-        // picks low-degree vertices, which end long patterns in dead ends)
-        const bool by_room = guided && !found;
+        for (uint32_t bm = pat.back[j]; bm; bm &= bm - 1u) set_bit<W>(B, __shfl_sync(kFull, d.my_v, __ffs(bm) - 1));
+        // the warp's pick: (most room, before the first match), then best
+        // score, then smaller vertex; before the first match only the
+        // children with the warp's most room are scored (the same pick)
+        const bool by_room = guided && !d.found;
+        int mr = 0;
+        if (by_room) {
+            int lroom = -1;  // -1: no child in this lane
+#pragma unroll
+            for (int w = 0; w < W; ++w)
+                if ((rem[w] >> lane) & 1u) {
+                    const int v = 32 * w + lane;
+                    int room = 0;
+#pragma unroll
+                    for (int y = 0; y < W; ++y) room += __popc(s.adj[v * adj_stride(W) + y] & R[y]);
+                    lroom = max(lroom, room);
+                }
+            mr = __reduce_max_sync(kFull, lroom);
+        }
         int32_t best = INT_MIN;
-        int bv = INT_MAX, broom = -1;
+        int bv = INT_MAX;
 #pragma unroll
         for (int w = 0; w < W; ++w)
             if ((rem[w] >> lane) & 1u) {
                 const int v = 32 * w + lane;
-                const int32_t x = S + sc.delta(v, B, R);
-                int room = 0;
                 if (by_room) {
+                    int room = 0;
 #pragma unroll
-                    for (int y = 0; y < W; ++y) room += __popc(s.adj[v * W + y] & R[y]);
+                    for (int y = 0; y < W; ++y) room += __popc(s.adj[v * adj_stride(W) + y] & R[y]);
+                    if (room != mr) continue;
                 }
-                if (room > broom || (room == broom && x > best)) {
+                const int32_t x = S + sc.delta(v, B, R);
+                if (x > best) {  // a lane's children come in increasing vertex order
                     best = x;
                     bv = v;
-                    broom = room;
                 }
             }
-        // the warp's pick: most room, then best score, then smaller vertex
-        // (lanes without a child hold room -1)
         {
-            const int mr = __reduce_max_sync(kFull, broom);
-            const int32_t ms = __reduce_max_sync(kFull, broom == mr ? best : INT_MIN);
-            bv = __reduce_min_sync(kFull, (broom == mr && best == ms) ? bv : INT_MAX);
+            const int32_t ms = __reduce_max_sync(kFull, bv == INT_MAX ? INT_MIN : best);
+            bv = __reduce_min_sync(kFull, (bv != INT_MAX && best == ms) ? bv : INT_MAX);
             best = ms;
-            broom = mr;
         }
         if (lane == j) {
-            clear_bit<W>(my_rem, bv);
-            my_v = bv;
+            clear_bit<W>(d.my_rem, bv);
+            d.my_v = bv;
         }
+        if (j == 0) d.picked = true;
         if (j + 1 == k) {
-            if (!found) found_at = step;
-            if (!found || best > inc) rec_v = my_v;  // lanes < k hold the path, lane j its last vertex
-            inc = found ? max(inc, best) : best;
-            found = true;
+            const bool first = !d.found;
+            if (first) d.found_at = d.step;
+            if (first || best > d.inc) d.rec_v = d.my_v;  // lanes < k hold the path, lane j its last vertex
+            d.inc = first ? best : max(d.inc, best);
+            d.found = true;
+            if (one_root && first) {
+                ++d.step;
+                return kDiveFound;
+            }
             continue;
         }
         uint32_t R1[W];
@@ -819,8 +899,8 @@ __device__ bool dive_warp(const SmemTopo &s, const PatternArgs &pat, int32_t S0,
         for (int w = 0; w < W; ++w) R1[w] = R[w];
         clear_bit<W>(R1, bv);
         // only the score matters here, so ties with the incumbent are cut too
-        if (found && cut_off_warp<W>(s, R1, best, al, be, inc == INT_MAX ? INT_MAX : inc + 1, level_bound(pat, j + 1),
-                                     lane))
+        if (d.found && cut_off_warp<W>(s, R1, best, al, be, d.inc == INT_MAX ? INT_MAX : d.inc + 1,
+                                       level_bound(pat, j + 1), lane))
             continue;
         uint32_t cand[W];
 #pragma unroll
@@ -828,13 +908,13 @@ __device__ bool dive_warp(const SmemTopo &s, const PatternArgs &pat, int32_t S0,
         int lbv = -1;
         for (uint32_t bm = pat.back[j + 1]; bm; bm &= bm - 1u) {
             const int b = __ffs(bm) - 1;
-            const int vb = b == j ? bv : __shfl_sync(kFull, my_v, b);
+            const int vb = b == j ? bv : __shfl_sync(kFull, d.my_v, b);
 #pragma unroll
-            for (int w = 0; w < W; ++w) cand[w] &= s.adj[vb * W + w];
+            for (int w = 0; w < W; ++w) cand[w] &= s.adj[vb * adj_stride(W) + w];
         }
         for (uint32_t lm = pat.lo[j + 1]; lm; lm &= lm - 1u) {
             const int a = __ffs(lm) - 1;
-            lbv = max(lbv, a == j ? bv : __shfl_sync(kFull, my_v, a));
+            lbv = max(lbv, a == j ? bv : __shfl_sync(kFull, d.my_v, a));
         }
         and_above<W>(cand, lbv);
         if (guided) {
@@ -849,32 +929,192 @@ __device__ bool dive_warp(const SmemTopo &s, const PatternArgs &pat, int32_t S0,
                     and_above<W>(reach, bv);
                     set_bit<W>(reach, bv);
                 }
-                distance_balls<W>(s, reach, bv, lane, ball);
-                root_steps = 0;
+                distance_balls<W>(s, reach, bv, lane, d.ball);
+                d.root_steps = 0;
                 // fewer than k vertices reachable: no match below this root
                 int reachable = 0;
 #pragma unroll
-                for (int w = 0; w < W; ++w) reachable += __popc(__shfl_sync(kFull, ball[w], 31));
+                for (int w = 0; w < W; ++w) reachable += __popc(__shfl_sync(kFull, d.ball[w], 31));
                 if (reachable < k) continue;
             }
             const int dd = pat.dist0[j + 1];
             if (dd < 32) {
 #pragma unroll
-                for (int w = 0; w < W; ++w) cand[w] &= __shfl_sync(kFull, ball[w], dd);
+                for (int w = 0; w < W; ++w) cand[w] &= __shfl_sync(kFull, d.ball[w], dd);
             }
             degree_filter<W>(s, cand, R1, pat.fdeg[j + 1], lane);
         }
         if (lane == j + 1) {
-            my_S = best;
+            d.my_S = best;
 #pragma unroll
             for (int w = 0; w < W; ++w) {
-                my_R[w] = R1[w];
-                my_rem[w] = cand[w];
+                d.my_R[w] = R1[w];
+                d.my_rem[w] = cand[w];
             }
         }
-        ++j;
+        ++d.j;
     }
-    return false;
+    return kDiveCap;
+}
+
+// The whole dive on one warp, for at most `steps` node expansions.  On
+// return, inc/found hold the best complete score and lane j of rec_v the
+// vertex of pattern vertex j in that match; the result is true when the
+// whole search space was finished within the step limit (nothing abandoned).
+template <int W, int CT>
+__device__ bool dive_warp(const SmemTopo &s, const PatternArgs &pat, int32_t S0, const uint32_t (&F)[W], int32_t al,
+                          int32_t be, int lane, int steps, bool guided, int root_lo, int root_hi, int32_t &inc,
+                          bool &found, int &rec_v) {
+    uint32_t root_cand[W];
+    dive_root_candidates<W>(s, pat, F, guided, root_lo, root_hi, lane, root_cand);
+    Dive<W> d;
+    dive_init<W>(d, F, root_cand, S0, lane);
+    const int code = dive_run<W, CT>(d, s, pat, F, al, be, lane, steps, guided, false);
+    inc = d.inc;
+    found = d.found;
+    rec_v = d.rec_v;
+    return code == kDiveDone && !d.abandoned;
+}
+
+// The guided dive of one request on a block of kWarps warps, with the same
+// result as dive_warp.  Until its first match the dive takes the choices of
+// phi(0) in a fixed order (most free neighbours in F, then score, then
+// vertex: the depth-0 node never changes), and the search below a choice
+// depends only on which choices came before it.  So the block takes the
+// choices in waves of kWarps, warp w searching choice w of the wave as the
+// one warp would after the earlier ones; the steps each took, summed in
+// order, tell which choice the one warp would have reached within its step
+// limit and where it would have found its first match, and that warp goes
+// on from there as the one warp would.  Returns done (as dive_warp) on
+// every thread; inc / found / rec_v are those of warp *winner (or of warp 0
+// when nothing was found).
+template <int W, int CT>
+__device__ bool dive_block(const SmemTopo &s, const PatternArgs &pat, int32_t S0, const uint32_t (&F)[W], int32_t al,
+                           int32_t be, int steps, int root_lo, int root_hi, int32_t &inc, bool &found, int &rec_v,
+                           int *winner) {
+    __shared__ int s_root[kWarps], s_used[kWarps], s_code[kWarps], s_fat[kWarps], s_ab[kWarps];
+    __shared__ int s_state, s_win, s_start, s_abandoned, s_first;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    __syncthreads();  // the previous request's dive is done with the shared words
+    const Scorer<W, CT> sc(s, al, be);
+    uint32_t root_cand[W], taken[W];  // taken: choices of phi(0) before this wave
+    dive_root_candidates<W>(s, pat, F, true, root_lo, root_hi, lane, root_cand);
+#pragma unroll
+    for (int w = 0; w < W; ++w) taken[w] = 0u;
+    Dive<W> d;
+    dive_init<W>(d, F, root_cand, S0, lane);
+    int start = 0;  // steps the one warp would have taken before this wave
+    bool abandoned = false;
+    int state = 0, win = -1;
+    for (;;) {
+        // warp 0: the next kWarps choices of phi(0), in the one warp's order
+        if (threadIdx.x == 0) s_first = kWarps;  // no choice of the wave has found a match yet
+        if (warp == 0) {
+            uint32_t left[W];
+#pragma unroll
+            for (int w = 0; w < W; ++w) left[w] = root_cand[w] & ~taken[w];
+            for (int q = 0; q < kWarps; ++q) {
+                int32_t best = INT_MIN;
+                int bv = INT_MAX, broom = -1;
+#pragma unroll
+                for (int w = 0; w < W; ++w)
+                    if ((left[w] >> lane) & 1u) {
+                        const int v = 32 * w + lane;
+                        uint32_t none[W];
+#pragma unroll
+                        for (int y = 0; y < W; ++y) none[y] = 0u;
+                        const int32_t x = S0 + sc.delta(v, none, F);
+                        int room = 0;
+#pragma unroll
+                        for (int y = 0; y < W; ++y) room += __popc(s.adj[v * adj_stride(W) + y] & F[y]);
+                        if (room > broom || (room == broom && x > best)) {
+                            best = x;
+                            bv = v;
+                            broom = room;
+                        }
+                    }
+                const int mr = __reduce_max_sync(kFull, broom);
+                const int32_t ms = __reduce_max_sync(kFull, broom == mr ? best : INT_MIN);
+                bv = __reduce_min_sync(kFull, (broom == mr && best == ms) ? bv : INT_MAX);
+                const int v = mr < 0 ? -1 : bv;
+                if (lane == 0) s_root[q] = v;
+                if (v >= 0) clear_bit<W>(left, v);
+            }
+        }
+        __syncthreads();
+        // warp w: choice w of the wave, after the earlier ones
+        const int my_root = s_root[warp];
+        if (my_root >= 0) {
+            uint32_t rem0[W];
+#pragma unroll
+            for (int w = 0; w < W; ++w) rem0[w] = root_cand[w] & ~taken[w];
+            for (int q = 0; q < warp; ++q) clear_bit<W>(rem0, s_root[q]);
+            dive_init<W>(d, F, rem0, S0, lane);
+            const int code =
+                dive_run<W, CT>(d, s, pat, F, al, be, lane, 2 * kRootSteps + 2, true, true, &s_first, warp);
+            if (code == kDiveFound && lane == 0) atomicMin(&s_first, warp);
+            if (lane == 0) {
+                s_code[warp] = code;
+                s_used[warp] = d.step;
+                s_fat[warp] = d.found_at;
+                s_ab[warp] = d.abandoned || code == kDiveCap;
+            }
+        }
+        __syncthreads();
+        // the one warp's accounting, in order
+        // states: 0 = next wave, 1 = choice s_win found the first match,
+        // 2 = no choice left (the search is finished), 3 = step limit
+        if (threadIdx.x == 0) {
+            int st = start, sw = 0, wq = -1, ab = 0;
+            for (int q = 0; q < kWarps; ++q) {
+                if (s_root[q] < 0) {  // no choice left: the one warp's next step ends the search
+                    sw = st < steps ? 2 : 3;
+                    break;
+                }
+                if (st >= steps) {
+                    sw = 3;
+                    break;
+                }
+                if (s_code[q] == kDiveFound && st + s_fat[q] < steps) {
+                    wq = q;
+                    sw = 1;
+                    break;
+                }
+                st += s_used[q];
+                ab |= s_ab[q];  // a choice abandoned before the outcome
+            }
+            if (sw == 0 && st >= steps) sw = 3;
+            s_state = sw;
+            s_win = wq;
+            s_start = st;
+            s_abandoned = ab;
+        }
+        __syncthreads();
+        state = s_state;
+        win = s_win;
+        start = s_start;
+        abandoned = abandoned || s_abandoned != 0;
+        if (state != 0) break;
+#pragma unroll
+        for (int q = 0; q < kWarps; ++q) set_bit<W>(taken, s_root[q]);
+        __syncthreads();  // the shared words are rewritten by the next wave
+    }
+    *winner = state == 1 ? win : 0;
+    const bool done = state == 2 && !abandoned;
+    if (state == 1 && warp == win) {
+        // the one warp goes on from its first match
+        d.step += start;
+        d.found_at += start;
+        dive_run<W, CT>(d, s, pat, F, al, be, lane, steps, true, false);
+    }
+    if (state != 1) {
+        d.found = false;
+        d.inc = INT_MIN;
+    }
+    inc = d.inc;
+    found = d.found;
+    rec_v = d.rec_v;
+    return done;
 }
 
 // Per bounded request (one warp each): the seed dive.  thr = the best
@@ -882,14 +1122,53 @@ __device__ bool dive_warp(const SmemTopo &s, const PatternArgs &pat, int32_t S0,
 // finished the whole search space without a match (there is none); INT_MIN
 // otherwise (no cut-offs).  An anytime request also keeps the dive's best
 // match as its fallback.
-template <int W, int CT>
 //
 // fallback = 1 (run after the enumeration, exhaustive mode): only anytime
 // requests that went past the work budget dive, for their fallback match
 // alone (no threshold is written); nothing runs when the device-driven pass
 // overflowed (*overflow: the chunked redo decides the group instead).
+// Returns 0 when request i does not dive, 1 for an unguided dive, 2 for a
+// guided one (anytime: it keeps the dive's match as its fallback).
+__device__ __forceinline__ int dive_kind(const GroupArgs &g, const mapa_request &q, int i, int fallback) {
+    const int32_t al = g.alpha[i], be = g.beta[i];
+    const bool bounded = q.policy.mode == MAPA_MODE_BOUNDED;
+    const bool anytime = (q.policy.flags & MAPA_POLICY_ANYTIME) != 0 && g.dive_s != nullptr;
+    if (g.sens || al < 0 || be < 0) return 0;
+    if (!fallback && (!bounded || g.best_valid[i] != 0)) return 0;
+    if (fallback && (bounded || !anytime || !g.work || g.work[i] <= g.work_budget || g.best_valid[i] < 0)) return 0;
+    return anytime ? 2 : 1;
+}
+
+// Writes a dive's outcome for request i (one warp; lane j of rec_v holds
+// phi(j) of the match).
+__device__ __forceinline__ void dive_outcome(const GroupArgs &g, const PatternArgs &pat, int i, int fallback,
+                                             bool anytime, bool done, bool found, int32_t inc, int rec_v, int lane) {
+    // a finished dive without a match proves there is none (cut every
+    // partial, in either mode); a found score seeds the cut-offs of the
+    // bounded mode only (an exhaustive request must count every match)
+    if (lane == 0 && !fallback) g.thr[i] = found ? inc : (done ? INT_MAX : INT_MIN);
+    // a fallback dive that finished its whole search without a match
+    // proves there is none: the request is a no-fit, not a budget end
+    if (fallback && done && !found && lane == 0) g.dive_s[i] = kDiveNoMatch;
+    if (anytime && found) {
+#pragma unroll
+        for (int w = 0; w < 8; ++w) {
+            uint32_t word = 0u;
+#pragma unroll
+            for (int b = 0; b < 4; ++b)
+                word |= static_cast<uint32_t>(__shfl_sync(kFull, rec_v, 4 * w + b) & 0xFF) << (8 * b);
+            if (lane == 0) g.dive_t[static_cast<uint64_t>(i) * 8 + w] = 4 * w < pat.k ? word : 0u;
+        }
+        if (lane == 0) g.dive_s[i] = inc;
+    }
+}
+
+// One warp per request.  block_guided: the guided dives are left to
+// k_dive_block.  An anytime request gets enough steps for several complete
+// descents (256 per pattern vertex).
+template <int W, int CT>
 __global__ void __launch_bounds__(kTpb) k_dive(TopoArgs topo, PatternArgs pat, GroupArgs g, LevelView L0, int steps,
-                                               int fallback, const int32_t *overflow) {
+                                               int fallback, const int32_t *overflow, int block_guided) {
     if (fallback && overflow && *overflow) return;
     const SmemTopo s = stage_topology<W>(topo, true);
     const int lane = threadIdx.x & 31;
@@ -897,14 +1176,9 @@ __global__ void __launch_bounds__(kTpb) k_dive(TopoArgs topo, PatternArgs pat, G
     const int nw = static_cast<int>((gridDim.x * blockDim.x) >> 5);
     for (int i = gw; i < g.size; i += nw) {
         const mapa_request &q = g.reqs[g.req_index[i]];
-        const int32_t al = g.alpha[i], be = g.beta[i];
-        const bool bounded = q.policy.mode == MAPA_MODE_BOUNDED;
-        // an anytime request keeps the dive's match as its fallback, so it
-        // gets enough steps for several complete descents
-        const bool anytime = (q.policy.flags & MAPA_POLICY_ANYTIME) != 0 && g.dive_s != nullptr;
-        if (g.sens || al < 0 || be < 0) continue;
-        if (!fallback && (!bounded || g.best_valid[i] != 0)) continue;
-        if (fallback && (bounded || !anytime || !g.work || g.work[i] <= g.work_budget || g.best_valid[i] < 0)) continue;
+        const int kind = dive_kind(g, q, i, fallback);
+        if (kind == 0 || (kind == 2 && block_guided)) continue;
+        const bool anytime = kind == 2;
         uint32_t F[W];
 #pragma unroll
         for (int w = 0; w < W; ++w) F[w] = L0.R[w * L0.cap + i];
@@ -912,26 +1186,33 @@ __global__ void __launch_bounds__(kTpb) k_dive(TopoArgs topo, PatternArgs pat, G
         bool found;
         int rec_v;
         const int my_steps = anytime ? max(steps, 256 * pat.k) : steps;
-        const bool done = dive_warp<W, CT>(s, pat, L0.S[i], F, al, be, lane, my_steps, anytime, q.root_lo, q.root_hi,
-                                           inc, found, rec_v);
-        // a finished dive without a match proves there is none (cut every
-        // partial, in either mode); a found score seeds the cut-offs of the
-        // bounded mode only (an exhaustive request must count every match)
-        if (lane == 0 && !fallback) g.thr[i] = found ? inc : (done ? INT_MAX : INT_MIN);
-        // a fallback dive that finished its whole search without a match
-        // proves there is none: the request is a no-fit, not a budget end
-        if (fallback && done && !found && lane == 0) g.dive_s[i] = kDiveNoMatch;
-        if (anytime && found) {
+        const bool done = dive_warp<W, CT>(s, pat, L0.S[i], F, g.alpha[i], g.beta[i], lane, my_steps, anytime,
+                                           q.root_lo, q.root_hi, inc, found, rec_v);
+        dive_outcome(g, pat, i, fallback, anytime, done, found, inc, rec_v, lane);
+    }
+}
+
+// The guided dives (anytime requests), one block per request (dive_block:
+// the same outcome as the one-warp dive, with the choices of phi(0) taken
+// kWarps at a time).
+template <int W, int CT>
+__global__ void __launch_bounds__(kTpb) k_dive_block(TopoArgs topo, PatternArgs pat, GroupArgs g, LevelView L0,
+                                                     int steps, int fallback, const int32_t *overflow) {
+    if (fallback && overflow && *overflow) return;
+    const SmemTopo s = stage_topology<W>(topo, true);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int i = blockIdx.x; i < g.size; i += gridDim.x) {
+        const mapa_request &q = g.reqs[g.req_index[i]];
+        if (dive_kind(g, q, i, fallback) != 2) continue;  // the same for the whole block
+        uint32_t F[W];
 #pragma unroll
-            for (int w = 0; w < 8; ++w) {
-                uint32_t word = 0u;
-#pragma unroll
-                for (int b = 0; b < 4; ++b)
-                    word |= static_cast<uint32_t>(__shfl_sync(kFull, rec_v, 4 * w + b) & 0xFF) << (8 * b);
-                if (lane == 0) g.dive_t[static_cast<uint64_t>(i) * 8 + w] = 4 * w < pat.k ? word : 0u;
-            }
-            if (lane == 0) g.dive_s[i] = inc;
-        }
+        for (int w = 0; w < W; ++w) F[w] = L0.R[w * L0.cap + i];
+        int32_t inc;
+        bool found;
+        int rec_v, winner;
+        const bool done = dive_block<W, CT>(s, pat, L0.S[i], F, g.alpha[i], g.beta[i], max(steps, 256 * pat.k),
+                                            q.root_lo, q.root_hi, inc, found, rec_v, &winner);
+        if (warp == winner) dive_outcome(g, pat, i, fallback, true, done, found, inc, rec_v, lane);
     }
 }
 
@@ -1412,7 +1693,7 @@ __global__ void __launch_bounds__(kTpb) k_last(TopoArgs topo, LevelView in, cons
 template <int W>
 __device__ __forceinline__ int32_t delta_rolled(const SmemTopo &s, int v, const uint32_t (&B)[W],
                                                 const uint32_t (&R)[W], int32_t al, int32_t be) {
-    const uint32_t *x = s.cls + static_cast<size_t>(v) * s.C * W;
+    const uint32_t *x = s.cls + static_cast<size_t>(v) * s.cs;
     int32_t acc = 0;
 #pragma unroll 1
     for (int c = 0; c < s.C; ++c) {
@@ -1435,7 +1716,7 @@ __device__ __forceinline__ int32_t delta_c(const SmemTopo &s, int v, const uint3
     if constexpr (CT == 0) {
         return delta_rolled<W>(s, v, B, R, al, be);
     } else {
-        const uint32_t *x = s.cls + v * (CT * W);
+        const uint32_t *x = s.cls + v * cls_stride(CT, W);
         int32_t acc = 0;
 #pragma unroll
         for (int c = 0; c < CT; ++c) {
@@ -1505,7 +1786,7 @@ __device__ __forceinline__ void short_tail_first(const SmemTopo &s, const LevelV
                 int u;
                 while ((u = pop_lowest<W>(x)) >= 0) {
 #pragma unroll
-                    for (int w = 0; w < W; ++w) N[w] |= s.adj[u * W + w];
+                    for (int w = 0; w < W; ++w) N[w] |= s.adj[u * adj_stride(W) + w];
                 }
 #pragma unroll
                 for (int w = 0; w < W; ++w) st.c1[w] &= N[w];
@@ -1531,7 +1812,7 @@ __device__ __forceinline__ void walk_short_tail(const SmemTopo &s, const LevelVi
             for (int w = 0; w < W; ++w) R1[w] = st.R[w];
             clear_bit<W>(R1, v1);
 #pragma unroll
-            for (int w = 0; w < W; ++w) c2[w] = R1[w] & st.A2[w] & (st.nb ? s.adj[v1 * W + w] : ~0u);
+            for (int w = 0; w < W; ++w) c2[w] = R1[w] & st.A2[w] & (st.nb ? s.adj[v1 * adj_stride(W) + w] : ~0u);
             and_above<W>(c2, st.nl ? max(st.lb2, v1) : st.lb2);
             if (!popc_mask<W>(c2)) continue;  // no leaf below: its score is not needed
             const int32_t s1 = st.S + delta_c<W, CT>(s, v1, st.B, st.R, al, be);
@@ -1875,7 +2156,7 @@ __global__ void __launch_bounds__(kTpb) k_last_coop3(TopoArgs topo, LevelView in
             clear_bit<W>(R1, v1);
             if (nb21) set_bit<W>(B2n, v1);
 #pragma unroll
-            for (int w = 0; w < W; ++w) c2[w] = R1[w] & A2s[w] & (nb21 ? s.adj[v1 * W + w] : ~0u);
+            for (int w = 0; w < W; ++w) c2[w] = R1[w] & A2s[w] & (nb21 ? s.adj[v1 * adj_stride(W) + w] : ~0u);
             and_above<W>(c2, nl21 ? max(lb2s, v1) : lb2s);
             int32_t smax = INT_MIN;
             uint32_t leaves = 0;
@@ -1888,7 +2169,7 @@ __global__ void __launch_bounds__(kTpb) k_last_coop3(TopoArgs topo, LevelView in
                 clear_bit<W>(R2, v2);
 #pragma unroll
                 for (int w = 0; w < W; ++w)
-                    c3[w] = R2[w] & A3s[w] & (nb31 ? s.adj[v1 * W + w] : ~0u) & (nb32 ? s.adj[v2 * W + w] : ~0u);
+                    c3[w] = R2[w] & A3s[w] & (nb31 ? s.adj[v1 * adj_stride(W) + w] : ~0u) & (nb32 ? s.adj[v2 * adj_stride(W) + w] : ~0u);
                 int lb = lb3s;
                 if (nl31) lb = max(lb, v1);
                 if (nl32) lb = max(lb, v2);
@@ -1991,14 +2272,14 @@ __global__ void k_resolve(TopoArgs topo, LevelView in, const unsigned long long 
 }
 
 __device__ __forceinline__ int link_class(const SmemTopo &s, int W, int x, int y) {
-    const uint32_t *row = s.cls + static_cast<size_t>(x) * s.C * W;
+    const uint32_t *row = s.cls + static_cast<size_t>(x) * s.cs;
     for (int c = 0; c < s.C; ++c)
         if ((row[c * W + (y >> 5)] >> (y & 31)) & 1u) return c;
     return -1;
 }
 
 __device__ __forceinline__ int32_t link_weight(const SmemTopo &s, int W, int x, int y) {
-    const uint32_t *row = s.cls + static_cast<size_t>(x) * s.C * W;
+    const uint32_t *row = s.cls + static_cast<size_t>(x) * s.cs;
     for (int c = 0; c < s.C; ++c)
         if ((row[c * W + (y >> 5)] >> (y & 31)) & 1u) return s.wc[c];
     return 0;
@@ -2079,7 +2360,7 @@ __global__ void k_finalize(TopoArgs topo, PatternArgs pat, GroupArgs g) {
             long long twice = 0;
             for (int v = lane; v < s.n; v += 32) {
                 if (!((rem[v >> 5] >> (v & 31)) & 1u)) continue;
-                const uint32_t *x = s.cls + static_cast<size_t>(v) * s.C * W;
+                const uint32_t *x = s.cls + static_cast<size_t>(v) * s.cs;
                 for (int c = 0; c < s.C; ++c) {
                     int pc = 0;
 #pragma unroll

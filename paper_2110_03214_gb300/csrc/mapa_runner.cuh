@@ -118,6 +118,7 @@ struct Runner {
         const int b = static_cast<int>(smem_all);
         MAPA_CUDA_TRY(cudaFuncSetAttribute(k_setup<W>, cudaFuncAttributeMaxDynamicSharedMemorySize, b));
         MAPA_CUDA_TRY(cudaFuncSetAttribute(k_dive<W, CT>, cudaFuncAttributeMaxDynamicSharedMemorySize, b));
+        MAPA_CUDA_TRY(cudaFuncSetAttribute(k_dive_block<W, CT>, cudaFuncAttributeMaxDynamicSharedMemorySize, b));
         MAPA_CUDA_TRY(cudaFuncSetAttribute(k_count<W>, cudaFuncAttributeMaxDynamicSharedMemorySize, b));
         MAPA_CUDA_TRY(cudaFuncSetAttribute(k_write<W, CT>, cudaFuncAttributeMaxDynamicSharedMemorySize, b));
         MAPA_CUDA_TRY(cudaFuncSetAttribute(k_expand<W, CT, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, b));
@@ -140,6 +141,26 @@ struct Runner {
         return MAPA_OK;
     }
 
+    // The dives of the group: one warp per request, or for guided (anytime)
+    // requests one block each where the group is too small to fill the GPU
+    // with warps (a served chain: one request); the outcome is the same.
+    int dives(int fallback, const int32_t *overflow) {
+        const unsigned dgrid = static_cast<unsigned>(std::min<uint64_t>(ceil_div(g.size, kWarps), 4096));
+        const bool block_guided = e->dive_block == 1 || (e->dive_block == 2 && g.size < 2 * e->sm_count);
+        k_dive<W, CT><<<dgrid, kTpb, smem_all, st>>>(targs, pat, g, lay.level[0], e->dive_steps, fallback, overflow,
+                                                     block_guided ? 1 : 0);
+        MAPA_CUDA_TRY(cudaGetLastError());
+        e->st.kernel_launches += 1;
+        if (block_guided) {
+            const unsigned bgrid = static_cast<unsigned>(std::min<uint64_t>(g.size, 8192));
+            k_dive_block<W, CT><<<bgrid, kTpb, smem_all, st>>>(targs, pat, g, lay.level[0], e->dive_steps, fallback,
+                                                               overflow);
+            MAPA_CUDA_TRY(cudaGetLastError());
+            e->st.kernel_launches += 1;
+        }
+        return MAPA_OK;
+    }
+
     int setup(unsigned long long *count0) {
         const unsigned sgrid = static_cast<unsigned>(std::min<uint64_t>(ceil_div(g.size, kWarps), 4096));
         k_setup<W><<<sgrid, kTpb, smem_all, st>>>(targs, g, lay.level[0], count0);
@@ -149,10 +170,8 @@ struct Runner {
         if (gr.bounded && !gr.sens) {
             // bounded mode: seed scores for the cut-offs (and the fallback
             // match of anytime requests); one warp per request, others skip
-            const unsigned dgrid = static_cast<unsigned>(std::min<uint64_t>(ceil_div(g.size, kWarps), 4096));
-            k_dive<W, CT><<<dgrid, kTpb, smem_all, st>>>(targs, pat, g, lay.level[0], e->dive_steps, 0, nullptr);
-            MAPA_CUDA_TRY(cudaGetLastError());
-            e->st.kernel_launches += 1;
+            const int rc = dives(0, nullptr);
+            if (rc != MAPA_OK) return rc;
         }
         return MAPA_OK;
     }
@@ -171,14 +190,14 @@ struct Runner {
     int finalize() {
         if (g.work && !gr.sens) {
             // exhaustive anytime requests past the budget: their fallback dive
-            const unsigned dgrid = static_cast<unsigned>(std::min<uint64_t>(ceil_div(g.size, kWarps), 4096));
-            k_dive<W, CT><<<dgrid, kTpb, smem_all, st>>>(targs, pat, g, lay.level[0], e->dive_steps, 1,
-                                                         gr.redo ? nullptr : gr.overflow);
-            MAPA_CUDA_TRY(cudaGetLastError());
-            e->st.kernel_launches += 1;
+            const int rc = dives(1, gr.redo ? nullptr : gr.overflow);
+            if (rc != MAPA_OK) return rc;
         }
-        const unsigned fgrid = static_cast<unsigned>(std::min<uint64_t>(ceil_div(g.size, 4), 4096));
-        k_finalize<W><<<fgrid, 128, smem_all, st>>>(t.args(), pat, g);  // real weights: AggBW, PreservedBW
+        // one warp per request, eight per block, at most two blocks per SM
+        // (each block stages the topology once for all its requests)
+        const unsigned fgrid =
+            static_cast<unsigned>(std::min<uint64_t>(ceil_div(g.size, kWarps), uint64_t(2) * e->sm_count));
+        k_finalize<W><<<fgrid, kTpb, smem_all, st>>>(t.args(), pat, g);  // real weights: AggBW, PreservedBW
         MAPA_CUDA_TRY(cudaGetLastError());
         e->st.kernel_launches += 1;
         e->st.requests += static_cast<uint64_t>(g.size);

@@ -338,3 +338,25 @@ def test_budget_size_does_not_change_the_boards_decisions(M):
     assert np.array_equal(got[0], got[1])
     st = got[0]["status"]
     assert int((st == M.MAPA_INEXACT).sum()) > 50 and int((st == M.MAPA_NO_FIT).sum()) >= 90
+
+
+@pytest.mark.parametrize("name,mode", [("boards256", 0), ("boards256", 1), ("dragonfly128", 0)])
+def test_block_dive_equals_the_one_warp_dive(M, monkeypatch, name, mode):
+    """The guided dive of an anytime request runs on a block, its choices of
+    phi(0) searched eight at a time; its outcome (fallback match, no-fit
+    proof, bounded-mode seed) equals that of the one-warp dive for every
+    request (MAPA_DIVE_BLOCK=0 selects the one-warp form)."""
+    wl = W.workload(name, num_requests=300)
+    out = []
+    for flag in ("0", "1"):
+        monkeypatch.setenv("MAPA_DIVE_BLOCK", flag)
+        with M.Context(0) as ctx:
+            tid = ctx.topology_load(wl.topology)
+            pids = [ctx.pattern_load(p) for p in wl.requests.patterns]
+            reqs = ctx.requests(wl.requests, pids, mode=mode)
+            reqs["flags"] |= M.MAPA_POLICY_ANYTIME
+            ctx.set_work_budget(1 << 16)
+            out.append(ctx.allocate_batch(tid, reqs))
+    assert np.array_equal(out[0], out[1])
+    if name == "boards256":
+        assert int((out[1]["status"] == M.MAPA_INEXACT).sum()) > 50
