@@ -319,6 +319,8 @@ Engine *engine_create(int device, uint64_t frontier_cap, std::string *err) {
     if (const char *ov = std::getenv("MAPA_TAIL_SORT")) en->tail_sorted = std::atoi(ov) != 0;
     if (const char *ov = std::getenv("MAPA_CHUNK_SINGLE_PASS")) en->chunk_single_pass = std::atoi(ov) != 0;
     if (const char *ov = std::getenv("MAPA_DIVE_BLOCK")) en->dive_block = std::max(0, std::min(std::atoi(ov), 2));
+    if (const char *ov = std::getenv("MAPA_DIVE_EAGER")) en->dive_eager = std::atoi(ov) != 0;
+    if (const char *ov = std::getenv("MAPA_HOST_HINT")) en->host_hint_on = std::atoi(ov) != 0;
     if (const char *ov = std::getenv("MAPA_DIVE_STEPS")) en->dive_steps = std::max(0, std::min(std::atoi(ov), 1 << 20));
     if (const char *ov = std::getenv("MAPA_BOUND_DEGREE_MIN_M")) en->degree_min_m = std::max(0, std::atoi(ov));
     if (cudaStreamCreateWithFlags(&en->own_stream, cudaStreamNonBlocking) != cudaSuccess ||
@@ -340,6 +342,14 @@ Engine *engine_create(int device, uint64_t frontier_cap, std::string *err) {
 void engine_destroy(Engine *e) {
     if (!e) return;
     cudaSetDevice(e->device);
+    for (Slot &sl : e->slots) {
+        if (sl.side) {
+            cudaStreamSynchronize(sl.side);
+            cudaStreamDestroy(sl.side);
+        }
+        if (sl.side_fork) cudaEventDestroy(sl.side_fork);
+        if (sl.side_join) cudaEventDestroy(sl.side_join);
+    }
     if (e->stream) cudaStreamSynchronize(e->stream);
     e->clear_graphs();
     for (Slot &sl : e->slots) {
@@ -758,6 +768,16 @@ int engine_run_batch(Engine *e, const TopoDevice &t, const std::vector<PatternAr
         }
     }
     if (runs.empty()) return end_batch(e, err);
+    // A group whose device-driven run overflowed in one of the last batches
+    // goes straight to the chunked path (the same result, without the
+    // overflowing pass); every kHostHintBatches batches it tries again.
+    constexpr int kHostHintBatches = 16;
+    std::vector<char> direct(runs.size(), 0);
+    if (e->host_hint_on)
+        for (size_t i = 0; i < runs.size(); ++i) {
+            auto h = e->host_hint.find({t.id, runs[i].pat->id});
+            direct[i] = h != e->host_hint.end() && h->second > 0;
+        }
     // The groups are independent: they run concurrently, one per slot (own
     // stream, arena and group arrays; round robin beyond kSlots), so one
     // group's small early levels overlap another's large ones.
@@ -808,6 +828,7 @@ int engine_run_batch(Engine *e, const TopoDevice &t, const std::vector<PatternAr
             for (int s = 0; s < nslots; ++s) MAPA_CUDA_TRY(cudaStreamWaitEvent(e->slots[s].stream, e->fork, 0));
         }
         for (size_t i = 0; i < runs.size(); ++i) {
+            if (direct[i]) continue;
             const int r = run_group(e, t, runs[i], true, err);
             if (r != MAPA_OK) return r;
         }
@@ -834,6 +855,7 @@ int engine_run_batch(Engine *e, const TopoDevice &t, const std::vector<PatternAr
             key.push_back(reinterpret_cast<int64_t>(sl.group_mem));
             key.push_back(reinterpret_cast<int64_t>(sl.stream));
         }
+        for (size_t i = 0; i < runs.size(); ++i) key.push_back(direct[i]);
         for (const GroupRun &gr : runs) {
             key.push_back(gr.pat->id);
             key.push_back(gr.g.size);
@@ -900,15 +922,27 @@ int engine_run_batch(Engine *e, const TopoDevice &t, const std::vector<PatternAr
                                   e->stream));
     MAPA_CUDA_TRY(cudaStreamSynchronize(e->stream));
     for (size_t i = 0; i < runs.size(); ++i) {
-        if (!ovf[i]) continue;
+        if (!ovf[i] && !direct[i]) continue;
         // redo on the engine's stream (the slot's memory is free by now), so
         // its results are in place before anything later on that stream
         GroupRun redo = runs[i];
         redo.stream = nullptr;
         redo.redo = true;
+        redo.detach = true;  // its dives and finish overlap the next redo
         rc = run_group(e, t, redo, false, err);
         if (rc != MAPA_OK) return rc;
     }
+    for (Slot &sl : e->slots)
+        if (sl.side_busy) {
+            MAPA_CUDA_TRY(cudaStreamWaitEvent(e->stream, sl.side_join, 0));
+            sl.side_busy = false;
+        }
+    if (e->host_hint_on)
+        for (size_t i = 0; i < runs.size(); ++i) {
+            int &h = e->host_hint[{t.id, runs[i].pat->id}];
+            if (ovf[i]) h = kHostHintBatches;
+            else if (direct[i] && h > 0) --h;
+        }
     return end_batch(e, err);
 }
 

@@ -36,6 +36,12 @@ struct Slot {
     uint64_t group_bytes = 0;
     cudaStream_t stream = nullptr;  // concurrent groups (created on first use)
     cudaEvent_t done = nullptr;
+    // eager anytime dives (and a detached run's finalize) of the slot's
+    // host-driven runs (created on first use); side_busy: work on it that the
+    // engine's stream has not joined yet
+    cudaStream_t side = nullptr;
+    cudaEvent_t side_fork = nullptr, side_join = nullptr;
+    bool side_busy = false;
 };
 constexpr int kSlots = 4;
 
@@ -73,6 +79,14 @@ struct Engine {
     bool chunk_single_pass = true;  // chunked levels by single-pass k_expand (MAPA_CHUNK_SINGLE_PASS=0: count + write)
     bool tail_sorted = false;    // short fused tail: parents of a tile ordered by estimated subtree size (MAPA_TAIL_SORT=1)
     int dive_block = 2;          // guided dives on blocks: 0 never, 1 always, 2 groups below 2 x SMs (MAPA_DIVE_BLOCK)
+    // host-driven runs under a work budget start the anytime dives at once on
+    // their slot's side stream, beside their own enumeration (MAPA_DIVE_EAGER=0:
+    // after it)
+    bool dive_eager = true;
+    // (topology, pattern) -> batches left that run the group straight on the
+    // chunked path because its device-driven run overflowed (MAPA_HOST_HINT=0: off)
+    bool host_hint_on = true;
+    std::map<std::pair<int32_t, int32_t>, int> host_hint;
     std::map<std::pair<int32_t, int32_t>, int> tail_table;  // (topology, pattern) -> tuned depth
     // (topology, pattern) -> tuned largest entries of a stored level (0 = as
     // many as the frontier cap allows): smaller levels make the chunked path
@@ -128,6 +142,7 @@ struct GroupRun {
     bool bounded = false;   // some request of the group is in bounded mode (g.thr set)
     bool sens = false;      // the group's requests are bandwidth-sensitive
     bool redo = false;      // rerun of a group whose device-driven run overflowed (on the chunked path)
+    bool detach = false;    // host-driven: finish the group on its slot's side stream (the caller joins it)
     int slot = 0;           // arena of the group
     cudaStream_t stream = nullptr;  // stream of its launches (nullptr = the engine's)
 };

@@ -1127,6 +1127,9 @@ __device__ bool dive_block(const SmemTopo &s, const PatternArgs &pat, int32_t S0
 // requests that went past the work budget dive, for their fallback match
 // alone (no threshold is written); nothing runs when the device-driven pass
 // overflowed (*overflow: the chunked redo decides the group instead).
+// fallback = 2 (eager, beside the enumeration): every anytime request of an
+// exhaustive group dives, whether or not it will pass its budget (the match
+// is used only if it does).
 // Returns 0 when request i does not dive, 1 for an unguided dive, 2 for a
 // guided one (anytime: it keeps the dive's match as its fallback).
 __device__ __forceinline__ int dive_kind(const GroupArgs &g, const mapa_request &q, int i, int fallback) {
@@ -1135,7 +1138,8 @@ __device__ __forceinline__ int dive_kind(const GroupArgs &g, const mapa_request 
     const bool anytime = (q.policy.flags & MAPA_POLICY_ANYTIME) != 0 && g.dive_s != nullptr;
     if (g.sens || al < 0 || be < 0) return 0;
     if (!fallback && (!bounded || g.best_valid[i] != 0)) return 0;
-    if (fallback && (bounded || !anytime || !g.work || g.work[i] <= g.work_budget || g.best_valid[i] < 0)) return 0;
+    if (fallback && (bounded || !anytime || !g.work || g.best_valid[i] < 0)) return 0;
+    if (fallback == 1 && g.work[i] <= g.work_budget) return 0;
     return anytime ? 2 : 1;
 }
 

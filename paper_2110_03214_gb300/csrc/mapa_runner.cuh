@@ -144,17 +144,17 @@ struct Runner {
     // The dives of the group: one warp per request, or for guided (anytime)
     // requests one block each where the group is too small to fill the GPU
     // with warps (a served chain: one request); the outcome is the same.
-    int dives(int fallback, const int32_t *overflow) {
+    int dives(int fallback, const int32_t *overflow, cudaStream_t s) {
         const unsigned dgrid = static_cast<unsigned>(std::min<uint64_t>(ceil_div(g.size, kWarps), 4096));
         const bool block_guided = e->dive_block == 1 || (e->dive_block == 2 && g.size < 2 * e->sm_count);
-        k_dive<W, CT><<<dgrid, kTpb, smem_all, st>>>(targs, pat, g, lay.level[0], e->dive_steps, fallback, overflow,
-                                                     block_guided ? 1 : 0);
+        k_dive<W, CT><<<dgrid, kTpb, smem_all, s>>>(targs, pat, g, lay.level[0], e->dive_steps, fallback, overflow,
+                                                    block_guided ? 1 : 0);
         MAPA_CUDA_TRY(cudaGetLastError());
         e->st.kernel_launches += 1;
         if (block_guided) {
             const unsigned bgrid = static_cast<unsigned>(std::min<uint64_t>(g.size, 8192));
-            k_dive_block<W, CT><<<bgrid, kTpb, smem_all, st>>>(targs, pat, g, lay.level[0], e->dive_steps, fallback,
-                                                               overflow);
+            k_dive_block<W, CT><<<bgrid, kTpb, smem_all, s>>>(targs, pat, g, lay.level[0], e->dive_steps, fallback,
+                                                              overflow);
             MAPA_CUDA_TRY(cudaGetLastError());
             e->st.kernel_launches += 1;
         }
@@ -170,7 +170,7 @@ struct Runner {
         if (gr.bounded && !gr.sens) {
             // bounded mode: seed scores for the cut-offs (and the fallback
             // match of anytime requests); one warp per request, others skip
-            const int rc = dives(0, nullptr);
+            const int rc = dives(0, nullptr, st);
             if (rc != MAPA_OK) return rc;
         }
         return MAPA_OK;
@@ -187,18 +187,33 @@ struct Runner {
         return MAPA_OK;
     }
 
-    int finalize() {
-        if (g.work && !gr.sens) {
+    // eager: the anytime dives were started beside the enumeration on the
+    // slot's side stream; finish after them -- on the side stream itself when
+    // the run is detached (once the enumeration on st is done), else on st.
+    int finalize(bool eager = false) {
+        cudaStream_t fs = st;
+        if (eager) {
+            Slot &sl = e->slots[gr.slot];
+            if (gr.detach) {
+                MAPA_CUDA_TRY(cudaEventRecord(sl.side_fork, st));
+                MAPA_CUDA_TRY(cudaStreamWaitEvent(sl.side, sl.side_fork, 0));
+                fs = sl.side;
+                sl.side_busy = true;
+            } else {
+                MAPA_CUDA_TRY(cudaStreamWaitEvent(st, sl.side_join, 0));
+            }
+        } else if (g.work && !gr.sens) {
             // exhaustive anytime requests past the budget: their fallback dive
-            const int rc = dives(1, gr.redo ? nullptr : gr.overflow);
+            const int rc = dives(1, gr.redo ? nullptr : gr.overflow, st);
             if (rc != MAPA_OK) return rc;
         }
         // one warp per request, eight per block, at most two blocks per SM
         // (each block stages the topology once for all its requests)
         const unsigned fgrid =
             static_cast<unsigned>(std::min<uint64_t>(ceil_div(g.size, kWarps), uint64_t(2) * e->sm_count));
-        k_finalize<W><<<fgrid, kTpb, smem_all, st>>>(t.args(), pat, g);  // real weights: AggBW, PreservedBW
+        k_finalize<W><<<fgrid, kTpb, smem_all, fs>>>(t.args(), pat, g);  // real weights: AggBW, PreservedBW
         MAPA_CUDA_TRY(cudaGetLastError());
+        if (fs != st) MAPA_CUDA_TRY(cudaEventRecord(e->slots[gr.slot].side_join, fs));
         e->st.kernel_launches += 1;
         e->st.requests += static_cast<uint64_t>(g.size);
         return MAPA_OK;
@@ -444,16 +459,40 @@ struct Runner {
     }
 
     int run_host() {
+        Slot &slot = e->slots[gr.slot];
+        if (slot.side_busy) {  // a detached run still uses the slot's memory
+            MAPA_CUDA_TRY(cudaStreamSynchronize(slot.side));
+            slot.side_busy = false;
+        }
         int rc = allow_smem();
         if (rc != MAPA_OK) return rc;
         rc = plan_layout(e, gr.slot, g.size, pat.k, T, W, false, t.n, &lay, err, chunk_limit(e, t.id, pat.id));
         if (rc != MAPA_OK) return rc;
         rc = setup(nullptr);
         if (rc != MAPA_OK) return rc;
+        // Under a work budget the anytime dives depend only on the request,
+        // so they start now on a side stream, beside the enumeration (a dive
+        // of a request that ends within its budget is not used).
+        const bool eager = e->dive_eager && g.work && !gr.sens;
+        if (eager) {
+            // the slot's own side stream: the dives of the batch's host-driven
+            // runs (one slot each) overlap one another as well
+            Slot &sl = e->slots[gr.slot];
+            if (!sl.side) {
+                MAPA_CUDA_TRY(cudaStreamCreateWithFlags(&sl.side, cudaStreamNonBlocking));
+                MAPA_CUDA_TRY(cudaEventCreateWithFlags(&sl.side_fork, cudaEventDisableTiming));
+                MAPA_CUDA_TRY(cudaEventCreateWithFlags(&sl.side_join, cudaEventDisableTiming));
+            }
+            MAPA_CUDA_TRY(cudaEventRecord(sl.side_fork, st));
+            MAPA_CUDA_TRY(cudaStreamWaitEvent(sl.side, sl.side_fork, 0));
+            rc = dives(2, nullptr, sl.side);
+            if (rc != MAPA_OK) return rc;
+            MAPA_CUDA_TRY(cudaEventRecord(sl.side_join, sl.side));
+        }
         rc = e->chunk_single_pass ? process_sp(0, static_cast<uint64_t>(g.size))
                                   : process(0, static_cast<uint64_t>(g.size));
         if (rc != MAPA_OK) return rc;
-        return finalize();
+        return finalize(eager);
     }
 };
 

@@ -360,3 +360,31 @@ def test_block_dive_equals_the_one_warp_dive(M, monkeypatch, name, mode):
     assert np.array_equal(out[0], out[1])
     if name == "boards256":
         assert int((out[1]["status"] == M.MAPA_INEXACT).sum()) > 50
+
+
+@pytest.mark.parametrize("env", [{"MAPA_DIVE_EAGER": "0"}, {"MAPA_HOST_HINT": "0"}])
+def test_eager_dive_and_host_hint_keep_the_results(M, monkeypatch, env):
+    """Two scheduling choices of the chunked path that must not change any
+    result: the anytime dives started beside the enumeration (side stream)
+    instead of after it, and a group sent straight to the chunked path after
+    its device-driven run overflowed.  Three batches under a 1 GiB frontier
+    cap (the first overflows, the others follow the hint) equal the same
+    batches with the choice switched off."""
+    wl = W.workload("boards256", num_requests=300)
+    out = []
+    for on in (False, True):
+        for k, v in env.items():
+            if on:
+                monkeypatch.delenv(k, raising=False)
+            else:
+                monkeypatch.setenv(k, v)
+        with M.Context(0, frontier_mem_cap=1 << 30) as ctx:
+            tid = ctx.topology_load(wl.topology)
+            pids = [ctx.pattern_load(p) for p in wl.requests.patterns]
+            reqs = ctx.requests(wl.requests, pids)
+            reqs["flags"] |= M.MAPA_POLICY_ANYTIME
+            ctx.set_work_budget(1 << 16)
+            out.append([ctx.allocate_batch(tid, reqs) for _ in range(3)])
+    for a, b in zip(out[0], out[1]):
+        assert np.array_equal(a, b)
+    assert all(np.array_equal(out[1][0], x) for x in out[1][1:])
