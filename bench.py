@@ -201,12 +201,29 @@ class NvmlSampler:
 
 
 def _kernel_source_hash() -> str:
-    """Hash of the sources that define the fused-tail kernel and its launch."""
+    """Hash of the sources that define the level and fused-tail kernels and
+    their launches (a traffic record taken on other sources is not used)."""
     h = hashlib.sha256()
     for name in ("mapa_kernels.cuh", "mapa_runner.cuh"):
         with open(os.path.join(ROOT, "paper_2110_03214_gb300", "csrc", name), "rb") as f:
             h.update(f.read())
     return h.hexdigest()[:16]
+
+
+def _expand_traffic_per_launch(workload: str, algorithmic_bytes: float):
+    """DRAM bytes per launch of the level expansion: the committed ncu ratio
+    of DRAM bytes to algorithmic frontier bytes over every expansion launch
+    of a smaller batch of the same workload, times the algorithmic bytes of an
+    average launch; None when the kernel source changed since the capture."""
+    path = os.path.join(ROOT, "profiles", "k_expand_traffic.json")
+    try:
+        with open(path) as f:
+            rec = json.load(f)
+    except OSError:
+        return None
+    if rec.get("source_sha256_16") != _kernel_source_hash() or rec.get("workload") != workload:
+        return None
+    return rec["dram_bytes_per_algorithmic_byte"] * algorithmic_bytes
 
 
 def _traffic_per_launch(workload: str, parents_per_launch: float):
@@ -363,7 +380,7 @@ def served_sweep(M, W, kmax: int = 16, rates=(1e3, 1e4, 1e5, 1e6), budget: int =
     matches (so an oversized request cannot stall the queue)."""
     out = []
     for rate in rates:
-        count = int(min(3000, max(1000, rate * 1.0)))
+        count = int(min(3000, max(2000, rate * 1.0)))
         row = {"rate_per_s": rate}
         for mb, key in ((4096, "batched"), (1, "plain")):
             row[key] = served_measure(M, W, rate, count, mb, kmax=kmax, mode=0, flags=2, budget=budget)
@@ -635,11 +652,14 @@ def roofline(r, peaks, peak_src, int_peak):
         achieved = bytes_per_launch / (launch_ms / 1000.0) / 1e9
         peak = float(peaks["hbm_gbs"])
         return {"bound": "hbm", "kernel": "level expansion (k_expand, or k_count + k_write when chunked)",
-                "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak, "traffic": None,
+                "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                "traffic": _expand_traffic_per_launch(r["wl"].name, bytes_per_launch),
                 "peak_source": f"{peak_src} hbm_gbs (copy bandwidth)",
                 "algorithmic_bytes_per_launch": bytes_per_launch, "launch_ms": launch_ms,
                 "launches_per_step": st["expand_launches"] / n, "share_of_step": exp_ms / step_ms,
                 "tail_share_of_step": tail_ms / step_ms,
+                "rest_of_step": "anytime dives (one warp per request, beside the chunked enumeration), budget "
+                                "counts, set-up and finish",
                 "measured": "separate 3-step pass, CUDA events around each launch on its stream, groups serial"}
     launch_ms = st["tail_ms"] / max(1, st["tail_launches"])
     ops_per_launch = st["tail_int_ops"] / max(1, st["tail_launches"])
