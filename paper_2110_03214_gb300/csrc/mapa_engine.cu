@@ -771,12 +771,12 @@ int engine_run_batch(Engine *e, const TopoDevice &t, const std::vector<PatternAr
     // A group whose device-driven run overflowed in one of the last batches
     // goes straight to the chunked path (the same result, without the
     // overflowing pass); every kHostHintBatches batches it tries again.
-    constexpr int kHostHintBatches = 16;
+    constexpr int kHostHintBatches = 16, kHostHintMax = 1024;
     std::vector<char> direct(runs.size(), 0);
     if (e->host_hint_on)
         for (size_t i = 0; i < runs.size(); ++i) {
             auto h = e->host_hint.find({t.id, runs[i].pat->id});
-            direct[i] = h != e->host_hint.end() && h->second > 0;
+            direct[i] = h != e->host_hint.end() && h->second.first > 0;
         }
     // The groups are independent: they run concurrently, one per slot (own
     // stream, arena and group arrays; round robin beyond kSlots), so one
@@ -937,11 +937,16 @@ int engine_run_batch(Engine *e, const TopoDevice &t, const std::vector<PatternAr
             MAPA_CUDA_TRY(cudaStreamWaitEvent(e->stream, sl.side_join, 0));
             sl.side_busy = false;
         }
+    // a retry that overflows again doubles the wait before the next one
     if (e->host_hint_on)
         for (size_t i = 0; i < runs.size(); ++i) {
-            int &h = e->host_hint[{t.id, runs[i].pat->id}];
-            if (ovf[i]) h = kHostHintBatches;
-            else if (direct[i] && h > 0) --h;
+            auto &h = e->host_hint[{t.id, runs[i].pat->id}];  // (batches left, period)
+            if (ovf[i]) {
+                h.second = h.second ? std::min(2 * h.second, kHostHintMax) : kHostHintBatches;
+                h.first = h.second;
+            } else if (direct[i] && h.first > 0) {
+                --h.first;
+            }
         }
     return end_batch(e, err);
 }
@@ -1120,7 +1125,10 @@ int engine_autotune(Engine *e, const TopoDevice &t, const std::vector<PatternArg
     cudaEvent_t ev0, ev1;
     MAPA_CUDA_TRY(cudaEventCreate(&ev0));
     MAPA_CUDA_TRY(cudaEventCreate(&ev1));
-    const bool timing = e->timing, graphs = e->use_graphs;
+    const bool timing = e->timing, graphs = e->use_graphs, hint = e->host_hint_on;
+    // every trial runs the device-driven pass first: a setting whose levels
+    // overflow pays for it here as it does whenever its group is retried
+    e->host_hint_on = false;
     e->timing = false;
     e->use_graphs = false;  // time the launches themselves, not graph capture and instantiation
     const mapa_stats saved = e->st;
@@ -1181,6 +1189,8 @@ int engine_autotune(Engine *e, const TopoDevice &t, const std::vector<PatternArg
     e->st = saved;
     e->timing = timing;
     e->use_graphs = graphs;
+    e->host_hint_on = hint;
+    e->host_hint.clear();  // overflows seen while trying settings say nothing about the kept ones
     cudaEventDestroy(ev0);
     cudaEventDestroy(ev1);
     return rc;

@@ -83,10 +83,11 @@ struct Engine {
     // their slot's side stream, beside their own enumeration (MAPA_DIVE_EAGER=0:
     // after it)
     bool dive_eager = true;
-    // (topology, pattern) -> batches left that run the group straight on the
-    // chunked path because its device-driven run overflowed (MAPA_HOST_HINT=0: off)
+    // (topology, pattern) -> (batches left that run the group straight on the
+    // chunked path because its device-driven run overflowed, the current wait
+    // between retries) (MAPA_HOST_HINT=0: off)
     bool host_hint_on = true;
-    std::map<std::pair<int32_t, int32_t>, int> host_hint;
+    std::map<std::pair<int32_t, int32_t>, std::pair<int, int>> host_hint;
     std::map<std::pair<int32_t, int32_t>, int> tail_table;  // (topology, pattern) -> tuned depth
     // (topology, pattern) -> tuned largest entries of a stored level (0 = as
     // many as the frontier cap allows): smaller levels make the chunked path
