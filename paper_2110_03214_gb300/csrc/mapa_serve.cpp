@@ -499,11 +499,9 @@ int decide_round(mapa_server srv, std::vector<Pending> &round, std::vector<mapa_
     bool final_no_fit_done = false;
     for (int32_t i = 0; i < n; ++i) {
         if (!deferred[i]) continue;
-        bool committed_this_round = false;
-        for (int32_t j = 0; j < n; ++j)
-            if (!deferred[j] && placed(res[j].status) && res[j].job_id > 0) committed_this_round = true;
-        const bool nothing_to_release = srv->live.empty() && srv->expiries.empty() && srv->departs.empty() &&
-                                        !committed_this_round;
+        // the jobs this round committed are live by now (published), unless
+        // the device already ended their lifetime
+        const bool nothing_to_release = srv->live.empty() && srv->expiries.empty() && srv->departs.empty();
         if (!final_no_fit_done && res[i].status == MAPA_NO_FIT && nothing_to_release) {
             deferred[i] = 0;  // answered: it cannot fit on what the server can free
             final_no_fit_done = true;
@@ -626,6 +624,10 @@ void worker_loop(mapa_server srv) {
                     srv->incoming.pop_front();
                 }
             }
+            // a head that waits for accelerators while nothing can be released
+            // any more is decided again (and answered MAPA_NO_FIT)
+            if (srv->blocked && srv->live.empty() && srv->expiries.empty() && srv->departs.empty())
+                srv->blocked = false;
             if (round.empty() && departing.empty() && out.empty()) {
                 int64_t next_due = -1;
                 if (!srv->blocked && !srv->incoming.empty()) next_due = srv->incoming.front().ev.at_ns;

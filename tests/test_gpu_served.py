@@ -200,3 +200,22 @@ def test_admission_keeps_to_the_frontier_memory_budget(M):
     got = out["result"].copy()
     got["job_id"] = 0
     assert np.array_equal(got, ref)
+
+
+def test_fifo_head_is_answered_when_its_round_released_everything(M):
+    """FIFO waiting with a job that ends inside its own round: the first
+    request commits a K4 with a 1 ns lifetime (freed on the device before the
+    next decision), the second asks for a K8, which the 8-vertex cube mesh
+    does not hold, and waits at the head of the queue.  Nothing is left to
+    release, so it is answered MAPA_NO_FIT at once (no wait for a departure
+    that cannot come), and the request behind it is decided next."""
+    topo = W.hybrid_cube_mesh8(W.Rng(1, 1))
+    with M.Context(0) as ctx:
+        tid = ctx.topology_load(topo)
+        k4 = ctx.pattern_load(W.pattern("clique", 4))
+        k8 = ctx.pattern_load(W.pattern("clique", 8))
+        ev = M.make_events([k4, k8, k4], [0, 0, 0], lifetime_ns=[1, 0, 0])
+        out, counters = _serve(M, ctx, tid, ev, max_batch=8)
+    out = out[np.argsort(out["request_id"])]
+    assert list(out["result"]["status"]) == [0, 1, 0]
+    assert counters["decisions"] == 3
