@@ -69,7 +69,7 @@ struct TopoArgs {
 // One frontier level in structure-of-arrays form, `cap` entries per column.
 //   S[i]                      partial score of entry i
 //   r[i]                      request index within the group
-//   R[w * cap + i]            free vertices not yet used (word w)
+//   R[i * W + w]              free vertices not yet used (word w; an entry's words together)
 //   T[j * cap + i]            tuple bytes 4j..4j+3 (phi of pattern vertices)
 //   root != 0 (level 0 only): T[i] holds the request's range of phi(0),
 //   root_lo | root_hi << 16 (root_hi = 0: no restriction)

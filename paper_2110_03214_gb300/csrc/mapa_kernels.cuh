@@ -262,6 +262,44 @@ __device__ __forceinline__ uint32_t col_at(const LevelView &L, uint32_t j, uint3
     return j * static_cast<uint32_t>(L.cap) + p;
 }
 
+// The free set R of entry p: its W words are stored together at R + p W
+// (entry-major), so a thread moves them with W / 4 16-byte accesses (8 or
+// 4 bytes for W = 2, 1) and a warp's accesses to 32 consecutive entries
+// cover 128 W contiguous bytes.  Arena columns start 256-byte aligned.
+template <int W>
+__device__ __forceinline__ void load_R(const LevelView &L, uint64_t p, uint32_t (&R)[W]) {
+    if constexpr (W % 4 == 0) {
+        const uint4 *src = reinterpret_cast<const uint4 *>(L.R + p * W);
+#pragma unroll
+        for (int q = 0; q < W / 4; ++q) {
+            const uint4 x = src[q];
+            R[4 * q] = x.x;
+            R[4 * q + 1] = x.y;
+            R[4 * q + 2] = x.z;
+            R[4 * q + 3] = x.w;
+        }
+    } else if constexpr (W == 2) {
+        const uint2 x = reinterpret_cast<const uint2 *>(L.R)[p];
+        R[0] = x.x;
+        R[1] = x.y;
+    } else {
+        R[0] = L.R[p];
+    }
+}
+
+template <int W>
+__device__ __forceinline__ void store_R(const LevelView &L, uint64_t p, const uint32_t (&R)[W]) {
+    if constexpr (W % 4 == 0) {
+        uint4 *dst = reinterpret_cast<uint4 *>(L.R + p * W);
+#pragma unroll
+        for (int q = 0; q < W / 4; ++q) dst[q] = make_uint4(R[4 * q], R[4 * q + 1], R[4 * q + 2], R[4 * q + 3]);
+    } else if constexpr (W == 2) {
+        reinterpret_cast<uint2 *>(L.R)[p] = make_uint2(R[0], R[1]);
+    } else {
+        L.R[p] = R[0];
+    }
+}
+
 __device__ __forceinline__ int tuple_byte(const LevelView &L, uint32_t p, int j) {
     return static_cast<int>((L.T[col_at(L, static_cast<uint32_t>(j >> 2), p)] >> ((j & 3) * 8)) & 0xFFu);
 }
@@ -615,8 +653,10 @@ __global__ void k_setup(TopoArgs topo, GroupArgs g, LevelView L0, unsigned long 
             const long long wfree = acc / 2;
             L0.S[i] = state == 0 ? static_cast<int32_t>(be * wfree) : 0;
             L0.r[i] = static_cast<uint32_t>(i);
+            uint32_t F0[W];
 #pragma unroll
-            for (int w = 0; w < W; ++w) L0.R[w * L0.cap + i] = state == 0 ? F[w] : 0u;
+            for (int w = 0; w < W; ++w) F0[w] = state == 0 ? F[w] : 0u;
+            store_R<W>(L0, i, F0);
             L0.T[i] = q.root_hi ? (static_cast<uint32_t>(q.root_lo) | (static_cast<uint32_t>(q.root_hi) << 16)) : 0u;
             g.alpha[i] = al;
             g.beta[i] = be;
@@ -1184,8 +1224,7 @@ __global__ void __launch_bounds__(kTpb) k_dive(TopoArgs topo, PatternArgs pat, G
         if (kind == 0 || (kind == 2 && block_guided)) continue;
         const bool anytime = kind == 2;
         uint32_t F[W];
-#pragma unroll
-        for (int w = 0; w < W; ++w) F[w] = L0.R[w * L0.cap + i];
+        load_R<W>(L0, i, F);
         int32_t inc;
         bool found;
         int rec_v;
@@ -1209,8 +1248,7 @@ __global__ void __launch_bounds__(kTpb) k_dive_block(TopoArgs topo, PatternArgs 
         const mapa_request &q = g.reqs[g.req_index[i]];
         if (dive_kind(g, q, i, fallback) != 2) continue;  // the same for the whole block
         uint32_t F[W];
-#pragma unroll
-        for (int w = 0; w < W; ++w) F[w] = L0.R[w * L0.cap + i];
+        load_R<W>(L0, i, F);
         int32_t inc;
         bool found;
         int rec_v, winner;
@@ -1248,9 +1286,9 @@ __global__ void __launch_bounds__(kTpb, W >= 4 ? 4 : 1) k_count(TopoArgs topo, L
             level_masks<W>(in, p, back, lo, s.adj, A, B, lb);
             root_range<W>(in, static_cast<uint32_t>(p), A, lb);
             uint32_t R[W];
+            load_R<W>(in, p, R);
 #pragma unroll
             for (int w = 0; w < W; ++w) {
-                R[w] = in.R[w * in.cap + p];
                 c[w] = R[w] & A[w];
             }
             and_above<W>(c, lb);
@@ -1319,8 +1357,7 @@ __device__ __forceinline__ void emit_children(const SmemTopo &s, const LevelView
             out.S[o] = Ss + d;
             out.r[o] = rs;
             clear_bit<W>(Rs, v);
-#pragma unroll
-            for (int w = 0; w < W; ++w) out.R[col_at(out, w, o)] = Rs[w];
+            store_R<W>(out, o, Rs);
             for (int jw = 0; jw < nw_in; ++jw) {
                 uint32_t word = in.T[col_at(in, jw, ps)];
                 if (jw == new_word) word |= static_cast<uint32_t>(v) << new_shift;
@@ -1339,9 +1376,9 @@ __device__ __forceinline__ void parent_state(const SmemTopo &s, const LevelView 
     int lb;
     level_masks<W>(in, p, back, lo, s.adj, A, B, lb);
     root_range<W>(in, p, A, lb);
+    load_R<W>(in, p, R);
 #pragma unroll
     for (int w = 0; w < W; ++w) {
-        R[w] = in.R[col_at(in, w, p)];
         cand[w] = R[w] & A[w];
     }
     and_above<W>(cand, lb);
@@ -1605,8 +1642,7 @@ __global__ void __launch_bounds__(kTpb) k_last(TopoArgs topo, LevelView in, cons
                 bcnt = 0ull;
             }
             uint32_t R[W];
-#pragma unroll
-            for (int w = 0; w < W; ++w) R[w] = in.R[w * in.cap + p];
+            load_R<W>(in, p, R);
             if constexpr (Bnd) {
                 if (cut_off<W>(s, R, in.S[p], alpha[r], beta[r], thr[r], ta.bound)) continue;
             }
@@ -1760,9 +1796,9 @@ __device__ __forceinline__ void short_tail_first(const SmemTopo &s, const LevelV
     st.S = in.S[p];
     level_masks<W>(in, p, ta.back_old[0], ta.lo_old[0], s.adj, st.A, st.B, st.lb);
     root_range<W>(in, p, st.A, st.lb);
+    load_R<W>(in, p, st.R);
 #pragma unroll
     for (int w = 0; w < W; ++w) {
-        st.R[w] = in.R[col_at(in, w, p)];
         st.c1[w] = st.R[w] & st.A[w];
     }
     and_above<W>(st.c1, st.lb);
@@ -2101,9 +2137,9 @@ __global__ void __launch_bounds__(kTpb) k_last_coop3(TopoArgs topo, LevelView in
             root_range<W>(in, p, A1, lb1);
             level_masks<W>(in, p, ta.back_old[1], ta.lo_old[1], s.adj, A2, B2, lb2);
             level_masks<W>(in, p, ta.back_old[2], ta.lo_old[2], s.adj, A3, B3, lb3);
+            load_R<W>(in, p, R);
 #pragma unroll
             for (int w = 0; w < W; ++w) {
-                R[w] = in.R[col_at(in, w, static_cast<uint32_t>(p))];
                 c1[w] = R[w] & A1[w];
             }
             and_above<W>(c1, lb1);
@@ -2242,8 +2278,7 @@ __global__ void k_resolve(TopoArgs topo, LevelView in, const unsigned long long 
         TailPre<W, T> pre;
         tail_precompute<W, T>(in, p, ta, s.adj, pre);
         uint32_t R[W];
-#pragma unroll
-        for (int w = 0; w < W; ++w) R[w] = in.R[w * in.cap + p];
+        load_R<W>(in, p, R);
         const Scorer<W, CT> sc(s, g.alpha[r], g.beta[r]);
         FindLeaf<T> leaf;
         leaf.target = target;
