@@ -280,9 +280,11 @@ int mapa_result_merge(int32_t nparts, const mapa_result *parts, mapa_result *out
  * round of n), and each segment's decisions are published when it ends.
  * Admission: the window doubles after a round whose parallel decisions all
  * committed and shrinks after one that met an overlap or a wait (at most
- * max_batch); after a parallel pass of which fewer than half committed, the
- * next large rounds (1, 2, 4 ... 64 of them) skip it and go straight to the
- * chain, up to 64 requests each.  Under a work budget B
+ * max_batch); the parallel pass runs for rounds of at least 16 requests that
+ * arrived faster than the chain decides (their mean arrival gap below the
+ * chain's measured time per decision); after a parallel pass of which fewer
+ * than half committed, the next large rounds (1, 2, 4 ... 64 of them) skip
+ * it and go straight to the chain, up to 64 requests each.  Under a work budget B
  * (mapa_ctx_set_work_budget) admission also keeps to the frontier memory of
  * the context's concurrent groups (4 x frontier_mem_cap): a round admits
  * requests while the sum of their largest frontiers, (1 + the topology's

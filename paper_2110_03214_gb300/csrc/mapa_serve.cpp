@@ -82,6 +82,7 @@ struct mapa_server_s {
     int32_t spec_skip = 0;                         // large rounds left that go straight to the chain
     int32_t deg_max = 0;                           // largest vertex degree of the topology
     int32_t spec_backoff = 0;                      // their number after the next parallel pass that fails
+    double chain_ns = 100000.0;                    // device chain time per decision (running mean)
     std::unordered_map<int64_t, Job> live;         // committed jobs
     uint32_t occ[MAPA_MASK_WORDS] = {};            // host copy of the device occupancy
     std::atomic<uint64_t> rounds{0}, decisions{0}, conflicts{0};
@@ -325,7 +326,10 @@ int decide_round(mapa_server srv, std::vector<Pending> &round, std::vector<mapa_
     // The parallel pass pays when most of its decisions commit; after one
     // where fewer than half did, the next large rounds skip it (exponential
     // back-off), since the chain redoes what overlaps anyway.
-    const bool speculate = n >= kSpeculateMin && srv->spec_skip == 0;
+    // It also pays only when requests arrive faster than the chain decides
+    // them (otherwise the chain keeps up, and publishes each decision sooner).
+    const double gap = n > 1 ? static_cast<double>(round.back().ev.at_ns - round.front().ev.at_ns) / (n - 1) : 0.0;
+    const bool speculate = n >= kSpeculateMin && srv->spec_skip == 0 && gap < srv->chain_ns;
     if (n >= kSpeculateMin && srv->spec_skip > 0) --srv->spec_skip;
     std::vector<int64_t> done_at(n, -1);
     // jobs of this round that the device freed before they were published
@@ -449,6 +453,7 @@ int decide_round(mapa_server srv, std::vector<Pending> &round, std::vector<mapa_
         lf.host_log_job = srv->h_log_job;
         lf.host_log_pos = srv->h_log_pos;
         lf.host_first = kLogFirst;
+        const int64_t t_seg0 = srv->now_ns();
         rc = clear_log(srv, err);
         if (rc == MAPA_OK)
             rc = mapa::engine_run_chain(ctx->engine, t, ctx->pattern_args, m, chain_pids.data() + c0,
@@ -457,6 +462,8 @@ int decide_round(mapa_server srv, std::vector<Pending> &round, std::vector<mapa_
         std::vector<std::pair<int32_t, int64_t>> log;
         if (rc == MAPA_OK) rc = read_log(srv, log, err, true);
         if (rc != MAPA_OK) return rc;
+        const int64_t t_seg = srv->now_ns();
+        srv->chain_ns = 0.9 * srv->chain_ns + 0.1 * static_cast<double>(t_seg - t_seg0) / m;
         // replay the segment on the host mask in device order: what was
         // freed before decision j, then decision j
         size_t li = 0;

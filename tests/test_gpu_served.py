@@ -73,19 +73,19 @@ def test_arrival_order_commit_and_conflict_redo(M):
     with M.Context(0) as ctx:
         tid = ctx.topology_load(topo)
         k4 = ctx.pattern_load(W.pattern("clique", 4))
-        # 16 requests: large enough for the parallel pass
-        ev = M.make_events([k4] * 16, [0] * 16)
+        # 48 requests arriving together: the parallel pass runs
+        ev = M.make_events([k4] * 48, [0] * 48)
         out, counters = _serve(M, ctx, tid, ev, max_batch=64, flags=M.MAPA_SERVE_REJECT)
     out = out[np.argsort(out["request_id"])]
     st = out["result"]["status"]
-    assert list(st) == [0, 0] + [1] * 14  # two K4 exist; the others find none
-    # all sixteen chose the same K4 against the shared snapshot; the first
+    assert list(st) == [0, 0] + [1] * 46  # two K4 exist; the others find none
+    # all 48 chose the same K4 against the shared snapshot; the first
     # commits, the rest are decided again in arrival order in the same round
-    assert list(out["rounds"]) == [1] + [2] * 15
-    assert counters["conflicts"] == 15 and counters["rounds"] == 1
+    assert list(out["rounds"]) == [1] + [2] * 47
+    assert counters["conflicts"] == 47 and counters["rounds"] == 1
     first, second = (set(out["result"]["verts"][i][:4].tolist()) for i in (0, 1))
     assert first.isdisjoint(second) and first | second == set(range(8))
-    assert [bin(int(x[0])).count("1") for x in out["snapshot"]] == [0, 4] + [8] * 14
+    assert [bin(int(x[0])).count("1") for x in out["snapshot"]] == [0, 4] + [8] * 46
 
 
 def test_departure_frees_vertices(M):
