@@ -378,8 +378,8 @@ int mapa_serve_close(mapa_server srv);
  * while a CUDA graph is being captured on its thread, a hook running inside
  * another framework's allocator, or a process whose device memory a serving
  * runtime has fully reserved.  This call launches one kernel whose scratch
- * (per-request argmax keys, match counts and a completion ticket) is a fixed
- * 64 KiB + 256 B device array compiled into the library; every GPU that
+ * (per-request argmax keys, match counts and completion tickets) is a fixed
+ * 80 KiB device array compiled into the library; every GPU that
  * loads the library holds it until the process exits.  Nothing is allocated,
  * freed or committed.
  *

@@ -7,9 +7,9 @@
 // runtime.  For them this file decides small batches (up to 4096 requests on
 // servers of up to 32 accelerators, patterns of up to 8 vertices) with one
 // kernel launch and no allocation: the kernel's scratch -- per-request argmax
-// keys, match counts and a completion ticket -- lives in the file-scope
+// keys, match counts and completion tickets -- lives in the file-scope
 // device array below, which every GPU that loads this library holds until the
-// process exits (64 KiB + 256 B per GPU).
+// process exits (80 KiB per GPU).
 //
 // The enumeration is the same one the batched engine runs (matches in
 // pattern-id order under the automorphism order constraints, scores grown by
@@ -33,8 +33,11 @@ constexpr int kNaMaxN = MAPA_NOALLOC_MAX_N;
 constexpr int kNaMaxK = MAPA_NOALLOC_MAX_K;
 constexpr int kNaItems = kNaMaxN * kNaMaxN;  // (phi(0), phi(1)) pairs per request
 constexpr int kNaThreads = 256;
+constexpr int kNaBlocksPerRequest = kNaItems / kNaThreads;  // a block's items belong to one request
+static_assert(kNaItems % kNaThreads == 0, "a block must cover items of one request only");
 constexpr size_t kNaKeyBytes = sizeof(unsigned long long) * kNaMaxRequests;
-constexpr size_t kNaScratchBytes = 2 * kNaKeyBytes + 256;  // keys, counts, ticket
+constexpr size_t kNaTicketBytes = sizeof(unsigned int) * kNaMaxRequests;
+constexpr size_t kNaScratchBytes = 2 * kNaKeyBytes + kNaTicketBytes;  // keys, counts, tickets
 
 // Kernel scratch shared by every call on a device (see mapa.h for the rules).
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNaScratchBytes];
@@ -171,7 +174,7 @@ __global__ void __launch_bounds__(kNaThreads)
     __syncthreads();
     unsigned long long *keys = reinterpret_cast<unsigned long long *>(scratch);
     unsigned long long *counts = reinterpret_cast<unsigned long long *>(scratch + kNaKeyBytes);
-    unsigned int *ticket = reinterpret_cast<unsigned int *>(scratch + 2 * kNaKeyBytes);
+    unsigned int *tickets = reinterpret_cast<unsigned int *>(scratch + 2 * kNaKeyBytes);
 
     // ---- enumerate: thread = (request, phi(0), phi(1))
     const long long g = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x;
@@ -214,16 +217,18 @@ __global__ void __launch_bounds__(kNaThreads)
         atomicAdd(counts + r, cnt);
     }
 
-    // ---- the last block to finish resolves and writes every result
+    // ---- the last of a request's blocks to finish resolves and writes its
+    // result (every block's items belong to one request)
+    const int rb = static_cast<int>((static_cast<long long>(blockIdx.x) * blockDim.x) / kNaItems);
     __syncthreads();
     if (threadIdx.x == 0) {
         __threadfence();
-        s_last = atomicAdd(ticket, 1u) == gridDim.x - 1;
+        s_last = rb < nreq && atomicAdd(tickets + rb, 1u) == kNaBlocksPerRequest - 1;
     }
     __syncthreads();
     if (!s_last) return;
     __threadfence();
-    for (int i = threadIdx.x; i < nreq; i += blockDim.x) {
+    for (int i = rb + static_cast<int>(threadIdx.x); i == rb; ++i) {  // thread 0 only
         const mapa_request q = reqs[i];
         mapa_result res;
         memset(&res, 0, sizeof(res));
@@ -333,10 +338,10 @@ int noalloc_decide(const TopoDevice &t, const PatternArgs &pat, int32_t pattern_
         scratch = g_scratch_ptr[dev];
     }
     unsigned char *base = static_cast<unsigned char *>(scratch);
-    // keys, counts and the ticket must start at zero on every call
+    // keys, counts and tickets must start at zero on every call
     e = cudaMemsetAsync(base, 0, sizeof(unsigned long long) * nreq, stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(base + kNaKeyBytes, 0, sizeof(unsigned long long) * nreq, stream);
-    if (e == cudaSuccess) e = cudaMemsetAsync(base + 2 * kNaKeyBytes, 0, 256, stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(base + 2 * kNaKeyBytes, 0, sizeof(unsigned int) * nreq, stream);
     if (e != cudaSuccess) {
         if (err) *err = std::string("cudaMemsetAsync: ") + cudaGetErrorString(e);
         return MAPA_E_CUDA;
