@@ -112,8 +112,10 @@ enum mapa_policy_flags { MAPA_POLICY_BW_SENSITIVE = 1u, MAPA_POLICY_ANYTIME = 2u
  * MAPA_POLICY_BW_SENSITIVE, in either mode) changes what a request past the
  * context's work budget (mapa_ctx_set_work_budget) returns: instead of
  * MAPA_E_BUDGET, the best match of the request's seed dive (in bounded mode
- * the dive that seeds its cut-offs; in exhaustive mode a dive run after the
- * enumeration, for the requests past the budget only), with status
+ * the dive that seeds its cut-offs; in exhaustive mode a dive that depends
+ * only on the request, run after the enumeration for the requests past the
+ * budget, or beside it on a side stream when the group is produced in
+ * chunks, its match then used only if the request passes the budget), with status
  * MAPA_INEXACT, its
  * score, AggBW and PreservedBW recomputed from the tuple, count 0.  For such
  * a request the dive runs up to 256 k steps and is guided towards a match
