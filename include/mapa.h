@@ -296,9 +296,10 @@ int mapa_result_merge(int32_t nparts, const mapa_result *parts, mapa_result *out
  * after every chain decision the vertices whose time has passed are freed
  * before the next one, so a job holds its accelerators for its lifetime
  * whatever the round length.  DEPART events return a job's vertices before
- * later arrivals are decided.  Requests that arrive while a round is on the
- * GPU wait for the next round.  max_batch = 1 gives the plain per-request
- * form (one request per round). */
+ * later arrivals are decided.  Requests that arrive while a round's chain
+ * runs join its end between segments (in arrival order, up to the round's
+ * admission limit and 64 requests unless the round began larger).
+ * max_batch = 1 gives the plain per-request form (one request per round). */
 
 enum mapa_event_kind { MAPA_EVENT_ARRIVE = 0, MAPA_EVENT_DEPART = 1 };
 

@@ -208,6 +208,29 @@ uint64_t frontier_estimate(mapa_server srv, int32_t pattern_id) {
     return (1 + static_cast<uint64_t>(srv->deg_max)) * B * entry;
 }
 
+// Requests a round admits: the window, or while the parallel pass is backed
+// off a whole chain of up to kChainRound.
+int32_t admit_limit(mapa_server srv) {
+    return srv->spec_skip > 0 ? std::max(srv->window, std::min(srv->max_batch, kChainRound)) : srv->window;
+}
+
+// Moves the requests that have arrived by `now` from the queue into round,
+// in order, while the round holds fewer than limit requests and, under a
+// work budget, while the round's requests can all hold their largest
+// frontier at once (mem: the round's frontier bytes so far).  The caller
+// holds srv->mu.
+void admit_arrivals(mapa_server srv, std::vector<Pending> &round, int32_t limit, int64_t now, uint64_t &mem) {
+    const uint64_t mem_cap = mapa::engine_frontier_budget(srv->ctx->engine);
+    while (!srv->incoming.empty() && srv->incoming.front().ev.at_ns <= now &&
+           static_cast<int32_t>(round.size()) < limit) {
+        const uint64_t est = frontier_estimate(srv, srv->incoming.front().ev.pattern_id);
+        if (!round.empty() && mem + est > mem_cap) break;
+        mem += est;
+        round.push_back(srv->incoming.front());
+        srv->incoming.pop_front();
+    }
+}
+
 mapa::ServeLife life_args(mapa_server srv) {
     mapa::ServeLife lf;
     lf.life = srv->d_life;
@@ -314,7 +337,10 @@ int decide_round(mapa_server srv, std::vector<Pending> &round, std::vector<mapa_
     mapa_ctx ctx = srv->ctx;
     const mapa::TopoDevice &t = ctx->topos[srv->topo_id].dev;
     cudaStream_t st = mapa::engine_stream(ctx->engine);
-    const int32_t n = static_cast<int32_t>(round.size());
+    // n grows when requests that arrive during the round's chain join it;
+    // n0 is the round as admitted (the parallel pass's requests)
+    int32_t n = static_cast<int32_t>(round.size());
+    const int32_t n0 = n;
     // lifetimes that ended before the round: freed before its snapshot (the
     // device ends a lifetime no later than the host schedule says)
     int rc = MAPA_OK;
@@ -423,10 +449,40 @@ int decide_round(mapa_server srv, std::vector<Pending> &round, std::vector<mapa_
     if (!first_pass.empty()) publish(first_pass, res, snaps, deferred);
     // The chain runs in segments; after one that ended waiting (FIFO), the
     // rest of the chain waits too and is not decided.
-    const int32_t m_all = static_cast<int32_t>(chain.size());
     const int32_t seg = std::max(1, std::min(kChainSegment, n / 4));
     bool chain_blocked = false;
-    for (int32_t c0 = 0; c0 < m_all; c0 += seg) {
+    // Continuous batching: requests that arrive while the chain runs join
+    // its end between segments (they are later than every request of the
+    // round, so arrival order holds), up to the round's admission limit and
+    // at most kChainRound requests unless the round began larger.
+    const int32_t grow_limit = std::min(admit_limit(srv), std::max(n0, kChainRound));
+    uint64_t round_mem = 0;
+    for (const Pending &p : round) round_mem += frontier_estimate(srv, p.ev.pattern_id);
+    auto join_arrivals = [&]() {
+        const size_t before = round.size();
+        {
+            std::lock_guard<std::mutex> lock(srv->mu);
+            if (srv->stop) return;
+            admit_arrivals(srv, round, grow_limit, srv->now_ns(), round_mem);
+        }
+        for (size_t i = before; i < round.size(); ++i) {
+            chain.push_back(static_cast<int32_t>(i));
+            chain_pids.push_back(round[i].ev.pattern_id);
+            chain_bounded.push_back(static_cast<uint8_t>(
+                (round[i].ev.policy.mode == MAPA_MODE_BOUNDED ? mapa::kKindBounded : 0) |
+                ((round[i].ev.policy.flags & MAPA_POLICY_BW_SENSITIVE) ? mapa::kKindSensitive : 0)));
+        }
+        n = static_cast<int32_t>(round.size());
+        res.resize(n);
+        snaps.resize(static_cast<size_t>(n) * MAPA_MASK_WORDS, 0u);
+        deferred.resize(n, 0);
+        done_at.resize(n, -1);
+        gone.resize(n, 0);
+    };
+    for (int32_t c0 = 0;; c0 += seg) {
+        if (!chain_blocked) join_arrivals();
+        const int32_t m_all = static_cast<int32_t>(chain.size());
+        if (c0 >= m_all) break;
         const int32_t m = std::min(seg, m_all - c0);
         if (chain_blocked) {
             for (int32_t j = 0; j < m; ++j) deferred[chain[c0 + j]] = 1;
@@ -495,7 +551,8 @@ int decide_round(mapa_server srv, std::vector<Pending> &round, std::vector<mapa_
             }
         }
         freed_before(m);
-        if (speculate) srv->conflicts += static_cast<uint64_t>(m);  // decided again after an overlap
+        if (speculate)  // decided again after an overlap (not the requests that joined the chain)
+            for (int32_t j = 0; j < m; ++j) srv->conflicts += chain[c0 + j] < n0 ? 1u : 0u;
         publish(std::vector<int32_t>(chain.begin() + c0, chain.begin() + c0 + m), res, snaps, deferred);
     }
     srv->rounds += 1;
@@ -526,17 +583,19 @@ int decide_round(mapa_server srv, std::vector<Pending> &round, std::vector<mapa_
     // shrinks it towards twice what it committed, so contended stretches
     // spend little on speculative decisions that the chain redoes anyway.
     int32_t prefix = 0;  // decisions the parallel pass committed
-    for (int32_t i = 0; i < n; ++i)
+    for (int32_t i = 0; i < n0; ++i)
         if (speculate && srv->h_conflict[i] == 0) ++prefix;
     if (speculate) {
-        if (2 * prefix >= n) {
+        if (2 * prefix >= n0) {
             srv->spec_backoff = 0;
         } else {
             srv->spec_backoff = std::min(kMaxBackoff, std::max(1, 2 * srv->spec_backoff));
             srv->spec_skip = srv->spec_backoff;
         }
     }
-    if ((!speculate || chain.empty()) && requeue.empty())
+    int32_t redone = 0;  // chain requests from the parallel pass
+    for (const int32_t i : chain) redone += i < n0 ? 1 : 0;
+    if ((!speculate || redone == 0) && requeue.empty())
         srv->window = std::min(srv->max_batch, std::max(srv->window, 1) * 2);
     else if (speculate)
         srv->window = std::max(std::min(srv->max_batch, 8), std::min(srv->max_batch, 2 * prefix));
@@ -615,21 +674,8 @@ void worker_loop(mapa_server srv) {
             if (!departing.empty()) srv->blocked = false;
             // 2. arrivals in order, unless the head of the queue waits for a departure
             if (!srv->blocked) {
-                // while the parallel pass is backed off a round is one chain
-                const int32_t admit =
-                    srv->spec_skip > 0 ? std::max(srv->window, std::min(srv->max_batch, kChainRound)) : srv->window;
-                // frontier-memory budget: under a work budget, admit while the
-                // round's requests can all hold their largest frontier at once
-                const uint64_t mem_cap = mapa::engine_frontier_budget(srv->ctx->engine);
                 uint64_t mem = 0;
-                while (!srv->incoming.empty() && srv->incoming.front().ev.at_ns <= now &&
-                       static_cast<int32_t>(round.size()) < admit) {
-                    const uint64_t est = frontier_estimate(srv, srv->incoming.front().ev.pattern_id);
-                    if (!round.empty() && mem + est > mem_cap) break;
-                    mem += est;
-                    round.push_back(srv->incoming.front());
-                    srv->incoming.pop_front();
-                }
+                admit_arrivals(srv, round, admit_limit(srv), now, mem);
             }
             // a head that waits for accelerators while nothing can be released
             // any more is decided again (and answered MAPA_NO_FIT)
